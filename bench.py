@@ -1,0 +1,309 @@
+"""Benchmark: singular values of a dense 8192 x 8192 FP32 matrix on GB300.
+
+Workload (one step = the whole hot path once): nla_gesvd_vals on an
+8192 x 8192 FP32 matrix with entries iid U[-1, 1] (seeded), i.e. dense ->
+band (QR/LQ panels + trailing updates), band -> bidiagonal (bulge chase),
+bidiagonal -> singular values (bisection), with the tuned configuration when
+a tuned table is installed (kt_load_config) and the default otherwise.  The
+input (256 MiB) is larger than L2 (129 MB), so no flush is needed between
+steps; the library copies A into its workspace (preserve_a) as part of each
+step, so every step sees the same input.
+
+Metric: GFLOP/s = (4 m n^2 - 4 n^3 / 3) / time (the Householder
+bidiagonalisation count), whole-job (summed over ranks).  Multi-GPU runs are
+independent replicas (weak scaling): a single matrix does not shard.
+
+--impl reference times the FP64 CPU oracle (the only reference available for
+this method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_MAIN = 8192
+SEED = 280  # 200 + (n / 1024) * 10 for n = 8192
+SAMPLE_N = 1536  # oracle sample size (bounded CPU work)
+METRIC = "SVD GFLOP/s (4mn^2 - 4n^3/3 per matrix), singular values of a dense FP32 matrix"
+
+
+def flops(m, n):
+    m, n = max(m, n), min(m, n)
+    return 4.0 * m * n * n - 4.0 * n ** 3 / 3.0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def oracle_sample(n_sample, steps):
+    """Time the FP64 CPU oracle on U[-1, 1] n_sample^2 matrices; returns (GFLOP/s, seconds, cores)."""
+    import oracle
+    from paper_2608_21227_gb300 import inputs
+
+    A = inputs.uniform(n_sample, n_sample, SEED)
+    cores = host_cores()
+    oracle.svdvals(A[:64, :64], nthreads=cores)  # load + warm
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        oracle.svdvals(A, nthreads=cores)
+    dt = (time.perf_counter() - t0) / steps
+    return flops(n_sample, n_sample) / dt / 1e9, dt, cores
+
+
+def trail_flops_per_step(M, N, b, side):
+    """Algorithmic flops of every QR-side (side 0) or LQ-side (side 1) trailing update in one step."""
+    tot = 0.0
+    for kb in range(0, N, b):
+        nb = min(b, N - kb)
+        c0 = kb + nb
+        if c0 >= N:
+            break
+        if side == 0:
+            tot += 4.0 * nb * (M - kb) * (N - c0)
+        else:
+            tot += 4.0 * nb * (M - c0) * (N - c0)
+    return tot
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    steps = []
+    gf = None
+    for _ in range(args.warmup):
+        oracle_sample(SAMPLE_N, 1)
+    for _ in range(args.steps):
+        gf, dt, cores = oracle_sample(SAMPLE_N, 1)
+        steps.append(dt)
+    ms = float(np.median(steps)) * 1e3
+    value = flops(SAMPLE_N, SAMPLE_N) / (ms / 1e3) / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GFLOP/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"svdvals FP32 {N_MAIN}x{N_MAIN} U[-1,1]; reference = FP64 CPU oracle on a "
+                               f"{SAMPLE_N}x{SAMPLE_N} sample of the same distribution"},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": host_cores(), "kind": "oracle",
+                         "sample": f"{SAMPLE_N}x{SAMPLE_N} U[-1,1] per step"},
+        "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_MAIN)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+
+    from paper_2608_21227_gb300 import inputs, nla
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+
+    n = args.n
+    A = inputs.uniform_device(n, n, seed=SEED + rank, dtype=torch.float32, device=dev)
+    m_, n_, _ = nla.col_major_view(A)
+    need = nla.gesvd_vals_workspace(m_, n_, nla.F32, preserve_a=True)
+    work = nla.workspace(need, dev)
+    S = torch.empty(n, dtype=torch.float32, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        nla.gesvd_vals(A, preserve_a=True, work=work, S=S, info=info, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    assert int(info.item()) == 0, f"device info {int(info.item())}"
+
+    # ---------------- timed region (device-resident input)
+    clocks = ClockSampler(local)
+    clocks.start()
+    nla.trace_reset()
+    nla.trace_enable(True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    nla.trace_enable(False)
+    trace = nla.trace_read()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if pg is not None:
+        pg.all_reduce(t_max, op=pg.ReduceOp.MAX)
+    ms_max = float(t_max.item())
+    value = world * flops(n, n) / (ms_max / 1e3) / 1e9
+
+    # ---------------- end-to-end through the C ABI with host buffers
+    A_host = torch.empty((n, n), dtype=torch.float32, pin_memory=True)
+    A_host.copy_(A)
+    S_host = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    A_dev = torch.empty_like(A)
+    e2e_steps = max(2, min(args.steps, 3))
+    torch.cuda.synchronize(dev)
+    barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(e2e_steps):
+        A_dev.copy_(A_host, non_blocking=True)
+        nla.gesvd_vals(A_dev, work=work, S=S, info=info, stream=stream)
+        S_host.copy_(S, non_blocking=True)
+    f1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = f0.elapsed_time(f1) / e2e_steps
+    t_e2e = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+    if pg is not None:
+        pg.all_reduce(t_e2e, op=pg.ReduceOp.MAX)
+    e2e_value = world * flops(n, n) / (float(t_e2e.item()) / 1e3) / 1e9
+
+    # ---------------- roofline of the dominant kernel (live CUDA-event timing of its launches)
+    launches = sum(v[0] for v in trace.values())
+    dom = max(trace.items(), key=lambda kv: kv[1][1])[0] if trace else None
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    roof = None
+    if dom in ("trail_left", "trail_right"):
+        b = 32
+        fl = trail_flops_per_step(n, n, b, 0 if dom == "trail_left" else 1) * args.steps
+        achieved = fl / (trace[dom][1] / 1e3) / 1e12
+        sm_max = peaks.get("sm_max_mhz", 2070.0)
+        peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FFMA lanes x 2 flop x max SM clock
+        roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x max SM clock"}
+    elif dom is not None:
+        roof = {"kernel": dom, "bound": "latency", "achieved": None, "peak": None, "unit": None, "frac": None,
+                "traffic": None}
+
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": round(ms_max, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"svdvals FP32 {n}x{n} U[-1,1] seed {SEED}+rank (dense->band->bidiagonal->sigma)",
+                   "l2": "input 256 MiB > 129 MB L2; no flush", "parallelism": f"replicas x{world}"},
+        "e2e": {"value": round(e2e_value, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": n * n * 4,
+                "d2h_bytes_per_step": n * 4},
+        "gpu_launches": launches,
+        "kernels": {k: {"launches": v[0], "ms_per_step": round(v[1] / args.steps, 3)} for k, v in trace.items()},
+        "roofline": roof,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        gf, dt, cores = oracle_sample(SAMPLE_N, 1)
+        line["cpu_baseline"] = {"value": round(gf, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                                "sample": f"FP64 oracle on one {SAMPLE_N}x{SAMPLE_N} U[-1,1] matrix ({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * nla.h -- singular values of dense real matrices on one GB300 (sm_103a).
+ *
+ * The library computes the singular values of a dense m x n matrix by the
+ * two-stage reduction of the paper's Section 5.1.1 (Fig. 3, Algorithm 1):
+ *   stage 1  dense -> upper band of width b by tiled Householder QR / LQ panels
+ *            (GEQRT/TSQRT-style panel factorisation, Algorithm 1 steps
+ *            "QR sweep" / "LQ sweep") and a blocked trailing update
+ *            (UNMQR/TSMQR, Algorithm 2);
+ *   stage 2  band -> bidiagonal by bulge chasing (Section 5.1.1, Fig. 3);
+ *   stage 3  bidiagonal -> singular values (Section 5.1.1: "finally to ...
+ *            diagonal form"), here by Sturm-count bisection in FP64.
+ * Every step keeps the singular values intact because it applies orthogonal
+ * transformations only (Section 5.1.1).
+ *
+ * Conventions shared by every call:
+ *   - Pointers named d* are DEVICE pointers owned by the caller; pointers named
+ *     h* are host pointers.  The library never allocates device memory on
+ *     these paths: scratch comes from the caller's workspace (dWork).
+ *   - Matrices are column-major with leading dimension lda >= rows.  A
+ *     row-major PyTorch tensor of shape (r, c) passed as-is is the column-major
+ *     c x r matrix A^T, which has the same singular values.
+ *   - All work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream) and the call returns without synchronising.
+ *   - Argument errors are returned synchronously and nothing is enqueued.
+ *     Device-side outcomes go to the int pointed to by dInfo after the stream
+ *     completes: 0 = success, > 0 = number of values that did not converge,
+ *     < 0 = -(nla_status) of a device-side failure (e.g. -NLA_ERR_TIMEOUT when
+ *     a bounded inter-block wait gave up; the results are then undefined but
+ *     the context stays usable).
+ *   - m == 0 or n == 0 is a successful no-op.
+ *   - NaN or Inf entries give undefined singular values; no error is promised.
+ *   - nla_last_error() returns a thread-local message for the last non-OK
+ *     status returned on the calling thread.
+ */
+#ifndef NLA_H
+#define NLA_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *nla_stream_t; /* a cudaStream_t */
+
+typedef enum {
+    NLA_OK = 0,
+    NLA_ERR_ARG = 1,         /* invalid argument */
+    NLA_ERR_CUDA = 2,        /* a CUDA runtime call failed (message in nla_last_error) */
+    NLA_ERR_CONFIG = 3,      /* the launch configuration is not valid for this problem */
+    NLA_ERR_WORKSPACE = 4,   /* workspace too small or misaligned */
+    NLA_ERR_TIMEOUT = 5,     /* a bounded inter-block wait gave up (device side) */
+    NLA_ERR_NOCONV = 6,      /* an iteration hit its cap */
+    NLA_ERR_UNSUPPORTED = 7  /* problem outside the sizes this build supports */
+} nla_status;
+
+typedef enum { NLA_F64 = 0, NLA_F32 = 1 } nla_dtype;
+
+/* Operand precision of the trailing update (Algorithm 2).  NATIVE computes in
+ * the matrix dtype.  TF32 / BF16 round the (power-of-two column-scaled)
+ * operands to that type and run the contraction on the tensor cores with FP32
+ * accumulation; the matrix itself stays in its dtype, and panel
+ * factorisation, bulge chasing and the singular-value solve are unchanged. */
+typedef enum { NLA_UPD_NATIVE = 0, NLA_UPD_TF32 = 1, NLA_UPD_BF16 = 2 } nla_update;
+
+/* Launch configuration of the trailing-update kernels (Algorithm 2's tunable
+ * parameters, Section 5.2 search-space table, re-expressed for this GPU):
+ *   band            b  : band width = panel width (the pipeline parameter);
+ *   tile            th : rows (QR side) / columns (LQ side) of X staged per step;
+ *   threads            : threads per block (multiple of 32, <= 1024);
+ *   cols_per_block  cpb: the block owns 32*cpb columns (QR side) or rows (LQ
+ *                        side) of the trailing matrix;
+ *   unroll          u  : unroll factor of the reduction loop over the staged tile.
+ * A field <= 0 means "use the tuned or default value". */
+typedef struct {
+    int band;
+    int tile;
+    int threads;
+    int cols_per_block;
+    int unroll;
+} nla_cfg;
+
+typedef struct {
+    nla_update update;  /* trailing-update operand precision */
+    const nla_cfg *cfg; /* NULL = tuned table (kt_load_config) else defaults */
+    int preserve_a;     /* nonzero: A is copied to the workspace and left intact */
+} nla_opts;
+
+/* ---------------------------------------------------------------- whole SVD */
+
+/* Workspace bytes needed by nla_gesvd_vals for this problem and options. */
+nla_status nla_gesvd_vals_workspace(int m, int n, nla_dtype dtype, const nla_opts *opts,
+                                    size_t *bytes);
+
+/* Singular values of the column-major m x n matrix dA (dtype elements, lda >= m).
+ * dS receives min(m, n) values in descending order, in dtype.  dA is
+ * overwritten unless opts->preserve_a (or m < n, where A^T is formed in the
+ * workspace and dA is left intact).  dWork: >= nla_gesvd_vals_workspace bytes,
+ * 256-byte aligned.  dInfo: one device int (see conventions). */
+nla_status nla_gesvd_vals(int m, int n, nla_dtype dtype, void *dA, int lda, void *dS,
+                          void *dWork, size_t work_bytes, int *dInfo,
+                          const nla_opts *opts, nla_stream_t stream);
+
+/* Batched singular values of `batch` independent matrices of uneven shapes
+ * (one persistent launch; matrices bucketed by size, largest first).  hM, hN,
+ * hLda: host arrays of shapes.  dA_array / dS_array: DEVICE arrays of device
+ * pointers; matrix i is overwritten; dS_array[i] receives min(m_i, n_i)
+ * values, descending.  dInfo: `batch` device ints.  Only NLA_F32 and
+ * min(m_i, n_i) <= 256 are supported by the persistent kernel. */
+nla_status nla_gesvd_vals_batched_workspace(int batch, nla_dtype dtype, const int *hM,
+                                            const int *hN, size_t *bytes);
+nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *hM, const int *hN,
+                                  const int *hLda, void *const *dA_array, void *const *dS_array,
+                                  void *dWork, size_t work_bytes, int *dInfo,
+                                  const nla_opts *opts, nla_stream_t stream);
+
+/* ---------------------------------------------------------------- stages */
+
+/* Stage 1 (Algorithm 1): reduce the column-major m x n matrix dA (m >= n) to
+ * upper band form of width `band` in place.  On return the band
+ * (entries with 0 <= j - i <= band) holds the band matrix; the QR reflectors
+ * are stored below the diagonal of each panel column block and the LQ
+ * reflectors to the right of the band in each panel row block.  dTauQ, dTauP
+ * (dtype, ceil(n/band)*band entries each, may be NULL) receive the reflector
+ * scalars tau.  Returns NLA_ERR_ARG if m < n. */
+nla_status nla_gebrd_band_workspace(int m, int n, int band, nla_dtype dtype,
+                                    const nla_opts *opts, size_t *bytes);
+nla_status nla_gebrd_band(int m, int n, int band, nla_dtype dtype, void *dA, int lda,
+                          void *dTauQ, void *dTauP, void *dWork, size_t work_bytes,
+                          int *dInfo, const nla_opts *opts, nla_stream_t stream);
+
+/* Copy the upper band (0 <= j - i <= band) of the column-major n x n matrix dA
+ * into compact band storage dAB (dtype, ldab >= 3*band + 1): entry (i, j)
+ * with -band <= j - i <= 2*band lives at dAB[(2*band + i - j) + j*ldab]; rows
+ * outside the upper band are zeroed (room for the bulges of stage 2). */
+nla_status nla_band_extract(int n, int band, nla_dtype dtype, const void *dA, int lda,
+                            void *dAB, int ldab, nla_stream_t stream);
+
+/* Stage 2: reduce the upper band matrix in dAB (layout of nla_band_extract,
+ * overwritten) to upper bidiagonal form by Householder bulge chasing; dD (n)
+ * and dE (n-1) receive the FP64 diagonal and superdiagonal. */
+nla_status nla_band2bd_workspace(int n, int band, nla_dtype dtype, size_t *bytes);
+nla_status nla_band2bd(int n, int band, nla_dtype dtype, void *dAB, int ldab, double *dD,
+                       double *dE, void *dWork, size_t work_bytes, int *dInfo,
+                       const nla_opts *opts, nla_stream_t stream);
+
+/* Stage 3: singular values of the upper bidiagonal (dD, dE), FP64 bisection on
+ * Sturm counts of the Golub-Kahan tridiagonal; dS receives n values
+ * descending, converted to dtype. */
+nla_status nla_bdsvd_vals(int n, const double *dD, const double *dE, void *dS,
+                          nla_dtype dtype, int *dInfo, nla_stream_t stream);
+
+/* ---------------------------------------------------------------- tracing */
+
+/* Per-kernel-class timing (the tuner's timing observer, paper Section 4.2,
+ * made available to callers).  While enabled, every kernel the library
+ * launches is bracketed by a pair of CUDA events recorded on the launching
+ * stream; nla_trace_read synchronises those events and returns, per kernel
+ * class, the number of launches and their summed device time.  Classes:
+ * "panel_qr", "panel_lq", "trail_left", "trail_right", "stage_copy",
+ * "band_extract", "band2bd", "bisect", "batched".  Tracing adds two event
+ * records per launch; it is off by default. */
+typedef struct {
+    const char *name;   /* static string owned by the library */
+    int launches;
+    double total_ms;
+} nla_trace_entry;
+nla_status nla_trace_enable(int on);
+/* Fills up to max_entries entries and returns how many classes were seen. */
+int nla_trace_read(nla_trace_entry *out, int max_entries);
+void nla_trace_reset(void);
+
+/* Message for the last non-OK status returned on this thread. */
+const char *nla_last_error(void);
+
+/* Library version string. */
+const char *nla_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NLA_H */

@@ -1,0 +1,257 @@
+// band.cu -- input staging, band extraction and stage 2 (band -> bidiagonal).
+//
+// Band storage (entries with -b <= j - i <= 2b): A(i, j) at AB[(2b + i - j) + j*ldab],
+// ldab >= 3b + 1.  Stage 1 leaves an upper band 0 <= j - i <= b; the extra b
+// rows below and b rows above hold the bulges created while chasing.
+//
+// Bulge chasing (Section 5.1.1: band -> bidiagonal by orthogonal
+// transformations that keep the singular values intact).  Sweep s makes row s
+// bidiagonal.  Its block step k (k = 0, 1, ...) applies
+//   right:  a reflector on columns c0..c1 = s+kb+1 .. s+(k+1)b that zeroes row
+//           tr (tr = s for k = 0, s+(k-1)b+1 otherwise) beyond column c0; it is
+//           applied to rows tr..c1 and fills the block below the diagonal;
+//   left:   a reflector on rows c0..r1 = c0 .. s+(k+1)b that zeroes column c0
+//           below the diagonal; it is applied to columns c0..s+(k+2)b and fills
+//           row c0 beyond the band, which the right reflector of step k+1
+//           removes.
+// Fill that one sweep leaves behind (the rest of each triangular bulge) is
+// exactly what the next sweep's reflectors at the same position remove.  Block
+// step k of sweep s touches rows s+(k-1)b+1 .. s+(k+1)b only, so it is
+// independent of every step >= k+3 of sweep s-1: sweeps run concurrently,
+// one per block, each waiting (bounded spin) until its predecessor has
+// finished three more steps.
+#include <algorithm>
+#include <climits>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace nla {
+
+// ------------------------------------------------------------------ copies
+template <typename T>
+__global__ void copy_kernel(const T *__restrict__ A, long lda, int m, int n, T *__restrict__ B, long ldb) {
+    long total = (long)m * n;
+    for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+        long j = idx / m, i = idx % m;
+        B[i + j * ldb] = A[i + j * lda];
+    }
+}
+
+// B (n x m) = A^T via 32 x 32 shared-memory tiles
+template <typename T>
+__global__ void transpose_kernel(const T *__restrict__ A, long lda, int m, int n, T *__restrict__ B, long ldb) {
+    __shared__ T tile[32][33];
+    int bi = blockIdx.x * 32, bj = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        int i = bi + threadIdx.x, j = bj + y;
+        if (i < m && j < n) tile[y][threadIdx.x] = A[i + (long)j * lda];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        int j = bj + threadIdx.x, i = bi + y;  // B(j, i) = A(i, j)
+        if (i < m && j < n) B[j + (long)i * ldb] = tile[threadIdx.x][y];
+    }
+}
+
+template <typename T>
+cudaError_t copy_matrix(const T *A, long lda, int m, int n, T *B, long ldb, bool transpose, cudaStream_t st) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    if (!transpose) {
+        long total = (long)m * n;
+        int blocks = (int)std::min<long>((total + 255) / 256, 152L * 16);
+        copy_kernel<T><<<blocks, 256, 0, st>>>(A, lda, m, n, B, ldb);
+    } else {
+        dim3 grid((m + 31) / 32, (n + 31) / 32);
+        transpose_kernel<T><<<grid, dim3(32, 8), 0, st>>>(A, lda, m, n, B, ldb);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void band_extract_kernel(const T *__restrict__ A, long lda, int n, int b, T *__restrict__ AB,
+                                    long ldab) {
+    const int j = blockIdx.x;
+    if (j >= n) return;
+    for (int q = threadIdx.x; q < ldab; q += blockDim.x) {
+        int i = q - 2 * b + j;  // storage row q holds A(i, j)
+        T v = T(0);
+        if (q >= b && q <= 2 * b && i >= 0) v = A[i + (long)j * lda];
+        AB[q + (long)j * ldab] = v;
+    }
+}
+
+template <typename T>
+cudaError_t band_extract(const T *A, long lda, int n, int b, T *AB, long ldab, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    band_extract_kernel<T><<<n, 128, 0, st>>>(A, lda, n, b, AB, ldab);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ bulge chasing
+constexpr int kChaseThreads = 128;
+
+size_t band2bd_scratch_bytes(int n) { return (size_t)std::max(n, 1) * sizeof(int); }
+
+template <typename T>
+struct Band {
+    T *AB;
+    long ldab;
+    int b2;  // 2b
+    NLA_DEV T *at(int i, int j) const { return AB + (b2 + i - j) + (long)j * ldab; }
+};
+
+template <typename T>
+NLA_DEV T ldg_cg(const T *p) { return __ldcg(p); }
+
+// One Householder reflector from x[0..L-1] (stride of the band accessor given by
+// the caller).  Warp 0 computes it; the result goes to v[] (v[0] = 1), *tau,
+// *beta in shared memory.  Returns nothing; caller syncs.
+template <typename T>
+NLA_DEV void make_reflector(const T *x0, int L, double *v, double *tau_out, double *beta_out) {
+    // called by all lanes of warp 0; x0[i] already staged in v[] as doubles
+    const int lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int i = 1 + lane; i < L; i += 32) s += v[i] * v[i];
+    s = warp_sum(s);
+    double alpha = v[0];
+    double tau = 0.0, beta = alpha, scale = 0.0;
+    if (s > 0.0) {
+        double r = sqrt(alpha * alpha + s);
+        beta = alpha >= 0.0 ? -r : r;
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+    }
+    __syncwarp();
+    for (int i = 1 + lane; i < L; i += 32) v[i] = (tau != 0.0) ? v[i] * scale : 0.0;
+    if (lane == 0) {
+        v[0] = 1.0;
+        *tau_out = tau;
+        *beta_out = beta;
+    }
+    (void)x0;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kChaseThreads)
+band2bd_kernel(T *AB, long ldab, int n, int b, int *progress, int *info) {
+    __shared__ double v[128];
+    __shared__ double sh_tau, sh_beta;
+    __shared__ int sh_fail;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    Band<T> A{AB, ldab, 2 * b};
+    const int nsweeps = n - 2;
+    if (tid == 0) sh_fail = 0;
+    __syncthreads();
+
+    for (int s = blockIdx.x; s < nsweeps; s += gridDim.x) {
+        for (int k = 0;; ++k) {
+            const int c0 = s + k * b + 1;
+            if (c0 > n - 1) break;
+            if (s > 0) {
+                if (tid == 0 && !spin_until_geq(&progress[s - 1], k + 3, info)) sh_fail = 1;
+                __syncthreads();
+                if (sh_fail) return;
+            }
+            // ---------------- right reflector on columns c0..c1, zeroing row tr
+            const int tr = (k == 0) ? s : s + (k - 1) * b + 1;
+            const int c1 = min(s + (k + 1) * b, n - 1);
+            const int L = c1 - c0 + 1;
+            if (L >= 2) {
+                for (int c = tid; c < L; c += blockDim.x) v[c] = (double)ldg_cg(A.at(tr, c0 + c));
+                __syncthreads();
+                if (warp == 0) make_reflector<T>(nullptr, L, v, &sh_tau, &sh_beta);
+                __syncthreads();
+                const double tau = sh_tau;
+                if (tau != 0.0) {
+                    for (int c = tid; c < L; c += blockDim.x) __stcg(A.at(tr, c0 + c), c == 0 ? (T)sh_beta : T(0));
+                    // rows tr+1 .. c1: one warp per row
+                    for (int i = tr + 1 + warp; i <= c1; i += nwarps) {
+                        double wsum = 0.0;
+                        for (int c = lane; c < L; c += 32) wsum += (double)ldg_cg(A.at(i, c0 + c)) * v[c];
+                        wsum = warp_sum(wsum) * tau;
+                        for (int c = lane; c < L; c += 32) {
+                            T *p = A.at(i, c0 + c);
+                            __stcg(p, (T)((double)ldg_cg(p) - wsum * v[c]));
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            // ---------------- left reflector on rows c0..r1, zeroing column c0
+            const int r1 = min(s + (k + 1) * b, n - 1);
+            const int L2 = r1 - c0 + 1;
+            const int cend = min(s + (k + 2) * b, n - 1);
+            if (L2 >= 2) {
+                for (int r = tid; r < L2; r += blockDim.x) v[r] = (double)ldg_cg(A.at(c0 + r, c0));
+                __syncthreads();
+                if (warp == 0) make_reflector<T>(nullptr, L2, v, &sh_tau, &sh_beta);
+                __syncthreads();
+                const double tau = sh_tau;
+                if (tau != 0.0) {
+                    for (int r = tid; r < L2; r += blockDim.x) __stcg(A.at(c0 + r, c0), r == 0 ? (T)sh_beta : T(0));
+                    for (int j = c0 + 1 + warp; j <= cend; j += nwarps) {
+                        double wsum = 0.0;
+                        for (int r = lane; r < L2; r += 32) wsum += (double)ldg_cg(A.at(c0 + r, j)) * v[r];
+                        wsum = warp_sum(wsum) * tau;
+                        for (int r = lane; r < L2; r += 32) {
+                            T *p = A.at(c0 + r, j);
+                            __stcg(p, (T)((double)ldg_cg(p) - wsum * v[r]));
+                        }
+                    }
+                }
+            }
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) st_release(&progress[s], k + 1);
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) st_release(&progress[s], INT_MAX);
+    }
+}
+
+template <typename T>
+__global__ void bidiag_extract_kernel(const T *__restrict__ AB, long ldab, int n, int b, double *d, double *e) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        d[i] = (double)AB[2 * b + (long)i * ldab];
+        if (i + 1 < n) e[i] = (double)AB[(2 * b - 1) + (long)(i + 1) * ldab];
+    }
+}
+
+template <typename T>
+cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *scratch, int *info,
+                    cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    int *progress = reinterpret_cast<int *>(scratch);
+    const int nsweeps = n - 2;
+    if (nsweeps > 0 && b > 1) {
+        cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)nsweeps, st);
+        if (err != cudaSuccess) return err;
+        int grid = std::min(nsweeps, device_sm_count());
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kChaseThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        err = cudaLaunchKernelEx(&cfg, band2bd_kernel<T>, AB, ldab, n, b, progress, info);
+        if (err != cudaSuccess) return err;
+    }
+    bidiag_extract_kernel<T><<<(n + 255) / 256, 256, 0, st>>>(AB, ldab, n, b, d, e);
+    return cudaGetLastError();
+}
+
+#define NLA_INST(T)                                                                                       \
+    template cudaError_t copy_matrix<T>(const T *, long, int, int, T *, long, bool, cudaStream_t);      \
+    template cudaError_t band_extract<T>(const T *, long, int, int, T *, long, cudaStream_t);           \
+    template cudaError_t band2bd<T>(T *, long, int, int, double *, double *, void *, int *, cudaStream_t);
+NLA_INST(double)
+NLA_INST(float)
+#undef NLA_INST
+
+}  // namespace nla

@@ -1,0 +1,93 @@
+// common.cuh -- small device/host helpers shared by the library's kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/nla.h"
+
+#define NLA_DEV __device__ __forceinline__
+
+namespace nla {
+
+// Device-side failure codes written to the caller's info word (negated status).
+constexpr int kInfoTimeout = -NLA_ERR_TIMEOUT;
+
+// Budget for every inter-block spin-wait, in nanoseconds of %globaltimer.
+// A wait that exceeds it records kInfoTimeout and the kernel returns.
+constexpr unsigned long long kSpinBudgetNs = 2000000000ull;  // 2 s
+
+NLA_DEV unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+NLA_DEV unsigned int ld_acquire(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+NLA_DEV int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+NLA_DEV void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Spin until *p >= target or the budget runs out.  Called by one thread.
+// Returns true on success; on timeout records kInfoTimeout in *info.
+NLA_DEV bool spin_until_geq(const unsigned int *p, unsigned int target, int *info) {
+    if (ld_acquire(p) >= target) return true;
+    unsigned long long t0 = global_ns();
+    unsigned int backoff = 32;
+    while (true) {
+        if (ld_acquire(p) >= target) return true;
+        if (info && ld_acquire(info) == kInfoTimeout) return false;  // someone else gave up
+        if (global_ns() - t0 > kSpinBudgetNs) {
+            if (info) atomicExch(info, kInfoTimeout);
+            return false;
+        }
+        __nanosleep(backoff);
+        if (backoff < 256) backoff <<= 1;
+    }
+}
+
+NLA_DEV bool spin_until_geq(const int *p, int target, int *info) {
+    if (ld_acquire(p) >= target) return true;
+    unsigned long long t0 = global_ns();
+    unsigned int backoff = 32;
+    while (true) {
+        if (ld_acquire(p) >= target) return true;
+        if (info && ld_acquire(info) == kInfoTimeout) return false;
+        if (global_ns() - t0 > kSpinBudgetNs) {
+            if (info) atomicExch(info, kInfoTimeout);
+            return false;
+        }
+        __nanosleep(backoff);
+        if (backoff < 256) backoff <<= 1;
+    }
+}
+
+template <typename T>
+NLA_DEV T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+NLA_DEV double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Loads that bypass L1 (data written by other blocks during the same launch).
+NLA_DEV double ld_cg(const double *p) { return __ldcg(p); }
+NLA_DEV float ld_cg(const float *p) { return __ldcg(p); }
+
+}  // namespace nla

@@ -1,0 +1,75 @@
+// kernels.cuh -- launch wrappers for every device kernel of the library.
+// Each returns cudaSuccess or the launch error; all work goes on `st`.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace nla {
+
+// ---------------------------------------------------------------- panel
+// Householder factorisation of an M x nb panel whose element (r, c) lives at
+// P[r*rs + c*cs] (QR panel: rs = 1, cs = lda; LQ panel seen transposed:
+// rs = lda, cs = 1).  Reflector tails overwrite the strictly lower part,
+// R the upper part; tau (nb) and the compact-WY factor T (nb x nb, column
+// major, upper triangular, ld nb) are written in the panel's type.
+struct PanelCtl {
+    unsigned int *bar;   // 2 counters (barrier, exit); zero before first use
+    double *part;        // >= panel_part_doubles(P) doubles of scratch
+    int *info;           // device info word (timeout reporting)
+};
+size_t panel_part_doubles(int P);
+int panel_max_ctas();    // cooperative CTAs usable by the panel kernel
+template <typename T>
+cudaError_t panel_factor(T *P, long rs, long cs, int M, int nb, T *tau, T *Tm,
+                         const PanelCtl &ctl, cudaStream_t st);
+
+// ---------------------------------------------------------------- trailing update
+struct UpdCfg {
+    int tile, threads, cpb, unroll;
+};
+// Validity of a configuration for the SIMT trailing-update kernels
+// (side 0 = QR/left, 1 = LQ/right); elem = bytes per element.
+bool upd_cfg_valid(int side, int elem, int nb, const UpdCfg &c, size_t *smem_bytes);
+
+// QR side: X (M x N at X, ldx) <- (I - V T V^T)^T X, V = unit lower M x nb at Vp (ldv).
+template <typename T>
+cudaError_t trail_left(T *X, long ldx, int M, int N, const T *Vp, long ldv, int nb,
+                       const T *Tm, const UpdCfg &c, cudaStream_t st);
+// LQ side: X (M x N) <- X (I - V T V^T), V = unit lower N x nb stored transposed:
+// V(c, k) = Vt[k + c*ldvt].
+template <typename T>
+cudaError_t trail_right(T *X, long ldx, int M, int N, const T *Vt, long ldvt, int nb,
+                        const T *Tm, const UpdCfg &c, cudaStream_t st);
+
+// Mixed precision (FP64 matrix, TF32 or BF16 tensor-core contraction).
+// prec: 1 = TF32, 2 = BF16.
+cudaError_t trail_left_tc(double *X, long ldx, int M, int N, const double *Vp, long ldv, int nb,
+                          const double *Tm, int prec, void *scratch, size_t scratch_bytes,
+                          cudaStream_t st);
+cudaError_t trail_right_tc(double *X, long ldx, int M, int N, const double *Vt, long ldvt,
+                           int nb, const double *Tm, int prec, void *scratch,
+                           size_t scratch_bytes, cudaStream_t st);
+size_t trail_tc_scratch_bytes(int M, int N, int nb);
+bool trail_tc_available();
+
+// ---------------------------------------------------------------- copies
+template <typename T>
+cudaError_t copy_matrix(const T *A, long lda, int m, int n, T *B, long ldb, bool transpose,
+                        cudaStream_t st);
+template <typename T>
+cudaError_t band_extract(const T *A, long lda, int n, int b, T *AB, long ldab, cudaStream_t st);
+
+// ---------------------------------------------------------------- stage 2 / 3
+size_t band2bd_scratch_bytes(int n);
+template <typename T>
+cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *scratch,
+                    int *info, cudaStream_t st);
+template <typename T>
+cudaError_t bdsvd_bisect(int n, const double *d, const double *e, T *S, int *info,
+                         cudaStream_t st);
+
+int device_sm_count();
+
+}  // namespace nla

@@ -1,0 +1,289 @@
+// update.cu -- blocked trailing-matrix update (the UNMQR/TSMQR step of
+// Algorithm 1, whose GPU kernel is Algorithm 2), FP64 and FP32 SIMT paths.
+//
+// QR side:  X <- (I - V T V^T)^T X = X - V (T^T (V^T X))      (X below/right of a tile column)
+// LQ side:  X <- X (I - V T V^T)   = X - ((X V) T) V^T        (X below a tile row)
+//
+// As in Algorithm 2, one block owns a strip of the trailing matrix -- 32*cpb
+// columns on the QR side, 32*cpb rows on the LQ side -- over its whole extent,
+// so the reflector block is applied in three steps without a grid-wide
+// reduction: (1) W = V^T X_strip accumulated over tiles of `tile` rows staged
+// through shared memory (Algorithm 2's reflector dot products, here all nb at
+// once), (2) W <- T^T W with the compact-WY factor, (3) X_strip -= V W, tile by
+// tile.  V is unit lower trapezoidal: its implicit unit diagonal and zero upper
+// part are substituted while staging, so the panel's stored R is never read
+// as reflector data.  Accumulation is in the matrix type.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace nla {
+
+constexpr int kMaxItems = 32;     // W entries held in registers per thread
+constexpr size_t kSmemLimit = 227 * 1024;
+
+static size_t left_smem(int elem, int nb, int th, int w) {
+    return (size_t)elem * ((size_t)th * (nb + 1) + (size_t)th * (w + 1) + (size_t)nb * w);
+}
+static size_t right_smem(int elem, int nb, int th, int h) {
+    return (size_t)elem * ((size_t)th * h + (size_t)th * nb + (size_t)nb * h);
+}
+
+bool upd_cfg_valid(int side, int elem, int nb, const UpdCfg &c, size_t *smem_bytes) {
+    if (nb < 1 || nb > 64) return false;
+    if (c.threads < 32 || c.threads > 1024 || c.threads % 32) return false;
+    if (c.cpb < 1 || c.cpb > 8 || c.tile < 1 || c.tile > 256) return false;
+    if (c.unroll != 1 && c.unroll != 2 && c.unroll != 4) return false;
+    const int w = 32 * c.cpb;
+    const long items = (long)nb * w;
+    if (items % c.threads) return false;  // every thread owns the same number of W entries
+    const long per = items / c.threads;
+    if (per < 1 || per > kMaxItems) return false;
+    if ((long)c.tile * w < c.threads) return false;  // phase-3 tile must cover the block
+    size_t sm = side == 0 ? left_smem(elem, nb, c.tile, w) : right_smem(elem, nb, c.tile, w);
+    if (sm > kSmemLimit) return false;
+    if (smem_bytes) *smem_bytes = sm;
+    return true;
+}
+
+// -------------------------------------------------------------------- QR side
+template <typename T, int U>
+__global__ void trail_left_kernel(T *__restrict__ X, long ldx, int M, int N, const T *__restrict__ V,
+                                  long ldv, int nb, const T *__restrict__ Tm, int th, int w) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ldvs = nb + 1, ldxs = w + 1;
+    T *Vs = reinterpret_cast<T *>(smem_raw);  // th x nb  (row r at Vs + r*ldvs)
+    T *Xs = Vs + (size_t)th * ldvs;          // th x w   (row r at Xs + r*ldxs)
+    T *Ws = Xs + (size_t)th * ldxs;          // nb x w   (row k at Ws + k*w)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int c0 = blockIdx.x * w;
+    const int wc = min(w, N - c0);
+    const int items = nb * w / nt;
+
+    T acc[kMaxItems];
+#pragma unroll
+    for (int i = 0; i < kMaxItems; ++i) acc[i] = T(0);
+
+    // (1) W = V^T X_strip
+    for (int r0 = 0; r0 < M; r0 += th) {
+        const int rows = min(th, M - r0);
+        for (int idx = tid; idx < th * nb; idx += nt) {
+            int r = idx % th, k = idx / th, gr = r0 + r;
+            T v = T(0);
+            if (r < rows) v = gr > k ? V[gr + (long)k * ldv] : (gr == k ? T(1) : T(0));
+            Vs[r * ldvs + k] = v;
+        }
+        for (int idx = tid; idx < th * w; idx += nt) {
+            int r = idx % th, c = idx / th;
+            Xs[r * ldxs + c] = (r < rows && c < wc) ? X[(r0 + r) + (long)(c0 + c) * ldx] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kMaxItems; ++i) {
+            if (i < items) {
+                const int it = tid + i * nt, k = it / w, c = it % w;
+                T s = acc[i];
+#pragma unroll U
+                for (int r = 0; r < rows; ++r) s += Vs[r * ldvs + k] * Xs[r * ldxs + c];
+                acc[i] = s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < kMaxItems; ++i)
+        if (i < items) {
+            const int it = tid + i * nt;
+            Ws[it] = acc[i];  // it = k*w + c
+        }
+    __syncthreads();
+    // (2) W <- T^T W : W'(i, c) = sum_{k <= i} T(k, i) W(k, c)
+#pragma unroll
+    for (int i = 0; i < kMaxItems; ++i)
+        if (i < items) {
+            const int it = tid + i * nt, ii = it / w, c = it % w;
+            T s = T(0);
+            for (int k = 0; k <= ii; ++k) s += Tm[k + (long)ii * nb] * Ws[k * w + c];
+            acc[i] = s;
+        }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kMaxItems; ++i)
+        if (i < items) Ws[tid + i * nt] = acc[i];
+    __syncthreads();
+    // (3) X_strip -= V W'
+    for (int r0 = 0; r0 < M; r0 += th) {
+        const int rows = min(th, M - r0);
+        for (int idx = tid; idx < th * nb; idx += nt) {
+            int r = idx % th, k = idx / th, gr = r0 + r;
+            T v = T(0);
+            if (r < rows) v = gr > k ? V[gr + (long)k * ldv] : (gr == k ? T(1) : T(0));
+            Vs[r * ldvs + k] = v;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < th * w; idx += nt) {
+            int r = idx % th, c = idx / th;
+            if (r < rows && c < wc) {
+                T s = T(0);
+#pragma unroll 4
+                for (int k = 0; k < nb; ++k) s += Vs[r * ldvs + k] * Ws[k * w + c];
+                T *px = X + (r0 + r) + (long)(c0 + c) * ldx;
+                *px = *px - s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// -------------------------------------------------------------------- LQ side
+template <typename T, int U>
+__global__ void trail_right_kernel(T *__restrict__ X, long ldx, int M, int N, const T *__restrict__ Vt,
+                                   long ldvt, int nb, const T *__restrict__ Tm, int th, int h) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);  // th cols x h rows (col c at Xs + c*h)
+    T *Vs = Xs + (size_t)th * h;             // th x nb (row c at Vs + c*nb)
+    T *Ys = Vs + (size_t)th * nb;            // nb x h  (col k at Ys + k*h)
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int i0 = blockIdx.x * h;
+    const int hr = min(h, M - i0);
+    const int items = nb * h / nt;
+
+    T acc[kMaxItems];
+#pragma unroll
+    for (int i = 0; i < kMaxItems; ++i) acc[i] = T(0);
+
+    // (1) Y = X_strip V
+    for (int cb = 0; cb < N; cb += th) {
+        const int cols = min(th, N - cb);
+        for (int idx = tid; idx < th * h; idx += nt) {
+            int i = idx % h, c = idx / h;
+            Xs[c * h + i] = (i < hr && c < cols) ? X[(i0 + i) + (long)(cb + c) * ldx] : T(0);
+        }
+        for (int idx = tid; idx < th * nb; idx += nt) {
+            int k = idx % nb, c = idx / nb, gc = cb + c;
+            T v = T(0);
+            if (c < cols) v = gc > k ? Vt[k + (long)gc * ldvt] : (gc == k ? T(1) : T(0));
+            Vs[c * nb + k] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < kMaxItems; ++q) {
+            if (q < items) {
+                const int it = tid + q * nt, i = it % h, k = it / h;
+                T s = acc[q];
+#pragma unroll U
+                for (int c = 0; c < cols; ++c) s += Xs[c * h + i] * Vs[c * nb + k];
+                acc[q] = s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < kMaxItems; ++q)
+        if (q < items) Ys[tid + q * nt] = acc[q];  // it = k*h + i
+    __syncthreads();
+    // (2) Y <- Y T : Y'(i, k) = sum_{j <= k} Y(i, j) T(j, k)
+#pragma unroll
+    for (int q = 0; q < kMaxItems; ++q)
+        if (q < items) {
+            const int it = tid + q * nt, i = it % h, k = it / h;
+            T s = T(0);
+            for (int j = 0; j <= k; ++j) s += Ys[j * h + i] * Tm[j + (long)k * nb];
+            acc[q] = s;
+        }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kMaxItems; ++q)
+        if (q < items) Ys[tid + q * nt] = acc[q];
+    __syncthreads();
+    // (3) X_strip -= Y' V^T
+    for (int cb = 0; cb < N; cb += th) {
+        const int cols = min(th, N - cb);
+        for (int idx = tid; idx < th * nb; idx += nt) {
+            int k = idx % nb, c = idx / nb, gc = cb + c;
+            T v = T(0);
+            if (c < cols) v = gc > k ? Vt[k + (long)gc * ldvt] : (gc == k ? T(1) : T(0));
+            Vs[c * nb + k] = v;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < th * h; idx += nt) {
+            int i = idx % h, c = idx / h;
+            if (i < hr && c < cols) {
+                T s = T(0);
+#pragma unroll 4
+                for (int k = 0; k < nb; ++k) s += Ys[k * h + i] * Vs[c * nb + k];
+                T *px = X + (i0 + i) + (long)(cb + c) * ldx;
+                *px = *px - s;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int U>
+static cudaError_t launch_left(T *X, long ldx, int M, int N, const T *V, long ldv, int nb, const T *Tm,
+                               const UpdCfg &c, size_t smem, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(trail_left_kernel<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemLimit);
+        attr = true;
+    }
+    const int w = 32 * c.cpb;
+    dim3 grid((N + w - 1) / w);
+    trail_left_kernel<T, U><<<grid, c.threads, smem, st>>>(X, ldx, M, N, V, ldv, nb, Tm, c.tile, w);
+    return cudaGetLastError();
+}
+
+template <typename T, int U>
+static cudaError_t launch_right(T *X, long ldx, int M, int N, const T *Vt, long ldvt, int nb,
+                                const T *Tm, const UpdCfg &c, size_t smem, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(trail_right_kernel<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmemLimit);
+        attr = true;
+    }
+    const int h = 32 * c.cpb;
+    dim3 grid((M + h - 1) / h);
+    trail_right_kernel<T, U><<<grid, c.threads, smem, st>>>(X, ldx, M, N, Vt, ldvt, nb, Tm, c.tile, h);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t trail_left(T *X, long ldx, int M, int N, const T *Vp, long ldv, int nb, const T *Tm,
+                       const UpdCfg &c, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
+    size_t smem = 0;
+    if (!upd_cfg_valid(0, (int)sizeof(T), nb, c, &smem)) return cudaErrorInvalidConfiguration;
+    switch (c.unroll) {
+        case 1: return launch_left<T, 1>(X, ldx, M, N, Vp, ldv, nb, Tm, c, smem, st);
+        case 2: return launch_left<T, 2>(X, ldx, M, N, Vp, ldv, nb, Tm, c, smem, st);
+        default: return launch_left<T, 4>(X, ldx, M, N, Vp, ldv, nb, Tm, c, smem, st);
+    }
+}
+
+template <typename T>
+cudaError_t trail_right(T *X, long ldx, int M, int N, const T *Vt, long ldvt, int nb, const T *Tm,
+                        const UpdCfg &c, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
+    size_t smem = 0;
+    if (!upd_cfg_valid(1, (int)sizeof(T), nb, c, &smem)) return cudaErrorInvalidConfiguration;
+    switch (c.unroll) {
+        case 1: return launch_right<T, 1>(X, ldx, M, N, Vt, ldvt, nb, Tm, c, smem, st);
+        case 2: return launch_right<T, 2>(X, ldx, M, N, Vt, ldvt, nb, Tm, c, smem, st);
+        default: return launch_right<T, 4>(X, ldx, M, N, Vt, ldvt, nb, Tm, c, smem, st);
+    }
+}
+
+template cudaError_t trail_left<double>(double *, long, int, int, const double *, long, int,
+                                        const double *, const UpdCfg &, cudaStream_t);
+template cudaError_t trail_left<float>(float *, long, int, int, const float *, long, int, const float *,
+                                       const UpdCfg &, cudaStream_t);
+template cudaError_t trail_right<double>(double *, long, int, int, const double *, long, int,
+                                         const double *, const UpdCfg &, cudaStream_t);
+template cudaError_t trail_right<float>(float *, long, int, int, const float *, long, int,
+                                        const float *, const UpdCfg &, cudaStream_t);
+
+}  // namespace nla
