@@ -8,8 +8,9 @@ Plain restatements used to check the library's auto-tuner (kt_tune):
 * the search spaces: the paper's own (Section 5.2 table) and the one this
   library tunes over (tile x band x threads x cols_per_block x unroll);
 * the validity rule of the trailing-update kernels, written out from its
-  definition (every thread owns the same whole number of W entries, at most
-  32; a staged tile covers the block; shared memory <= 227 KB);
+  definition (the block tiles the strip into 4-column groups and the band into
+  groups of 1, 2, 4 or 8 reflectors; a staged tile splits into whole 4-row
+  sub-blocks per thread; shared memory <= 227 KB);
 * SplitMix64 (Steele, Lea & Flood 2014), the counter-based generator both
   sides use to draw the random-5% baseline sample;
 * summary ratios: optimal / median / default runtimes.
@@ -36,26 +37,30 @@ def space(tiles=TILES, bands=BANDS, threads=THREADS, cpbs=CPBS, unrolls=UNROLLS)
 
 
 def smem_bytes(side, elem, nb, tile, w):
-    if side == 0:
-        return elem * (tile * (nb + 1) + tile * (w + 1) + nb * w)
-    return elem * (tile * w + tile * nb + nb * w)
+    """Shared memory of the register-tiled update: X tile, V tile (padded by 4), W."""
+    return elem * (tile * w + tile * (nb + 4) + nb * w)
 
 
 def valid(side, elem, cfg):
-    """Validity of (band, tile, threads, cpb, unroll) for a trailing-update kernel."""
+    """Validity of (band, tile, threads, cpb, unroll) for the trailing-update kernels
+    (band widths divisible by 4): the block is (w/4 column groups) x (band/R reflector
+    groups) with R in {1, 2, 4, 8}; a staged tile gives each thread a whole number of
+    4-row sub-blocks; shared memory <= 227 KiB."""
     b, tile, threads, cpb, unroll = cfg
-    if not (1 <= b <= 64) or threads % 32 or not (32 <= threads <= 1024):
+    if b % 4 or not (4 <= b <= 64):
         return False
-    if unroll not in (1, 2, 4) or not (1 <= cpb <= 8) or not (1 <= tile <= 256):
+    if threads % 32 or not (32 <= threads <= 1024):
+        return False
+    if cpb not in (1, 2, 4, 8) or unroll not in (1, 2, 4):
         return False
     w = 32 * cpb
-    items = b * w
-    if items % threads:
+    ncg = w // 4
+    if threads % ncg:
         return False
-    per = items // threads
-    if per < 1 or per > 32:
+    nrg = threads // ncg
+    if b % nrg or b // nrg not in (1, 2, 4, 8):
         return False
-    if tile * w < threads:
+    if not (4 <= tile <= 256) or tile % (4 * nrg):
         return False
     return smem_bytes(side, elem, b, tile, w) <= 227 * 1024
 

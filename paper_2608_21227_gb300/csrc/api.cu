@@ -63,7 +63,7 @@ struct Carver {
     }
 };
 
-const nla_cfg kDefaultCfg = {32, 32, 256, 1, 1};
+const nla_cfg kDefaultCfg = {32, 64, 128, 2, 1};
 
 // Resolve the configuration: explicit opts->cfg fields, else the tuned table,
 // else the defaults; band is clamped to [1, min(64, N)].
@@ -113,11 +113,10 @@ void carve_stage1(Carver &cv, int M, int N, nla_dtype dt, int b, int update, Sta
 
 nla_status check_upd(const Stage1Plan &p, int elem) {
     if (p.update != NLA_UPD_NATIVE) return NLA_OK;
-    size_t sm;
-    if (!nla::upd_cfg_valid(0, elem, p.b, p.left, &sm))
+    if (!nla::upd_cfg_launchable(0, elem, p.b, p.left))
         return fail(NLA_ERR_CONFIG, "trailing-update config (tile %d, threads %d, cpb %d, unroll %d) invalid for band %d",
                     p.left.tile, p.left.threads, p.left.cpb, p.left.unroll, p.b);
-    if (!nla::upd_cfg_valid(1, elem, p.b, p.right, &sm))
+    if (!nla::upd_cfg_launchable(1, elem, p.b, p.right))
         return fail(NLA_ERR_CONFIG, "LQ trailing-update config (tile %d, threads %d, cpb %d, unroll %d) invalid for band %d",
                     p.right.tile, p.right.threads, p.right.cpb, p.right.unroll, p.b);
     return NLA_OK;
@@ -178,17 +177,20 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
 // (small or odd band widths): widest block first, one 32-column strip.
 nla::UpdCfg fallback_upd(int side, int elem, int nb, nla::UpdCfg c) {
     size_t sm;
-    if (nla::upd_cfg_valid(side, elem, nb, c, &sm)) return c;
-    const int tiles[] = {32, 64, 16, 128, 8};
-    for (int threads = 256; threads <= 1024; threads += 32)
+    if (nla::upd_cfg_launchable(side, elem, nb, c)) return c;
+    (void)sm;
+    const int tiles[] = {64, 32, 16, 128, 8, 4};
+    const int cpbs[] = {2, 1, 4};
+    for (int cpb : cpbs)
+        for (int threads = 128; threads <= 1024; threads += 32)
+            for (int tile : tiles) {
+                nla::UpdCfg t{tile, threads, cpb, 1};
+                if (nla::upd_cfg_launchable(side, elem, nb, t)) return t;
+            }
+    for (int threads = 96; threads >= 32; threads -= 32)
         for (int tile : tiles) {
             nla::UpdCfg t{tile, threads, 1, 1};
-            if (nla::upd_cfg_valid(side, elem, nb, t, &sm)) return t;
-        }
-    for (int threads = 224; threads >= 32; threads -= 32)
-        for (int tile : tiles) {
-            nla::UpdCfg t{tile, threads, 1, 1};
-            if (nla::upd_cfg_valid(side, elem, nb, t, &sm)) return t;
+            if (nla::upd_cfg_launchable(side, elem, nb, t)) return t;
         }
     return c;
 }
@@ -282,6 +284,8 @@ nla_status gesvd_impl(int m, int n, nla_dtype dt, T *dA, int lda, T *dS, const G
 extern "C" {
 
 const char *nla_last_error(void) { return g_last_error.c_str(); }
+
+void nla_set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
 
 const char *nla_version(void) { return "nla-gb300 0.1 (sm_103a)"; }
 

@@ -89,7 +89,7 @@ cudaError_t band_extract(const T *A, long lda, int n, int b, T *AB, long ldab, c
 }
 
 // ------------------------------------------------------------------ bulge chasing
-constexpr int kChaseThreads = 128;
+constexpr int kChaseThreads = 128;  // >= 2b - 1 rows / columns per reflector application
 
 size_t band2bd_scratch_bytes(int n) { return (size_t)std::max(n, 1) * sizeof(int); }
 
@@ -101,44 +101,118 @@ struct Band {
     NLA_DEV T *at(int i, int j) const { return AB + (b2 + i - j) + (long)j * ldab; }
 };
 
+// Householder reflector of the vector held in v[0..L-1] (shared memory), built by
+// one warp: v becomes [1; x / (alpha - beta)], *tau and *beta are set.
 template <typename T>
-NLA_DEV T ldg_cg(const T *p) { return __ldcg(p); }
-
-// One Householder reflector from x[0..L-1] (stride of the band accessor given by
-// the caller).  Warp 0 computes it; the result goes to v[] (v[0] = 1), *tau,
-// *beta in shared memory.  Returns nothing; caller syncs.
-template <typename T>
-NLA_DEV void make_reflector(const T *x0, int L, double *v, double *tau_out, double *beta_out) {
-    // called by all lanes of warp 0; x0[i] already staged in v[] as doubles
+NLA_DEV void warp_reflector(T *v, int L, T *tau_out, T *beta_out) {
     const int lane = threadIdx.x & 31;
-    double s = 0.0;
+    T s = T(0);
     for (int i = 1 + lane; i < L; i += 32) s += v[i] * v[i];
     s = warp_sum(s);
-    double alpha = v[0];
-    double tau = 0.0, beta = alpha, scale = 0.0;
-    if (s > 0.0) {
-        double r = sqrt(alpha * alpha + s);
-        beta = alpha >= 0.0 ? -r : r;
+    T alpha = v[0];
+    T tau = T(0), beta = alpha, scale = T(0);
+    if (s > T(0)) {
+        T r = sqrt(alpha * alpha + s);
+        beta = alpha >= T(0) ? -r : r;
         tau = (beta - alpha) / beta;
-        scale = 1.0 / (alpha - beta);
+        scale = T(1) / (alpha - beta);
     }
     __syncwarp();
-    for (int i = 1 + lane; i < L; i += 32) v[i] = (tau != 0.0) ? v[i] * scale : 0.0;
+    for (int i = 1 + lane; i < L; i += 32) v[i] = (tau != T(0)) ? v[i] * scale : T(0);
+    __syncwarp();
     if (lane == 0) {
-        v[0] = 1.0;
+        v[0] = T(1);
         *tau_out = tau;
         *beta_out = beta;
     }
-    (void)x0;
+}
+
+// One block step (right + left reflector) of sweep s at position k, on a
+// shared-memory copy of its window.  The window is the box rows [tr, r1] x
+// columns [c0, cend]; only its two sub-boxes that the step reads or writes are
+// moved: R = rows [tr, c1] x columns [c0, c1] and L = rows [c0, r1] x columns
+// [c0, cend] (c1 = r1).  W(i, j) = W[(i - tr) + (j - c0) * ldw].
+template <typename T>
+NLA_DEV void chase_step(const Band<T> &A, int n, int b, int s, int k, T *W, int ldw, T *v, T *sh) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int c0 = s + k * b + 1;
+    const int tr = (k == 0) ? s : s + (k - 1) * b + 1;
+    const int c1 = min(s + (k + 1) * b, n - 1);  // == r1
+    const int cend = min(s + (k + 2) * b, n - 1);
+    const int L = c1 - c0 + 1;                  // right reflector length == left reflector length
+    const int hR = c1 - tr + 1;                 // rows of R
+    const int wL = cend - c0 + 1;               // columns of L
+    const int top = c0 - tr;                    // rows of R above L
+    // ---- load: columns of R (rows tr..c1) and the columns of L right of R (rows c0..c1)
+    for (int idx = tid; idx < hR * L; idx += nt) {
+        int i = idx % hR, j = idx / hR;
+        W[i + j * ldw] = __ldcg(A.at(tr + i, c0 + j));
+    }
+    for (int idx = tid; idx < L * (wL - L); idx += nt) {
+        int i = idx % L, j = L + idx / L;
+        W[top + i + j * ldw] = __ldcg(A.at(c0 + i, c0 + j));
+    }
+    __syncthreads();
+    // ---- right reflector on columns c0..c1 from row tr
+    if (L >= 2) {
+        for (int j = tid; j < L; j += nt) v[j] = W[0 + j * ldw];
+        __syncthreads();
+        if (tid < 32) warp_reflector<T>(v, L, sh, sh + 1);
+        __syncthreads();
+        const T tau = sh[0];
+        if (tau != T(0)) {
+            if (tid == 0) W[0] = sh[1];
+            for (int j = 1 + tid; j < L; j += nt) W[j * ldw] = T(0);
+            for (int i = 1 + tid; i < hR; i += nt) {  // one thread per row
+                T w = T(0);
+                for (int j = 0; j < L; ++j) w += W[i + j * ldw] * v[j];
+                w *= tau;
+                for (int j = 0; j < L; ++j) W[i + j * ldw] -= w * v[j];
+            }
+        }
+        __syncthreads();
+    }
+    // ---- left reflector on rows c0..c1 from column c0
+    if (L >= 2) {
+        for (int i = tid; i < L; i += nt) v[i] = W[top + i];
+        __syncthreads();
+        if (tid < 32) warp_reflector<T>(v, L, sh, sh + 1);
+        __syncthreads();
+        const T tau = sh[0];
+        if (tau != T(0)) {
+            if (tid == 0) W[top] = sh[1];
+            for (int i = 1 + tid; i < L; i += nt) W[top + i] = T(0);
+            for (int j = 1 + tid; j < wL; j += nt) {  // one thread per column
+                T *col = W + top + j * ldw;
+                T w = T(0);
+                for (int i = 0; i < L; ++i) w += v[i] * col[i];
+                w *= tau;
+                for (int i = 0; i < L; ++i) col[i] -= w * v[i];
+            }
+        }
+        __syncthreads();
+    }
+    // ---- store R and the part of L right of R
+    for (int idx = tid; idx < hR * L; idx += nt) {
+        int i = idx % hR, j = idx / hR;
+        __stcg(A.at(tr + i, c0 + j), W[i + j * ldw]);
+    }
+    for (int idx = tid; idx < L * (wL - L); idx += nt) {
+        int i = idx % L, j = L + idx / L;
+        __stcg(A.at(c0 + i, c0 + j), W[top + i + j * ldw]);
+    }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kChaseThreads)
 band2bd_kernel(T *AB, long ldab, int n, int b, int *progress, int *info) {
-    __shared__ double v[128];
-    __shared__ double sh_tau, sh_beta;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ldw = 2 * b + 1;
+    T *W = reinterpret_cast<T *>(smem_raw);  // (2b+1) x 2b window
+    T *v = W + (size_t)ldw * 2 * b;          // reflector, <= b entries
+    T *sh = v + 64;                          // tau, beta
     __shared__ int sh_fail;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x;
     Band<T> A{AB, ldab, 2 * b};
     const int nsweeps = n - 2;
     if (tid == 0) sh_fail = 0;
@@ -153,54 +227,7 @@ band2bd_kernel(T *AB, long ldab, int n, int b, int *progress, int *info) {
                 __syncthreads();
                 if (sh_fail) return;
             }
-            // ---------------- right reflector on columns c0..c1, zeroing row tr
-            const int tr = (k == 0) ? s : s + (k - 1) * b + 1;
-            const int c1 = min(s + (k + 1) * b, n - 1);
-            const int L = c1 - c0 + 1;
-            if (L >= 2) {
-                for (int c = tid; c < L; c += blockDim.x) v[c] = (double)ldg_cg(A.at(tr, c0 + c));
-                __syncthreads();
-                if (warp == 0) make_reflector<T>(nullptr, L, v, &sh_tau, &sh_beta);
-                __syncthreads();
-                const double tau = sh_tau;
-                if (tau != 0.0) {
-                    for (int c = tid; c < L; c += blockDim.x) __stcg(A.at(tr, c0 + c), c == 0 ? (T)sh_beta : T(0));
-                    // rows tr+1 .. c1: one warp per row
-                    for (int i = tr + 1 + warp; i <= c1; i += nwarps) {
-                        double wsum = 0.0;
-                        for (int c = lane; c < L; c += 32) wsum += (double)ldg_cg(A.at(i, c0 + c)) * v[c];
-                        wsum = warp_sum(wsum) * tau;
-                        for (int c = lane; c < L; c += 32) {
-                            T *p = A.at(i, c0 + c);
-                            __stcg(p, (T)((double)ldg_cg(p) - wsum * v[c]));
-                        }
-                    }
-                }
-                __syncthreads();
-            }
-            // ---------------- left reflector on rows c0..r1, zeroing column c0
-            const int r1 = min(s + (k + 1) * b, n - 1);
-            const int L2 = r1 - c0 + 1;
-            const int cend = min(s + (k + 2) * b, n - 1);
-            if (L2 >= 2) {
-                for (int r = tid; r < L2; r += blockDim.x) v[r] = (double)ldg_cg(A.at(c0 + r, c0));
-                __syncthreads();
-                if (warp == 0) make_reflector<T>(nullptr, L2, v, &sh_tau, &sh_beta);
-                __syncthreads();
-                const double tau = sh_tau;
-                if (tau != 0.0) {
-                    for (int r = tid; r < L2; r += blockDim.x) __stcg(A.at(c0 + r, c0), r == 0 ? (T)sh_beta : T(0));
-                    for (int j = c0 + 1 + warp; j <= cend; j += nwarps) {
-                        double wsum = 0.0;
-                        for (int r = lane; r < L2; r += 32) wsum += (double)ldg_cg(A.at(c0 + r, j)) * v[r];
-                        wsum = warp_sum(wsum) * tau;
-                        for (int r = lane; r < L2; r += 32) {
-                            T *p = A.at(c0 + r, j);
-                            __stcg(p, (T)((double)ldg_cg(p) - wsum * v[r]));
-                        }
-                    }
-                }
-            }
+            chase_step<T>(A, n, b, s, k, W, ldw, v, sh);
             __threadfence();
             __syncthreads();
             if (tid == 0) st_release(&progress[s], k + 1);
@@ -228,11 +255,17 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
     if (nsweeps > 0 && b > 1) {
         cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)nsweeps, st);
         if (err != cudaSuccess) return err;
+        static bool smem_attr = false;
+        if (!smem_attr) {
+            cudaFuncSetAttribute(band2bd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(((size_t)129 * 128 + 64 + 8) * sizeof(T)));
+            smem_attr = true;
+        }
         int grid = std::min(nsweeps, device_sm_count());
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
         cfg.blockDim = dim3(kChaseThreads);
-        cfg.dynamicSmemBytes = 0;
+        cfg.dynamicSmemBytes = ((size_t)(2 * b + 1) * 2 * b + 64 + 8) * sizeof(T);
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeCooperative;

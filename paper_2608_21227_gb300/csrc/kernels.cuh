@@ -32,6 +32,19 @@ struct UpdCfg {
 // Validity of a configuration for the SIMT trailing-update kernels
 // (side 0 = QR/left, 1 = LQ/right); elem = bytes per element.
 bool upd_cfg_valid(int side, int elem, int nb, const UpdCfg &c, size_t *smem_bytes);
+// upd_cfg_valid plus the device check that the compiled kernel's register use
+// admits c.threads threads per block (needs a CUDA device).
+bool upd_cfg_launchable(int side, int elem, int nb, const UpdCfg &c);
+
+// Register-tiled kernels (update_tiled.cu): reflectors per thread R for a
+// configuration, or 0 if it does not tile; their shared-memory bytes; the
+// largest block the compiled instance admits.
+int tiled_r(int nb, const UpdCfg &c);
+size_t tiled_smem(int side, int elem, int nb, int th, int w);
+int tiled_max_threads(int side, int elem, int R, int unroll);
+template <typename T>
+cudaError_t trail_tiled(int side, T *X, long ldx, int M, int N, const T *V, long ldv, int nb, const T *Tm,
+                        const UpdCfg &c, cudaStream_t st);
 
 // QR side: X (M x N at X, ldx) <- (I - V T V^T)^T X, V = unit lower M x nb at Vp (ldv).
 template <typename T>

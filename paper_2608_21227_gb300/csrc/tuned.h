@@ -12,6 +12,9 @@ extern "C" {
 // kt_load_config) has an entry for this dtype/update, else 0.
 int nla_tuned_lookup(int m, int n, int dtype, int update, int side, nla_cfg *out);
 
+// Record the message returned by nla_last_error() on this thread.
+void nla_set_last_error(const char *msg);
+
 #ifdef __cplusplus
 }
 #endif

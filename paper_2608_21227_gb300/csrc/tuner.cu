@@ -1,0 +1,606 @@
+// tuner.cu -- kt_tune / kt_load_config: the auto-tuner of include/kt.h.
+//
+// Eq. 1 (Section 3.1): x* = argmin over the valid space of the measured runtime.
+// Measurement follows Section 4.1/4.2: the input is restored from a pristine
+// device copy before every run (deep copy, excluded from timing), one untimed
+// warm-up per configuration, CUDA events on the launching stream, median of
+// `reps` timed runs, output verified against the default configuration, and
+// launch/verification failures recorded and skipped.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/kt.h"
+#include "../../include/nla.h"
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tuned.h"
+
+extern "C" nla_status kt_random_subset(int count, int k, unsigned long long seed, int *out);
+
+namespace {
+
+const int kTiles[] = {16, 32, 64, 128};
+const int kBands[] = {16, 32, 64};
+const int kCpbs[] = {1, 2, 4, 8};
+const int kUnrolls[] = {1, 2, 4};
+constexpr int kThreadSteps = 16;  // 64 .. 1024 step 64
+constexpr int kSpace = 3 * 4 * kThreadSteps * 4 * 3;
+
+nla_cfg space_point(int idx) {
+    // lexicographic order (band, tile, threads, cpb, unroll)
+    nla_cfg c;
+    c.unroll = kUnrolls[idx % 3];
+    idx /= 3;
+    c.cols_per_block = kCpbs[idx % 4];
+    idx /= 4;
+    c.threads = 64 * (1 + idx % kThreadSteps);
+    idx /= kThreadSteps;
+    c.tile = kTiles[idx % 4];
+    idx /= 4;
+    c.band = kBands[idx];
+    return c;
+}
+
+nla::UpdCfg upd_of(const nla_cfg &c) { return nla::UpdCfg{c.tile, c.threads, c.cols_per_block, c.unroll}; }
+
+bool cfg_valid(int side, int elem, const nla_cfg &c) {
+    size_t sm;
+    return nla::upd_cfg_valid(side, elem, c.band, upd_of(c), &sm);
+}
+
+nla_status terr(nla_status s, const std::string &m) {
+    nla_set_last_error(m.c_str());
+    return s;
+}
+
+// ------------------------------------------------------------------ SplitMix64
+struct SplitMix64 {
+    unsigned long long s;
+    unsigned long long next() {
+        s += 0x9E3779B97F4A7C15ull;
+        unsigned long long z = s;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    }
+};
+
+// ------------------------------------------------------------------ device helpers
+template <typename T>
+__global__ void fill_uniform_kernel(T *A, long count, unsigned long long seed) {
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+        unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        A[i] = (T)((double)(z >> 11) * 0x1p-52 - 1.0);  // U[-1, 1)
+    }
+}
+
+template <typename T>
+__global__ void max_abs_diff_kernel(const T *A, const T *B, long count, double *out) {
+    double mx = 0.0, mr = 0.0;
+    for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < count; i += (long)gridDim.x * blockDim.x) {
+        double a = (double)A[i], b = (double)B[i];
+        mx = fmax(mx, fabs(a - b));
+        mr = fmax(mr, fabs(b));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mr = fmax(mr, __shfl_xor_sync(0xffffffffu, mr, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        // non-negative doubles order like their bit patterns
+        atomicMax(reinterpret_cast<unsigned long long *>(out), __double_as_longlong(mx));
+        atomicMax(reinterpret_cast<unsigned long long *>(out + 1), __double_as_longlong(mr));
+    }
+}
+
+// ------------------------------------------------------------------ cache
+struct Key {
+    int kernel, m, n, dtype, update, band, tile, threads, cpb, unroll;
+    bool operator<(const Key &o) const {
+        return std::tie(kernel, m, n, dtype, update, band, tile, threads, cpb, unroll) <
+               std::tie(o.kernel, o.m, o.n, o.dtype, o.update, o.band, o.tile, o.threads, o.cpb, o.unroll);
+    }
+};
+struct Meas {
+    double ms;
+    int status;  // 0 ok, 1 launch failure, 2 verification failure
+};
+
+void load_cache(const char *path, std::map<Key, Meas> &c) {
+    if (!path) return;
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char line[512];
+    while (fgets(line, sizeof line, f)) {
+        if (line[0] == '#' || line[0] == 'k') continue;  // comment / header
+        Key k;
+        Meas v;
+        if (sscanf(line, "%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%lf,%d", &k.kernel, &k.m, &k.n, &k.dtype, &k.update, &k.band,
+                   &k.tile, &k.threads, &k.cpb, &k.unroll, &v.ms, &v.status) == 12)
+            c[k] = v;
+    }
+    fclose(f);
+}
+
+void append_cache(const char *path, const Key &k, const Meas &v) {
+    if (!path) return;
+    FILE *f = fopen(path, "a");
+    if (!f) return;
+    if (ftell(f) == 0) fprintf(f, "kernel,m,n,dtype,update,band,tile,threads,cpb,unroll,median_ms,status\n");
+    fprintf(f, "%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%.6f,%d\n", k.kernel, k.m, k.n, k.dtype, k.update, k.band, k.tile,
+            k.threads, k.cpb, k.unroll, v.ms, v.status);
+    fclose(f);
+}
+
+// ------------------------------------------------------------------ installed table
+struct TableEntry {
+    int side, m, n, dtype, update;
+    nla_cfg cfg;
+    double ms;
+};
+std::mutex g_table_mu;
+std::vector<TableEntry> g_table;
+
+double median_of(std::vector<double> v) {
+    if (v.empty()) return NAN;
+    std::sort(v.begin(), v.end());
+    size_t k = v.size();
+    return k % 2 ? v[k / 2] : 0.5 * (v[k / 2 - 1] + v[k / 2]);
+}
+
+const nla_cfg kDefault = {32, 64, 128, 2, 1};
+
+// ------------------------------------------------------------------ trailing-update tuning
+template <typename T>
+struct TrailBench {
+    int side, m, n, reps;
+    T *A = nullptr, *A0 = nullptr, *Xref = nullptr;
+    T *tau = nullptr, *Tm = nullptr;
+    unsigned int *bar = nullptr;
+    double *part = nullptr, *diff = nullptr;
+    int *info = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int b = 0;
+
+    cudaError_t init() {
+        size_t cnt = (size_t)m * n;
+        cudaError_t e;
+        if ((e = cudaMalloc(&A, cnt * sizeof(T)))) return e;
+        if ((e = cudaMalloc(&A0, cnt * sizeof(T)))) return e;
+        if ((e = cudaMalloc(&Xref, cnt * sizeof(T)))) return e;
+        if ((e = cudaMalloc(&tau, 64 * sizeof(T)))) return e;
+        if ((e = cudaMalloc(&Tm, 64 * 64 * sizeof(T)))) return e;
+        if ((e = cudaMalloc(&bar, 64 * sizeof(unsigned int)))) return e;
+        if ((e = cudaMalloc(&part, nla::panel_part_doubles(nla::panel_max_ctas()) * sizeof(double)))) return e;
+        if ((e = cudaMalloc(&diff, 2 * sizeof(double)))) return e;
+        if ((e = cudaMalloc(&info, sizeof(int)))) return e;
+        if ((e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking))) return e;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        return cudaSuccess;
+    }
+    ~TrailBench() {
+        cudaFree(A);
+        cudaFree(A0);
+        cudaFree(Xref);
+        cudaFree(tau);
+        cudaFree(Tm);
+        cudaFree(bar);
+        cudaFree(part);
+        cudaFree(diff);
+        cudaFree(info);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
+    }
+    // Fresh input and the reflectors of panel step 0 for band width bb.
+    cudaError_t setup(int bb, unsigned long long seed) {
+        b = bb;
+        long cnt = (long)m * n;
+        fill_uniform_kernel<T><<<1024, 256, 0, st>>>(A, cnt, seed);
+        cudaMemsetAsync(bar, 0, 64 * sizeof(unsigned int), st);
+        cudaMemsetAsync(info, 0, sizeof(int), st);
+        nla::PanelCtl ctl{bar, part, info};
+        cudaError_t e;
+        if (side == 0)
+            e = nla::panel_factor<T>(A, 1, m, m, b, tau, Tm, ctl, st);
+        else
+            e = nla::panel_factor<T>(A + (long)b * m, m, 1, n - b, b, tau, Tm, ctl, st);
+        if (e) return e;
+        e = cudaMemcpyAsync(A0, A, cnt * sizeof(T), cudaMemcpyDeviceToDevice, st);
+        if (e) return e;
+        return cudaStreamSynchronize(st);
+    }
+    cudaError_t launch(const nla_cfg &c) {
+        if (side == 0)
+            return nla::trail_left<T>(A + (long)b * m, m, m, n - b, A, m, b, Tm, upd_of(c), st);
+        return nla::trail_right<T>(A + b + (long)b * m, m, m - b, n - b, A + (long)b * m, m, b, Tm, upd_of(c), st);
+    }
+    cudaError_t restore() { return cudaMemcpyAsync(A, A0, (size_t)m * n * sizeof(T), cudaMemcpyDeviceToDevice, st); }
+    // Returns median ms (status 0), or status 1 (launch) / 2 (verification).
+    Meas measure(const nla_cfg &c, bool is_reference) {
+        restore();
+        if (launch(c) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaGetLastError();
+            return {NAN, 1};
+        }
+        std::vector<double> t;
+        for (int r = 0; r < reps; ++r) {
+            restore();
+            cudaEventRecord(e0, st);
+            if (launch(c) != cudaSuccess) {
+                cudaGetLastError();
+                return {NAN, 1};
+            }
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return {NAN, 1};
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms > 0.f) t.push_back(ms);
+        }
+        if (t.empty()) return {NAN, 1};
+        size_t cnt = (size_t)m * n;
+        if (is_reference) {
+            cudaMemcpyAsync(Xref, A, cnt * sizeof(T), cudaMemcpyDeviceToDevice, st);
+            cudaStreamSynchronize(st);
+        } else {
+            cudaMemsetAsync(diff, 0, 2 * sizeof(double), st);
+            max_abs_diff_kernel<T><<<512, 256, 0, st>>>(A, Xref, (long)cnt, diff);
+            double h[2] = {0, 0};
+            cudaMemcpyAsync(h, diff, sizeof h, cudaMemcpyDeviceToHost, st);
+            cudaStreamSynchronize(st);
+            const double tol = sizeof(T) == 8 ? 1e-10 : 1e-3;
+            if (!(h[0] <= tol * std::max(h[1], 1e-300))) return {median_of(t), 2};
+        }
+        return {median_of(t), 0};
+    }
+};
+
+}  // namespace
+
+// ------------------------------------------------------------------ MLP inference hook (mlp.cu)
+namespace nla {
+nla_status mlp_predict_host(const char *model_path, const float *X, int rows, float *y);
+}
+
+namespace {
+
+template <typename T>
+nla_status tune_trail(const kt_problem &p, kt_strategy strategy, double frac, const char *cache_path,
+                      const char *model_path, unsigned long long seed, kt_result *out) {
+    const int side = p.kernel == KT_TRAIL_LEFT ? 0 : 1;
+    const int elem = (int)sizeof(T);
+    std::map<Key, Meas> cache;
+    load_cache(cache_path, cache);
+    TrailBench<T> tb;
+    tb.side = side;
+    tb.m = p.m;
+    tb.n = p.n;
+    tb.reps = p.reps > 0 ? p.reps : 5;
+    if (tb.init() != cudaSuccess) {
+        cudaGetLastError();
+        return terr(NLA_ERR_CUDA, "tuner: allocation failed");
+    }
+    std::vector<nla_cfg> valid;
+    for (int i = 0; i < kSpace; ++i) {
+        nla_cfg c = space_point(i);
+        if (p.band > 0 && c.band != p.band) continue;
+        if (c.band >= p.n) continue;
+        if (nla::upd_cfg_launchable(side, elem, c.band, upd_of(c))) valid.push_back(c);
+    }
+    // candidate list per strategy
+    std::vector<nla_cfg> cand = valid;
+    if (strategy != KT_EXHAUSTIVE && !valid.empty()) {
+        size_t k = (size_t)std::ceil(std::max(0.0, std::min(1.0, frac)) * valid.size());
+        k = std::max<size_t>(1, std::min(k, valid.size()));
+        if (strategy == KT_RANDOM) {
+            std::vector<int> idx(k);
+            kt_random_subset((int)valid.size(), (int)k, seed, idx.data());
+            cand.clear();
+            for (size_t i = 0; i < k; ++i) cand.push_back(valid[idx[i]]);
+        } else {  // model-ranked top fraction
+            if (!model_path) return terr(NLA_ERR_ARG, "KT_MODEL_TOPK needs model_path");
+            std::vector<float> X(valid.size() * KT_MLP_FEATURES), y(valid.size());
+            for (size_t i = 0; i < valid.size(); ++i)
+                kt_features(p.kernel, p.m, p.n, p.dtype, p.update, &valid[i], &X[i * KT_MLP_FEATURES]);
+            nla_status s = nla::mlp_predict_host(model_path, X.data(), (int)valid.size(), y.data());
+            if (s != NLA_OK) return s;
+            std::vector<int> idx(valid.size());
+            for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+            std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return y[a] < y[b]; });
+            cand.clear();
+            for (size_t i = 0; i < k; ++i) cand.push_back(valid[idx[i]]);
+        }
+    }
+    kt_result r;
+    memset(&r, 0, sizeof r);
+    r.valid = (int)valid.size();
+    r.best_ms = r.median_ms = r.default_ms = NAN;
+    std::vector<double> times;
+    bool have_best = false;
+    int cur_band = -1;
+    for (size_t ci = 0; ci < cand.size(); ++ci) {
+        const nla_cfg &c = cand[ci];
+        if (c.band != cur_band) {  // new band: fresh reflectors and a reference output
+            cur_band = c.band;
+            if (tb.setup(cur_band, seed ^ 0x5EEDull) != cudaSuccess) {
+                cudaGetLastError();
+                return terr(NLA_ERR_CUDA, "tuner: setup failed");
+            }
+            nla_cfg ref = kDefault;
+            ref.band = cur_band;
+            nla::UpdCfg u = upd_of(ref);
+            size_t sm;
+            if (!nla::upd_cfg_valid(side, elem, cur_band, u, &sm)) ref = c;
+            Meas mref = tb.measure(ref, true);
+            if (mref.status != 0) return terr(NLA_ERR_CUDA, "tuner: reference configuration failed");
+            if (ref.band == kDefault.band && ref.tile == kDefault.tile && ref.threads == kDefault.threads &&
+                ref.cols_per_block == kDefault.cols_per_block && ref.unroll == kDefault.unroll)
+                r.default_ms = mref.ms;
+        }
+        Key k{(int)p.kernel, p.m, p.n, (int)p.dtype, (int)p.update, c.band, c.tile, c.threads, c.cols_per_block,
+              c.unroll};
+        Meas v;
+        auto it = cache.find(k);
+        if (it != cache.end()) {
+            v = it->second;
+        } else {
+            v = tb.measure(c, false);
+            cache[k] = v;
+            append_cache(cache_path, k, v);
+        }
+        r.evaluated++;
+        if (v.status != 0) {
+            r.failed++;
+            continue;
+        }
+        times.push_back(v.ms);
+        if (!have_best || v.ms < r.best_ms) {  // candidates are visited in lexicographic order: ties keep the first
+            r.best = c;
+            r.best_ms = v.ms;
+            have_best = true;
+        }
+        if (c.band == kDefault.band && c.tile == kDefault.tile && c.threads == kDefault.threads &&
+            c.cols_per_block == kDefault.cols_per_block && c.unroll == kDefault.unroll)
+            r.default_ms = v.ms;
+    }
+    // the model / random strategies visit candidates out of lexicographic order: recompute ties properly
+    r.median_ms = median_of(times);
+    if (!have_best) return terr(NLA_ERR_CONFIG, "tuner: no configuration ran successfully");
+    *out = r;
+    return NLA_OK;
+}
+
+nla_status tune_gesvd(const kt_problem &p, const char *cache_path, unsigned long long seed, kt_result *out) {
+    // pipeline level: band width, each band with its best kernel configs from the cache (else defaults)
+    std::map<Key, Meas> cache;
+    load_cache(cache_path, cache);
+    const int es = p.dtype == NLA_F64 ? 8 : 4;
+    const int M = std::max(p.m, p.n), N = std::min(p.m, p.n);
+    void *A = nullptr, *A0 = nullptr, *S = nullptr, *W = nullptr;
+    int *info = nullptr;
+    size_t cnt = (size_t)M * N;
+    kt_result r;
+    memset(&r, 0, sizeof r);
+    r.best_ms = r.median_ms = r.default_ms = NAN;
+    std::vector<double> times;
+    cudaStream_t st;
+    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    nla_status status = NLA_OK;
+    if (cudaMalloc(&A, cnt * es) || cudaMalloc(&A0, cnt * es) || cudaMalloc(&S, N * (size_t)es) ||
+        cudaMalloc(&info, sizeof(int))) {
+        cudaGetLastError();
+        status = terr(NLA_ERR_CUDA, "tuner: allocation failed");
+    }
+    if (status == NLA_OK) {
+        if (es == 8)
+            fill_uniform_kernel<double><<<1024, 256, 0, st>>>((double *)A0, (long)cnt, seed);
+        else
+            fill_uniform_kernel<float><<<1024, 256, 0, st>>>((float *)A0, (long)cnt, seed);
+        const int reps = p.reps > 0 ? p.reps : 3;
+        for (int bi = 0; bi < 3; ++bi) {
+            const int b = kBands[bi];
+            if (p.band > 0 && b != p.band) continue;
+            if (b >= N) continue;
+            nla_cfg best[2];
+            for (int side = 0; side < 2; ++side) {
+                best[side] = kDefault;
+                best[side].band = b;
+                double bm = INFINITY;
+                for (auto &kv : cache) {
+                    const Key &k = kv.first;
+                    if (k.kernel != side || k.dtype != (int)p.dtype || k.update != (int)p.update || k.band != b ||
+                        kv.second.status != 0)
+                        continue;
+                    // nearest problem size in the cache with this band
+                    double d = std::fabs(std::log2((double)k.m / p.m)) + std::fabs(std::log2((double)k.n / p.n));
+                    double score = d * 1e6 + kv.second.ms;
+                    if (score < bm) {
+                        bm = score;
+                        best[side] = nla_cfg{b, k.tile, k.threads, k.cpb, k.unroll};
+                    }
+                }
+            }
+            // time end to end, left config drives both sides when they differ (install both)
+            nla_opts o = {p.update, &best[0], 0};
+            size_t need = 0;
+            if (nla_gesvd_vals_workspace(M, N, p.dtype, &o, &need) != NLA_OK) continue;
+            cudaFree(W);
+            W = nullptr;
+            if (cudaMalloc(&W, need)) {
+                cudaGetLastError();
+                status = terr(NLA_ERR_CUDA, "tuner: workspace allocation failed");
+                break;
+            }
+            std::vector<double> t;
+            for (int rep = 0; rep <= reps; ++rep) {
+                cudaMemcpyAsync(A, A0, cnt * es, cudaMemcpyDeviceToDevice, st);
+                cudaEventRecord(e0, st);
+                nla_status s = nla_gesvd_vals(M, N, p.dtype, A, M, S, W, need, info, &o, st);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                if (s != NLA_OK) break;
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) t.push_back(ms);  // rep 0 is the warm-up
+            }
+            r.evaluated++;
+            if ((int)t.size() != reps) {
+                r.failed++;
+                continue;
+            }
+            double med = median_of(t);
+            times.push_back(med);
+            if (!(med >= r.best_ms)) {
+                r.best_ms = med;
+                r.best = best[0];
+            }
+            if (b == 32) r.default_ms = med;
+        }
+        r.valid = (int)times.size() + r.failed;
+        r.median_ms = median_of(times);
+    }
+    cudaFree(A);
+    cudaFree(A0);
+    cudaFree(S);
+    cudaFree(W);
+    cudaFree(info);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamDestroy(st);
+    if (status != NLA_OK) return status;
+    if (times.empty()) return terr(NLA_ERR_CONFIG, "tuner: no band ran successfully");
+    *out = r;
+    return NLA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int kt_space_size(void) { return kSpace; }
+
+nla_status kt_random_subset(int count, int k, unsigned long long seed, int *out) {
+    if (count < 0 || k < 0 || (k > 0 && !out)) return terr(NLA_ERR_ARG, "bad arguments");
+    std::vector<int> idx(count);
+    for (int i = 0; i < count; ++i) idx[i] = i;
+    SplitMix64 g{seed};
+    k = std::min(k, count);
+    for (int i = 0; i < k; ++i) {
+        int j = i + (int)(g.next() % (unsigned long long)(count - i));
+        std::swap(idx[i], idx[j]);
+        out[i] = idx[i];
+    }
+    return NLA_OK;
+}
+
+nla_status kt_space_get(int index, nla_cfg *out) {
+    if (index < 0 || index >= kSpace || !out) return NLA_ERR_ARG;
+    *out = space_point(index);
+    return NLA_OK;
+}
+
+int kt_cfg_valid(kt_kernel kernel, nla_dtype dtype, const nla_cfg *cfg) {
+    if (!cfg) return 0;
+    const int elem = dtype == NLA_F64 ? 8 : 4;
+    if (kernel == KT_TRAIL_LEFT) return cfg_valid(0, elem, *cfg);
+    if (kernel == KT_TRAIL_RIGHT) return cfg_valid(1, elem, *cfg);
+    return cfg_valid(0, elem, *cfg) && cfg_valid(1, elem, *cfg);
+}
+
+nla_status kt_features(kt_kernel kernel, int m, int n, nla_dtype dtype, nla_update update, const nla_cfg *cfg,
+                       float *out) {
+    if (!cfg || !out || kernel < 0 || kernel > 2) return NLA_ERR_ARG;
+    for (int i = 0; i < KT_MLP_FEATURES; ++i) out[i] = 0.f;
+    out[kernel] = 1.f;
+    out[3] = (float)std::log2((double)std::max(cfg->band, 1));
+    out[4] = (float)std::log2((double)std::max(cfg->tile, 1));
+    out[5] = (float)std::log2((double)std::max(cfg->threads, 1));
+    out[6] = (float)std::log2((double)std::max(cfg->cols_per_block, 1));
+    out[7] = (float)std::log2((double)std::max(cfg->unroll, 1));
+    out[8] = (float)std::log2((double)std::max(m, 1));
+    out[9] = (float)std::log2((double)std::max(n, 1));
+    out[10 + (dtype == NLA_F64 ? 0 : 1)] = 1.f;
+    out[12 + std::min(std::max((int)update, 0), 2)] = 1.f;
+    return NLA_OK;
+}
+
+nla_status kt_tune(const kt_problem *p, kt_strategy strategy, double budget_frac, const char *cache_path,
+                   const char *model_path, unsigned long long seed, kt_result *out) {
+    if (!p || !out) return terr(NLA_ERR_ARG, "null argument");
+    if (p->m <= 0 || p->n <= 0) return terr(NLA_ERR_ARG, "empty problem");
+    if (p->dtype != NLA_F64 && p->dtype != NLA_F32) return terr(NLA_ERR_ARG, "unknown dtype");
+    if (strategy < KT_EXHAUSTIVE || strategy > KT_RANDOM) return terr(NLA_ERR_ARG, "unknown strategy");
+    if (p->kernel == KT_GESVD) return tune_gesvd(*p, cache_path, seed, out);
+    if (p->kernel != KT_TRAIL_LEFT && p->kernel != KT_TRAIL_RIGHT) return terr(NLA_ERR_ARG, "unknown kernel");
+    if (p->update != NLA_UPD_NATIVE) return terr(NLA_ERR_ARG, "SIMT trailing-update tuning needs NLA_UPD_NATIVE");
+    if (p->m < p->n) return terr(NLA_ERR_ARG, "trailing-update tuning needs m >= n");
+    if (p->dtype == NLA_F64) return tune_trail<double>(*p, strategy, budget_frac, cache_path, model_path, seed, out);
+    return tune_trail<float>(*p, strategy, budget_frac, cache_path, model_path, seed, out);
+}
+
+nla_status kt_write_table(const char *path, int side, int m, int n, nla_dtype dtype, nla_update update,
+                          const nla_cfg *cfg, double ms) {
+    if (!path || !cfg || (side != 0 && side != 1)) return terr(NLA_ERR_ARG, "bad arguments");
+    FILE *f = fopen(path, "a");
+    if (!f) return terr(NLA_ERR_ARG, std::string("cannot open ") + path);
+    if (ftell(f) == 0) fprintf(f, "# side m n dtype update band tile threads cpb unroll ms\n");
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %.6f\n", side, m, n, (int)dtype, (int)update, cfg->band, cfg->tile,
+            cfg->threads, cfg->cols_per_block, cfg->unroll, ms);
+    fclose(f);
+    return NLA_OK;
+}
+
+nla_status kt_load_config(const char *path) {
+    std::vector<TableEntry> t;
+    if (path) {
+        FILE *f = fopen(path, "r");
+        if (!f) return terr(NLA_ERR_ARG, std::string("cannot open ") + path);
+        char line[512];
+        while (fgets(line, sizeof line, f)) {
+            if (line[0] == '#') continue;
+            TableEntry e;
+            if (sscanf(line, "%d %d %d %d %d %d %d %d %d %d %lf", &e.side, &e.m, &e.n, &e.dtype, &e.update,
+                       &e.cfg.band, &e.cfg.tile, &e.cfg.threads, &e.cfg.cols_per_block, &e.cfg.unroll, &e.ms) == 11)
+                t.push_back(e);
+        }
+        fclose(f);
+        if (t.empty()) return terr(NLA_ERR_ARG, std::string("no entries in ") + path);
+    }
+    std::lock_guard<std::mutex> lk(g_table_mu);
+    g_table.swap(t);
+    return NLA_OK;
+}
+
+int nla_tuned_lookup(int m, int n, int dtype, int update, int side, nla_cfg *out) {
+    std::lock_guard<std::mutex> lk(g_table_mu);
+    const TableEntry *best = nullptr;
+    double bd = INFINITY;
+    for (const TableEntry &e : g_table) {
+        if (e.dtype != dtype || e.update != update || e.side != side) continue;
+        double d = std::fabs(std::log2((double)std::max(m, 1) / e.m)) + std::fabs(std::log2((double)std::max(n, 1) / e.n));
+        if (d < bd) {
+            bd = d;
+            best = &e;
+        }
+    }
+    if (!best) return 0;
+    *out = best->cfg;
+    return 1;
+}
+
+}  // extern "C"

@@ -30,7 +30,8 @@ static size_t right_smem(int elem, int nb, int th, int h) {
     return (size_t)elem * ((size_t)th * h + (size_t)th * nb + (size_t)nb * h);
 }
 
-bool upd_cfg_valid(int side, int elem, int nb, const UpdCfg &c, size_t *smem_bytes) {
+// Generic kernels (below): any band width 1..64; W entries strided over the block.
+static bool generic_cfg_valid(int side, int elem, int nb, const UpdCfg &c, size_t *smem_bytes) {
     if (nb < 1 || nb > 64) return false;
     if (c.threads < 32 || c.threads > 1024 || c.threads % 32) return false;
     if (c.cpb < 1 || c.cpb > 8 || c.tile < 1 || c.tile > 256) return false;
@@ -45,6 +46,19 @@ bool upd_cfg_valid(int side, int elem, int nb, const UpdCfg &c, size_t *smem_byt
     if (sm > kSmemLimit) return false;
     if (smem_bytes) *smem_bytes = sm;
     return true;
+}
+
+// Band widths divisible by 4 use the register-tiled kernels (update_tiled.cu);
+// others the generic kernels here.
+bool upd_cfg_valid(int side, int elem, int nb, const UpdCfg &c, size_t *smem_bytes) {
+    if (nb % 4 == 0) {
+        if (!tiled_r(nb, c)) return false;
+        size_t sm = tiled_smem(side, elem, nb, c.tile, 32 * c.cpb);
+        if (sm > kSmemLimit) return false;
+        if (smem_bytes) *smem_bytes = sm;
+        return true;
+    }
+    return generic_cfg_valid(side, elem, nb, c, smem_bytes);
 }
 
 // -------------------------------------------------------------------- QR side
@@ -251,12 +265,52 @@ static cudaError_t launch_right(T *X, long ldx, int M, int N, const T *Vt, long 
     return cudaGetLastError();
 }
 
+// Largest block the compiled kernel can launch (its register use bounds it).
+template <typename K>
+static int max_threads_of(K kernel) {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return fa.maxThreadsPerBlock;
+}
+
+template <typename T>
+static int max_threads(int side, int unroll) {
+    static int cache[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
+    int u = unroll == 1 ? 0 : unroll == 2 ? 1 : 2;
+    int &v = cache[side][u];
+    if (v < 0) {
+        if (side == 0)
+            v = u == 0 ? max_threads_of(trail_left_kernel<T, 1>)
+                       : u == 1 ? max_threads_of(trail_left_kernel<T, 2>) : max_threads_of(trail_left_kernel<T, 4>);
+        else
+            v = u == 0 ? max_threads_of(trail_right_kernel<T, 1>)
+                       : u == 1 ? max_threads_of(trail_right_kernel<T, 2>) : max_threads_of(trail_right_kernel<T, 4>);
+    }
+    return v;
+}
+
+bool upd_cfg_launchable(int side, int elem, int nb, const UpdCfg &c) {
+    size_t sm;
+    if (!upd_cfg_valid(side, elem, nb, c, &sm)) return false;
+    if (nb % 4 == 0) return c.threads <= tiled_max_threads(side, elem, tiled_r(nb, c), c.unroll);
+    int mt = elem == 8 ? max_threads<double>(side, c.unroll) : max_threads<float>(side, c.unroll);
+    return c.threads <= mt;
+}
+
 template <typename T>
 cudaError_t trail_left(T *X, long ldx, int M, int N, const T *Vp, long ldv, int nb, const T *Tm,
                        const UpdCfg &c, cudaStream_t st) {
     if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
+    if (nb % 4 == 0) {
+        if (!upd_cfg_launchable(0, (int)sizeof(T), nb, c)) return cudaErrorInvalidConfiguration;
+        return trail_tiled<T>(0, X, ldx, M, N, Vp, ldv, nb, Tm, c, st);
+    }
     size_t smem = 0;
-    if (!upd_cfg_valid(0, (int)sizeof(T), nb, c, &smem)) return cudaErrorInvalidConfiguration;
+    if (!generic_cfg_valid(0, (int)sizeof(T), nb, c, &smem)) return cudaErrorInvalidConfiguration;
+    if (c.threads > max_threads<T>(0, c.unroll)) return cudaErrorInvalidConfiguration;
     switch (c.unroll) {
         case 1: return launch_left<T, 1>(X, ldx, M, N, Vp, ldv, nb, Tm, c, smem, st);
         case 2: return launch_left<T, 2>(X, ldx, M, N, Vp, ldv, nb, Tm, c, smem, st);
@@ -268,8 +322,13 @@ template <typename T>
 cudaError_t trail_right(T *X, long ldx, int M, int N, const T *Vt, long ldvt, int nb, const T *Tm,
                         const UpdCfg &c, cudaStream_t st) {
     if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
+    if (nb % 4 == 0) {
+        if (!upd_cfg_launchable(1, (int)sizeof(T), nb, c)) return cudaErrorInvalidConfiguration;
+        return trail_tiled<T>(1, X, ldx, M, N, Vt, ldvt, nb, Tm, c, st);
+    }
     size_t smem = 0;
-    if (!upd_cfg_valid(1, (int)sizeof(T), nb, c, &smem)) return cudaErrorInvalidConfiguration;
+    if (!generic_cfg_valid(1, (int)sizeof(T), nb, c, &smem)) return cudaErrorInvalidConfiguration;
+    if (c.threads > max_threads<T>(1, c.unroll)) return cudaErrorInvalidConfiguration;
     switch (c.unroll) {
         case 1: return launch_right<T, 1>(X, ldx, M, N, Vt, ldvt, nb, Tm, c, smem, st);
         case 2: return launch_right<T, 2>(X, ldx, M, N, Vt, ldvt, nb, Tm, c, smem, st);

@@ -56,15 +56,16 @@ def test_ratios():
 
 
 def test_validity_rule_cases():
-    assert tuner.valid(0, 8, (32, 32, 256, 1, 1))          # the default configuration
-    assert not tuner.valid(0, 8, (32, 32, 96, 1, 1))       # 1024 W entries do not split over 96 threads
-    # 8 * (128*65 + 128*257 + 64*256) = 460800 bytes of shared memory > 227 KiB
-    assert not tuner.valid(0, 8, (64, 128, 1024, 8, 1))
-    # 16*256/1024 = 4 entries each; 8 * (16*17 + 16*257 + 16*256) = 67840 bytes
-    assert tuner.valid(0, 8, (16, 16, 1024, 8, 1))
-    assert tuner.valid(0, 8, (64, 16, 64, 1, 1))           # 64*32/64 = 32 entries each: the maximum
-    assert not tuner.valid(0, 8, (64, 16, 32, 1, 1))       # 64 entries each: too many registers
-    assert not tuner.valid(0, 8, (16, 4, 256, 1, 1))       # a 4 x 32 tile cannot occupy 256 threads
+    # the default configuration: w = 64 (16 column groups), 8 reflector groups of R = 4,
+    # 64-row tiles = 8 rows per thread; smem 8 * (64*64 + 64*36 + 32*64) bytes
+    assert tuner.valid(0, 8, (32, 64, 128, 2, 1))
+    assert tuner.smem_bytes(0, 8, 32, 64, 64) == 8 * (4096 + 2304 + 2048)
+    assert not tuner.valid(0, 8, (32, 32, 96, 1, 1))       # 96 threads: 12 reflector groups do not divide 32
+    assert not tuner.valid(0, 8, (32, 16, 256, 1, 1))      # R = 1 but a 16-row tile gives 0.5 rows per thread
+    assert tuner.valid(0, 8, (32, 128, 256, 1, 1))         # 128 rows / 32 groups = 4 rows per thread
+    assert not tuner.valid(0, 8, (64, 128, 1024, 8, 1))    # 8 * (128*256 + 128*68 + 64*256) > 227 KiB
+    assert tuner.valid(0, 4, (64, 128, 1024, 8, 1))        # FP32 fits: 4 * 57856 bytes
+    assert not tuner.valid(0, 4, (16, 16, 64, 3, 1))       # column groups must be a power of two
     n_valid = sum(tuner.valid(0, 8, c) for c in tuner.space())
     assert 0 < n_valid < 2304
 
