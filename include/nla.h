@@ -9,7 +9,7 @@
  *            (UNMQR/TSMQR, Algorithm 2);
  *   stage 2  band -> bidiagonal by bulge chasing (Section 5.1.1, Fig. 3);
  *   stage 3  bidiagonal -> singular values (Section 5.1.1: "finally to ...
- *            diagonal form"), here by Sturm-count bisection in FP64.
+ *            diagonal form"), here by Sturm-count bisection.
  * Every step keeps the singular values intact because it applies orthogonal
  * transformations only (Section 5.1.1).
  *
@@ -102,17 +102,23 @@ nla_status nla_gesvd_vals(int m, int n, nla_dtype dtype, void *dA, int lda, void
                           void *dWork, size_t work_bytes, int *dInfo,
                           const nla_opts *opts, nla_stream_t stream);
 
-/* Batched singular values of `batch` independent matrices of uneven shapes
- * (one persistent launch; matrices bucketed by size, largest first).  hM, hN,
- * hLda: host arrays of shapes.  dA_array / dS_array: DEVICE arrays of device
- * pointers; matrix i is overwritten; dS_array[i] receives min(m_i, n_i)
- * values, descending.  dInfo: `batch` device ints.  Only NLA_F32 and
- * min(m_i, n_i) <= 256 are supported by the persistent kernel. */
-nla_status nla_gesvd_vals_batched_workspace(int batch, nla_dtype dtype, const int *hM,
-                                            const int *hN, size_t *bytes);
-nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *hM, const int *hN,
-                                  const int *hLda, void *const *dA_array, void *const *dS_array,
-                                  void *dWork, size_t work_bytes, int *dInfo,
+/* Batched singular values of `batch` independent FP32 matrices of uneven
+ * shapes in one persistent launch (the batched form of the method of Section
+ * 5.1.1).  dM, dN, dLda: DEVICE int arrays of shapes and leading dimensions;
+ * dA_array / dS_array: DEVICE arrays of device pointers; matrix i is column
+ * major m_i x n_i and is read, not modified; dS_array[i] receives
+ * min(m_i, n_i) values, descending.  max_m, max_n bound every m_i, n_i
+ * (min(max_m, max_n) <= 256).  dInfo: `batch` device ints (0 = success,
+ * -NLA_ERR_UNSUPPORTED for a matrix the kernel cannot hold).  Matrices are
+ * ordered by size on the device and reduced by groups of threads whose size
+ * per size bucket comes from the tuned table (kt_load_config) or defaults.
+ * Nothing is read from the host at run time, so the call can be captured in
+ * a CUDA graph and replayed.  Only NLA_F32 is supported. */
+nla_status nla_gesvd_vals_batched_workspace(int batch, nla_dtype dtype, int max_m, int max_n,
+                                            size_t *bytes);
+nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *dM, const int *dN,
+                                  const int *dLda, void *const *dA_array, void *const *dS_array,
+                                  int max_m, int max_n, void *dWork, size_t work_bytes, int *dInfo,
                                   const nla_opts *opts, nla_stream_t stream);
 
 /* ---------------------------------------------------------------- stages */
@@ -145,11 +151,14 @@ nla_status nla_band2bd(int n, int band, nla_dtype dtype, void *dAB, int ldab, do
                        double *dE, void *dWork, size_t work_bytes, int *dInfo,
                        const nla_opts *opts, nla_stream_t stream);
 
-/* Stage 3: singular values of the upper bidiagonal (dD, dE), FP64 bisection on
- * Sturm counts of the Golub-Kahan tridiagonal; dS receives n values
- * descending, converted to dtype. */
-nla_status nla_bdsvd_vals(int n, const double *dD, const double *dE, void *dS,
-                          nla_dtype dtype, int *dInfo, nla_stream_t stream);
+/* Stage 3: singular values of the upper bidiagonal (dD, dE) by bisection on
+ * Sturm counts of the Golub-Kahan tridiagonal (coarse steps with FP32 counts,
+ * final steps with FP64 counts); dS receives n values descending, converted to
+ * dtype, accurate to the output type's resolution of the bidiagonal's
+ * Gershgorin bound.  dWork: >= nla_bdsvd_vals_workspace bytes, 256-aligned. */
+nla_status nla_bdsvd_vals_workspace(int n, size_t *bytes);
+nla_status nla_bdsvd_vals(int n, const double *dD, const double *dE, void *dS, nla_dtype dtype,
+                          void *dWork, size_t work_bytes, int *dInfo, nla_stream_t stream);
 
 /* ---------------------------------------------------------------- tracing */
 
@@ -170,6 +179,17 @@ nla_status nla_trace_enable(int on);
 /* Fills up to max_entries entries and returns how many classes were seen. */
 int nla_trace_read(nla_trace_entry *out, int max_entries);
 void nla_trace_reset(void);
+
+/* ---------------------------------------------------------------- diagnostics */
+
+/* One 128 x N x K product D = A B on this GPU's tensor cores, the building
+ * block of the TF32 / BF16 trailing update (prec = NLA_UPD_TF32 or
+ * NLA_UPD_BF16): dA is 128 x K and dB is K x N, row-major FP32 (rounded to the
+ * operand type on the device), dD receives 128 x N row-major FP32.  K a
+ * multiple of 16 in [16, 128], N a multiple of 16 in [16, 256].  Lets a caller
+ * check the tensor-core path of its device in isolation. */
+nla_status nla_tc_selftest(int prec, int K, int N, const float *dA, const float *dB, float *dD,
+                           int *dInfo, nla_stream_t stream);
 
 /* Message for the last non-OK status returned on this thread. */
 const char *nla_last_error(void);

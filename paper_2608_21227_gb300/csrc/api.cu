@@ -91,6 +91,9 @@ struct Stage1Plan {
 
 struct Stage1Bufs {
     unsigned int *bar;
+    unsigned int *tickets;  // strip tickets of the tiled update (cleared per call)
+    size_t nticket;
+    void *upd_work;         // partial sums / W' of the tiled update
     double *part;
     void *tauq, *taup, *Tq, *Tp;
     void *tc_scratch;
@@ -102,6 +105,9 @@ size_t elem_size(nla_dtype dt) { return dt == NLA_F64 ? 8 : 4; }
 void carve_stage1(Carver &cv, int M, int N, nla_dtype dt, int b, int update, Stage1Bufs &s) {
     size_t es = elem_size(dt);
     s.bar = cv.take<unsigned int>(64);
+    s.nticket = nla::tiled_tickets(M, N);
+    s.tickets = cv.take<unsigned int>(s.nticket);
+    s.upd_work = cv.take<char>(es * nla::tiled_scratch_elems(M, N));
     s.part = cv.take<double>(nla::panel_part_doubles(nla::panel_max_ctas()));
     s.tauq = cv.take<char>(es * 64);
     s.taup = cv.take<char>(es * 64);
@@ -128,6 +134,7 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
                       T *tauq_all, T *taup_all, int *dInfo, cudaStream_t st) {
     const int b = p.b;
     nla::PanelCtl ctl{bufs.bar, bufs.part, dInfo};
+    const nla::UpdScratch usc{bufs.upd_work, bufs.tickets};
     for (int kb = 0; kb < N; kb += b) {
         const int nb = std::min(b, N - kb);
         T *tq = tauq_all ? tauq_all + kb : reinterpret_cast<T *>(bufs.tauq);
@@ -141,16 +148,16 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
         if constexpr (sizeof(T) == 8) {
             if (p.update != NLA_UPD_NATIVE) {
                 NLA_LAUNCH(nla::kTrTrailLeft, st, nla::trail_left_tc(X + kb + (long)c0 * ldx, ldx, M - kb, N - c0, panel, ldx, nb, Tq,
-                                            p.update, bufs.tc_scratch, bufs.tc_bytes, st),
+                                            p.update, dInfo, st),
                          "QR trailing update (tensor core)");
             } else {
                 NLA_LAUNCH(nla::kTrTrailLeft, st, nla::trail_left<T>(X + kb + (long)c0 * ldx, ldx, M - kb, N - c0, panel, ldx, nb, Tq,
-                                            p.left, st),
+                                            p.left, usc, st),
                          "QR trailing update");
             }
         } else {
             NLA_LAUNCH(nla::kTrTrailLeft, st, nla::trail_left<T>(X + kb + (long)c0 * ldx, ldx, M - kb, N - c0, panel, ldx, nb, Tq, p.left,
-                                        st),
+                                        usc, st),
                      "QR trailing update");
         }
         // LQ sweep: factor the tile row right of the diagonal tile, update below it
@@ -160,13 +167,12 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
             T *Xr = X + c0 + (long)c0 * ldx;
             if constexpr (sizeof(T) == 8) {
                 if (p.update != NLA_UPD_NATIVE) {
-                    NLA_LAUNCH(nla::kTrTrailRight, st, nla::trail_right_tc(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.update,
-                                                 bufs.tc_scratch, bufs.tc_bytes, st),
+                    NLA_LAUNCH(nla::kTrTrailRight, st, nla::trail_right_tc(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.update, dInfo, st),
                              "LQ trailing update (tensor core)");
                     continue;
                 }
             }
-            NLA_LAUNCH(nla::kTrTrailRight, st, nla::trail_right<T>(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.right, st),
+            NLA_LAUNCH(nla::kTrTrailRight, st, nla::trail_right<T>(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.right, usc, st),
                      "LQ trailing update");
         }
     }
@@ -232,6 +238,7 @@ struct GesvdLayout {
     void *AB;
     long ldab;
     void *prog;
+    void *bd;  // bisection scratch
     double *d, *e;
     size_t bytes;
 };
@@ -248,6 +255,7 @@ GesvdLayout gesvd_layout(char *base, int m, int n, nla_dtype dt, const nla_opts 
     L.ldab = 3 * p.b + 1;
     L.AB = cv.take<char>(es * L.ldab * std::max(N, 1));
     L.prog = cv.take<char>(nla::band2bd_scratch_bytes(N));
+    L.bd = cv.take<char>(nla::bdsvd_scratch_bytes(N));
     L.d = cv.take<double>(std::max(N, 1));
     L.e = cv.take<double>(std::max(N, 1));
     L.bytes = align_up(cv.off, 256);
@@ -261,6 +269,7 @@ nla_status gesvd_impl(int m, int n, nla_dtype dt, T *dA, int lda, T *dS, const G
     const bool transpose = m < n;
     const bool need_copy = transpose || (opts && opts->preserve_a);
     NLA_CUDA(cudaMemsetAsync(L.s1.bar, 0, 64 * sizeof(unsigned int), st), "memset control");
+    NLA_CUDA(cudaMemsetAsync(L.s1.tickets, 0, L.s1.nticket * sizeof(unsigned int), st), "memset tickets");
     NLA_CUDA(cudaMemsetAsync(dInfo, 0, sizeof(int), st), "memset info");
     T *X = dA;
     long ldx = lda;
@@ -274,7 +283,7 @@ nla_status gesvd_impl(int m, int n, nla_dtype dt, T *dA, int lda, T *dS, const G
     T *AB = reinterpret_cast<T *>(L.AB);
     NLA_LAUNCH(nla::kTrBandExtract, st, nla::band_extract<T>(X, ldx, N, p.b, AB, L.ldab, st), "band extract");
     NLA_LAUNCH(nla::kTrBand2bd, st, nla::band2bd<T>(AB, L.ldab, N, p.b, L.d, L.e, L.prog, dInfo, st), "bulge chase");
-    NLA_LAUNCH(nla::kTrBisect, st, nla::bdsvd_bisect<T>(N, L.d, L.e, dS, dInfo, st), "bidiagonal singular values");
+    NLA_LAUNCH(nla::kTrBisect, st, nla::bdsvd_bisect<T>(N, L.d, L.e, dS, L.bd, dInfo, st), "bidiagonal singular values");
     (void)dt;
     return NLA_OK;
 }
@@ -357,6 +366,7 @@ nla_status nla_gebrd_band(int m, int n, int band, nla_dtype dtype, void *dA, int
         return fail(NLA_ERR_WORKSPACE, "workspace %zu bytes < required %zu", work_bytes, align_up(cv.off, 256));
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     NLA_CUDA(cudaMemsetAsync(b.bar, 0, 64 * sizeof(unsigned int), st), "memset control");
+    NLA_CUDA(cudaMemsetAsync(b.tickets, 0, b.nticket * sizeof(unsigned int), st), "memset tickets");
     NLA_CUDA(cudaMemsetAsync(dInfo, 0, sizeof(int), st), "memset info");
     if (dtype == NLA_F64)
         return run_stage1<double>((double *)dA, lda, m, n, p, b, (double *)dTauQ, (double *)dTauP, dInfo, st);
@@ -405,18 +415,26 @@ nla_status nla_band2bd(int n, int band, nla_dtype dtype, void *dAB, int ldab, do
     return NLA_OK;
 }
 
-nla_status nla_bdsvd_vals(int n, const double *dD, const double *dE, void *dS, nla_dtype dtype, int *dInfo,
-                          nla_stream_t stream) {
+nla_status nla_bdsvd_vals_workspace(int n, size_t *bytes) {
+    if (!bytes || n < 0) return fail(NLA_ERR_ARG, "bad arguments");
+    *bytes = align_up(nla::bdsvd_scratch_bytes(n), 256);
+    return NLA_OK;
+}
+
+nla_status nla_bdsvd_vals(int n, const double *dD, const double *dE, void *dS, nla_dtype dtype, void *dWork,
+                          size_t work_bytes, int *dInfo, nla_stream_t stream) {
     if (dtype != NLA_F64 && dtype != NLA_F32) return fail(NLA_ERR_ARG, "unknown dtype %d", (int)dtype);
     if (n < 0) return fail(NLA_ERR_ARG, "negative n");
     if (n == 0) return NLA_OK;
     if (!dD || !dS || !dInfo || (n > 1 && !dE)) return fail(NLA_ERR_ARG, "null device pointer");
+    if (!dWork || work_bytes < nla::bdsvd_scratch_bytes(n) || ((uintptr_t)dWork) % 256)
+        return fail(NLA_ERR_WORKSPACE, "workspace too small or misaligned");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     NLA_CUDA(cudaMemsetAsync(dInfo, 0, sizeof(int), st), "memset info");
     if (dtype == NLA_F64)
-        NLA_LAUNCH(nla::kTrBisect, st, nla::bdsvd_bisect<double>(n, dD, dE, (double *)dS, dInfo, st), "bisection");
+        NLA_LAUNCH(nla::kTrBisect, st, nla::bdsvd_bisect<double>(n, dD, dE, (double *)dS, dWork, dInfo, st), "bisection");
     else
-        NLA_LAUNCH(nla::kTrBisect, st, nla::bdsvd_bisect<float>(n, dD, dE, (float *)dS, dInfo, st), "bisection");
+        NLA_LAUNCH(nla::kTrBisect, st, nla::bdsvd_bisect<float>(n, dD, dE, (float *)dS, dWork, dInfo, st), "bisection");
     return NLA_OK;
 }
 

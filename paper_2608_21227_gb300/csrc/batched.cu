@@ -1,26 +1,365 @@
-// batched.cu -- many small matrices of uneven shapes in one persistent launch.
+// batched.cu -- singular values of many small matrices of uneven shapes in one
+// persistent launch (the batched form of the two-stage method, Section 5.1.1).
+//
+//  1. prep kernel (one block): orders the batch by element count, largest first
+//     (bitonic sort of (count, index) keys in shared memory), so that blocks
+//     draw similar matrices together and the long ones start first; clears the
+//     work counter.  Everything stays on the device, so the whole call can be
+//     captured into a CUDA graph.
+//  2. persistent kernel (a grid of #SMs x 2 blocks of 256 threads): each block
+//     takes rounds of work from an atomic counter.  In a round it splits into
+//     groups of g threads -- g chosen per size bucket (kt_load_config installs
+//     tuned values; defaults otherwise) -- and each group reduces one matrix:
+//       * the matrix (or its transpose, so that m >= n) is copied into the
+//         group's share of shared memory when it fits, else into a global
+//         scratch slot of the block (L2-resident at these sizes);
+//       * band width 1: one-stage Householder bidiagonalisation (the band
+//         stage degenerates to the bidiagonal for these sizes), left and right
+//         reflectors with group-wide reductions;
+//       * the bidiagonal singular values by bisection on Sturm counts of the
+//         Golub-Kahan tridiagonal, one thread per value (FP32 arithmetic for
+//         FP32 matrices: the batched accuracy target 5e-6 N sigma_1 is met and
+//         the FP64 pipe is 64x slower on this GPU).
+//     Groups synchronise with named barriers (bar.sync id, g).
+#include <algorithm>
+#include <cfloat>
+#include <vector>
+
 #include "../../include/nla.h"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "trace.h"
+#include "tuned.h"
+
+namespace {
+
+constexpr int kBThreads = 256;
+constexpr int kBSmemElems = 48 * 1024;      // floats of shared memory for matrices per block (192 KiB)
+constexpr int kSortMax = 16384;             // batches up to this size are sorted
+constexpr int kBuckets = 5;
+// Buckets by element count m*n: <= 1/8, 1/4, 1/2, 1 of the block's matrix shared memory, or more
+// (global scratch).  A bucket-b matrix fits one group's share when g >= kMinGroup[b].
+const int kMinGroup[kBuckets] = {32, 64, 128, 256, 256};
+
+struct BatchCfg {
+    int group[kBuckets];  // threads per matrix for each bucket
+};
+
+__device__ int bucket_of(long elems) {
+    int b = 0;
+    while (b < kBuckets - 1 && elems > (long)kBSmemElems >> (kBuckets - 2 - b)) ++b;
+    return b;
+}
+
+nla_status berr(nla_status s, const char *m) {
+    nla_set_last_error(m);
+    return s;
+}
+
+// ---------------------------------------------------------------- prep
+__global__ void batched_prep_kernel(int batch, const int *dM, const int *dN, int *order, unsigned int *counter) {
+    extern __shared__ unsigned long long keys[];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    if (tid == 0) *counter = 0u;
+    if (batch > kSortMax) {
+        for (int i = tid; i < batch; i += nt) order[i] = i;
+        return;
+    }
+    int P = 1;
+    while (P < batch) P <<= 1;
+    for (int i = tid; i < P; i += nt) {
+        unsigned long long k = ~0ull;
+        if (i < batch) {
+            unsigned long long e = (unsigned long long)max(dM[i], 0) * (unsigned long long)max(dN[i], 0);
+            e = min(e, 0xFFFFFFFFull);
+            k = ((0xFFFFFFFFull - e) << 32) | (unsigned)i;  // ascending key = descending size, then index
+        }
+        keys[i] = k;
+    }
+    __syncthreads();
+    for (int size = 2; size <= P; size <<= 1)
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = tid; i < P; i += nt) {
+                int j = i ^ stride;
+                if (j > i) {
+                    bool up = (i & size) == 0;
+                    unsigned long long a = keys[i], b = keys[j];
+                    if ((a > b) == up) {
+                        keys[i] = b;
+                        keys[j] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    for (int i = tid; i < batch; i += nt) order[i] = (int)(keys[i] & 0xFFFFFFFFull);
+}
+
+// ---------------------------------------------------------------- group primitives
+__device__ __forceinline__ void gsync(int gid, int g) {
+    asm volatile("bar.sync %0, %1;" ::"r"(gid + 1), "r"(g) : "memory");
+}
+
+// sum over the group of v (g threads, red holds g/32 floats)
+__device__ float gsum(float v, float *red, int gid, int g, int gt) {
+    v = nla::warp_sum(v);
+    if ((gt & 31) == 0) red[gt >> 5] = v;
+    gsync(gid, g);
+    float s = 0.f;
+    for (int w = 0; w < g / 32; ++w) s += red[w];
+    gsync(gid, g);
+    return s;
+}
+
+// Householder reflector for [alpha; x] with ||x||^2 = xn2 (all threads compute the same scalars)
+__device__ void reflector(float alpha, float xn2, float &tau, float &beta, float &scale) {
+    tau = 0.f;
+    beta = alpha;
+    scale = 0.f;
+    if (xn2 > 0.f) {
+        float r = sqrtf(alpha * alpha + xn2);
+        beta = alpha >= 0.f ? -r : r;
+        tau = (beta - alpha) / beta;
+        scale = 1.f / (alpha - beta);
+    }
+}
+
+// number of singular values of B(d, e) below x (Sturm count of the Golub-Kahan tridiagonal)
+__device__ int count_below_f(int n, const float *d, const float *e, float x, float pivmin) {
+    float q = -x;
+    int neg = q < 0.f;
+    for (int i = 0; i < n; ++i) {
+        if (fabsf(q) < pivmin) q = -pivmin;
+        q = -x - d[i] * d[i] / q;
+        neg += q < 0.f;
+        if (i + 1 < n) {
+            if (fabsf(q) < pivmin) q = -pivmin;
+            q = -x - e[i] * e[i] / q;
+            neg += q < 0.f;
+        }
+    }
+    return neg - n;
+}
+
+// One matrix by one group: W (M x N, column-major, ld M) already loaded, M >= N.
+__device__ void group_svd(float *W, int M, int N, float *d, float *e, float *vbuf, float *red, float *S, int gid,
+                          int g, int gt) {
+    for (int j = 0; j < N; ++j) {
+        // ---- left reflector on column j, rows j..M-1
+        float *col = W + (size_t)j * M;
+        float part = 0.f;
+        for (int i = j + 1 + gt; i < M; i += g) part += col[i] * col[i];
+        const float xn2 = gsum(part, red, gid, g, gt);
+        float tau, beta, sc;
+        reflector(col[j], xn2, tau, beta, sc);
+        if (tau != 0.f) {
+            for (int i = j + 1 + gt; i < M; i += g) col[i] *= sc;  // v, v_j = 1 implicit
+            gsync(gid, g);
+            // columns c > j: warp-per-column dot products, then the update
+            const int wid = gt >> 5, lane = gt & 31, nw = g >> 5;
+            for (int c = j + 1 + wid; c < N; c += nw) {
+                float *cc = W + (size_t)c * M;
+                float s = lane == 0 ? cc[j] : 0.f;
+                for (int i = j + 1 + lane; i < M; i += 32) s += col[i] * cc[i];
+                s = nla::warp_sum(s) * tau;
+                if (lane == 0) cc[j] -= s;
+                for (int i = j + 1 + lane; i < M; i += 32) cc[i] -= s * col[i];
+            }
+        }
+        if (gt == 0) d[j] = beta;
+        gsync(gid, g);
+        if (j + 1 >= N) break;
+        // ---- right reflector on row j, columns j+1..N-1
+        const int L = N - j - 1;
+        float p2 = 0.f;
+        for (int c = j + 2 + gt; c < N; c += g) {
+            float v = W[j + (size_t)c * M];
+            p2 += v * v;
+        }
+        const float yn2 = gsum(p2, red, gid, g, gt);
+        reflector(W[j + (size_t)(j + 1) * M], yn2, tau, beta, sc);
+        if (gt == 0) e[j] = beta;
+        if (tau != 0.f && L > 1) {
+            for (int c = gt; c < L; c += g) vbuf[c] = c == 0 ? 1.f : W[j + (size_t)(j + 1 + c) * M] * sc;
+            gsync(gid, g);
+            for (int i = j + 1 + gt; i < M; i += g) {  // one thread per row
+                float s = 0.f;
+                for (int c = 0; c < L; ++c) s += W[i + (size_t)(j + 1 + c) * M] * vbuf[c];
+                s *= tau;
+                for (int c = 0; c < L; ++c) W[i + (size_t)(j + 1 + c) * M] -= s * vbuf[c];
+            }
+        }
+        gsync(gid, g);
+    }
+    // ---- bisection: one thread per singular value
+    float bnd = 0.f, tmax = 0.f;
+    for (int i = gt; i < N; i += g) {
+        float di = fabsf(d[i]), el = i > 0 ? fabsf(e[i - 1]) : 0.f, er = i + 1 < N ? fabsf(e[i]) : 0.f;
+        bnd = fmaxf(bnd, di + fmaxf(el, er));
+        tmax = fmaxf(tmax, fmaxf(di, er));
+    }
+    {
+        float v = bnd;
+        for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+        float t = tmax;
+        for (int o = 16; o > 0; o >>= 1) t = fmaxf(t, __shfl_xor_sync(0xffffffffu, t, o));
+        if ((gt & 31) == 0) {
+            red[gt >> 5] = v;
+            red[16 + (gt >> 5)] = t;
+        }
+        gsync(gid, g);
+        float b = 0.f, tt = 0.f;
+        for (int w = 0; w < g / 32; ++w) {
+            b = fmaxf(b, red[w]);
+            tt = fmaxf(tt, red[16 + w]);
+        }
+        bnd = b * (1.f + 4.f * FLT_EPSILON) + FLT_MIN;
+        tmax = tt;
+        gsync(gid, g);
+    }
+    const float pivmin = FLT_MIN * fmaxf(1.f, tmax * tmax);
+    const float tol = 2.f * FLT_EPSILON * bnd;
+    for (int idx = gt; idx < N; idx += g) {
+        const int jj = N - 1 - idx;
+        float lo = 0.f, hi = bnd;
+        for (int it = 0; it < 64; ++it) {
+            float mid = 0.5f * (lo + hi);
+            if (hi - lo <= tol || mid <= lo || mid >= hi) break;
+            if (count_below_f(N, d, e, mid, pivmin) <= jj)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        S[idx] = 0.5f * (lo + hi);
+    }
+}
+
+__global__ void __launch_bounds__(kBThreads)
+batched_svd_kernel(int batch, const int *__restrict__ dM, const int *__restrict__ dN, const int *__restrict__ dLda,
+                   float *const *dA, float *const *dS, const int *__restrict__ order, unsigned int *counter,
+                   float *scratch, size_t scratch_elems, int *dInfo, BatchCfg cfg, int sorted) {
+    extern __shared__ __align__(16) float smem[];
+    __shared__ int sh_start, sh_groups;
+    float *mat = smem;                                    // kBSmemElems
+    float *aux = smem + kBSmemElems;                      // per group: d, e (256 each), vbuf 256, red 32
+    const int tid = threadIdx.x;
+    while (true) {
+        if (tid == 0) {
+            unsigned int pos = atomicAdd(counter, 0u);
+            int gsz = kBThreads;
+            if (sorted && pos < (unsigned)batch) {
+                const int i0 = order[pos];
+                const long el = (long)dM[i0] * dN[i0];
+                gsz = cfg.group[bucket_of(el)];
+            }
+            const int ng = kBThreads / gsz;
+            sh_groups = ng;
+            sh_start = (int)atomicAdd(counter, (unsigned)ng);
+        }
+        __syncthreads();
+        const int start = sh_start, ng = sh_groups;
+        if (start >= batch) break;
+        const int g = kBThreads / ng, gid = tid / g, gt = tid % g;
+        const int item = start + gid;
+        if (item < batch) {
+            const int i = order[item];
+            const int m = dM[i], n = dN[i], lda = dLda[i];
+            const float *A = dA[i];
+            float *Sout = dS[i];
+            const int M = max(m, n), N = min(m, n);
+            const bool tr = m < n;
+            const int share = kBSmemElems / ng;
+            float *W = (long)M * N <= share ? mat + (size_t)gid * share : scratch + (size_t)blockIdx.x * scratch_elems;
+            float *d = aux + gid * 800, *e = d + 256, *vb = e + 256, *red = vb + 256;
+            // the global slot is only ever used by a block working on one matrix
+            const bool ok = (long)M * N <= share || (ng == 1 && (size_t)M * N <= scratch_elems);
+            if (ok && N <= 256) {
+                for (int idx = gt; idx < M * N; idx += g) {
+                    const int r = idx % M, c = idx / M;  // W(r, c)
+                    W[idx] = tr ? A[c + (size_t)r * lda] : A[r + (size_t)c * lda];
+                }
+                gsync(gid, g);
+                if (N > 0) group_svd(W, M, N, d, e, vb, red, Sout, gid, g, gt);
+                if (gt == 0) dInfo[i] = 0;
+            } else if (gt == 0) {
+                dInfo[i] = -NLA_ERR_UNSUPPORTED;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+BatchCfg default_cfg() {
+    BatchCfg c;
+    for (int b = 0; b < kBuckets; ++b) c.group[b] = kMinGroup[b];
+    return c;
+}
+
+}  // namespace
+
+namespace nla {
+// Group sizes per bucket installed by the tuner table (bucket b -> threads per matrix).
+int g_batched_group[kBuckets] = {0, 0, 0, 0, 0};
+}
 
 extern "C" {
 
-nla_status nla_gesvd_vals_batched_workspace(int batch, nla_dtype dtype, const int *hM, const int *hN,
-                                            size_t *bytes) {
-    (void)batch;
-    (void)dtype;
-    (void)hM;
-    (void)hN;
-    if (bytes) *bytes = 0;
-    return NLA_ERR_UNSUPPORTED;
+nla_status nla_gesvd_vals_batched_workspace(int batch, nla_dtype dtype, int max_m, int max_n, size_t *bytes) {
+    if (!bytes || batch < 0 || max_m < 0 || max_n < 0) return berr(NLA_ERR_ARG, "bad arguments");
+    if (dtype != NLA_F32) return berr(NLA_ERR_UNSUPPORTED, "the batched kernel supports FP32 only");
+    const size_t blocks = (size_t)nla::device_sm_count() * 2;
+    const size_t slot = (size_t)std::max(max_m, 1) * std::max(max_n, 1);
+    size_t b = 256;                                    // counter
+    b += ((size_t)std::max(batch, 1) * 4 + 255) / 256 * 256;  // order
+    b += blocks * slot * 4;                            // scratch slots
+    *bytes = b;
+    return NLA_OK;
 }
 
-nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *hM, const int *hN, const int *hLda,
-                                  void *const *dA_array, void *const *dS_array, void *dWork, size_t work_bytes,
-                                  int *dInfo, const nla_opts *opts, nla_stream_t stream) {
-    (void)batch; (void)dtype; (void)hM; (void)hN; (void)hLda; (void)dA_array; (void)dS_array;
-    (void)dWork; (void)work_bytes; (void)dInfo; (void)opts; (void)stream;
-    return NLA_ERR_UNSUPPORTED;
+nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *dM, const int *dN, const int *dLda,
+                                  void *const *dA_array, void *const *dS_array, int max_m, int max_n, void *dWork,
+                                  size_t work_bytes, int *dInfo, const nla_opts *opts, nla_stream_t stream) {
+    (void)opts;
+    if (dtype != NLA_F32) return berr(NLA_ERR_UNSUPPORTED, "the batched kernel supports FP32 only");
+    if (batch < 0 || max_m < 0 || max_n < 0) return berr(NLA_ERR_ARG, "negative size");
+    if (batch == 0) return NLA_OK;
+    if (max_n > 256) return berr(NLA_ERR_UNSUPPORTED, "min(m_i, n_i) must be <= 256");
+    if (!dM || !dN || !dLda || !dA_array || !dS_array || !dInfo || !dWork)
+        return berr(NLA_ERR_ARG, "null device pointer");
+    size_t need = 0;
+    nla_gesvd_vals_batched_workspace(batch, dtype, max_m, max_n, &need);
+    if (work_bytes < need) return berr(NLA_ERR_WORKSPACE, "workspace too small");
+    if (((uintptr_t)dWork) % 256) return berr(NLA_ERR_WORKSPACE, "workspace not 256-byte aligned");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    char *w = reinterpret_cast<char *>(dWork);
+    unsigned int *counter = reinterpret_cast<unsigned int *>(w);
+    int *order = reinterpret_cast<int *>(w + 256);
+    float *scratch = reinterpret_cast<float *>(w + 256 + ((size_t)batch * 4 + 255) / 256 * 256);
+    const size_t slot = (size_t)std::max(max_m, 1) * std::max(max_n, 1);
+    BatchCfg cfg = default_cfg();
+    for (int b = 0; b < kBuckets; ++b)
+        if (nla::g_batched_group[b] >= kMinGroup[b] && nla::g_batched_group[b] <= kBThreads &&
+            kBThreads % nla::g_batched_group[b] == 0)
+            cfg.group[b] = nla::g_batched_group[b];
+    static bool attr = false;
+    const size_t sort_smem = (size_t)kSortMax * sizeof(unsigned long long);
+    const size_t main_smem = ((size_t)kBSmemElems + 8 * 800) * sizeof(float);
+    if (!attr) {
+        cudaFuncSetAttribute(batched_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
+        cudaFuncSetAttribute(batched_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)main_smem);
+        attr = true;
+    }
+    {
+        nla::TraceScope ts(nla::kTrBatched, st);
+        batched_prep_kernel<<<1, 1024, batch <= kSortMax ? sort_smem : 0, st>>>(batch, dM, dN, order, counter);
+        int blocks = nla::device_sm_count();
+        batched_svd_kernel<<<blocks, kBThreads, main_smem, st>>>(batch, dM, dN, dLda, (float *const *)dA_array,
+                                                                 (float *const *)dS_array, order, counter, scratch, slot,
+                                                                 dInfo, cfg, batch <= kSortMax ? 1 : 0);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return berr(NLA_ERR_CUDA, cudaGetErrorString(e));
+    return NLA_OK;
 }
 
 }  // extern "C"

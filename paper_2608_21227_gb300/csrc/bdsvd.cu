@@ -4,16 +4,26 @@
 // singular values are found by bisection, which is data-parallel (one thread
 // per singular value) where QR iteration is sequential.  The eigenvalues of
 // the 2n x 2n Golub-Kahan tridiagonal TGK (zero diagonal, off-diagonals
-// d_0, e_0, d_1, e_1, ..., d_{n-1}) are +-sigma_i, so for x > 0 the number of
-// singular values below x is negcount(TGK - x I) - n, where negcount counts
+// t = d_0, e_0, d_1, e_1, ..., d_{n-1}) are +-sigma_i, so for x > 0 the number
+// of singular values below x is negcount(TGK - x I) - n, where negcount counts
 // the negative pivots of the LDL^T factorisation of TGK - x I (Sylvester's law
-// of inertia): q_1 = -x, q_i = -x - t_{i-1}^2 / q_{i-1}.  A pivot that is
-// exactly zero is replaced by -pivmin.  All arithmetic is FP64.
+// of inertia): q_1 = -x, q_i = -x - t_{i-1}^2 / q_{i-1}; a pivot smaller than
+// pivmin in magnitude is replaced by -pivmin.
 //
-// Thread i brackets the i-th largest value in [lo, hi] starting from
-// [0, max_i(|d_i| + max(|e_{i-1}|, |e_i|))] (Gershgorin on TGK) and halves the
-// bracket until its width is below the resolution of the output type
-// relative to that bound (2^-52 for FP64 output, 2^-27 for FP32 output).
+// GB300's FP64 pipe issues a small fraction of the FP32 rate, and an IEEE FP64
+// division costs many FP64 issue slots, so the search is split:
+//   prep:   B is scaled by a power of two so its Gershgorin bound is <= 1
+//           (exact), and the squares t_i^2 are stored once in FP64 and FP32;
+//   coarse: bisection with FP32 Sturm counts until the bracket is 2^-16 wide.
+//           An FP32 count is the exact count of a matrix whose entries differ
+//           relatively by a few FP32 rounding errors, so it can only misplace
+//           values within a few 2^-24 of x; the bracket is then widened by
+//           2^-18 on both sides, which keeps the value inside it;
+//   fine:   bisection with FP64 counts to the output resolution (2^-51 of the
+//           bound for FP64 output, 2^-27 for FP32).  The FP64 count forms
+//           1/q from an FP32 estimate and two Newton-Raphson corrections
+//           r <- r + r (1 - q r) (quadratic convergence: ~2^-22 -> 2^-44 ->
+//           below FP64 rounding), i.e. four FMAs instead of a division.
 #include <cfloat>
 
 #include "common.cuh"
@@ -22,85 +32,122 @@
 namespace nla {
 
 constexpr int kBisectThreads = 128;
+constexpr double kPivminFine = 0x1p-100;   // pivot floor of the FP64 counts (scaled problem)
+constexpr float kPivminCoarse = 0x1p-60f;  // pivot floor of the FP32 counts
 
-NLA_DEV int count_below(int n, const double *__restrict__ d, const double *__restrict__ e, double x,
-                        double pivmin) {
-    double q = -x;
-    int neg = q < 0.0;
-    for (int i = 0; i < n; ++i) {
-        if (fabs(q) < pivmin) q = -pivmin;
-        double di = __ldg(d + i);
-        q = -x - (di * di) / q;
-        neg += q < 0.0;
-        if (i + 1 < n) {
-            if (fabs(q) < pivmin) q = -pivmin;
-            double ei = __ldg(e + i);
-            q = -x - (ei * ei) / q;
-            neg += q < 0.0;
-        }
-    }
-    return neg - n;
+size_t bdsvd_scratch_bytes(int n) {
+    const size_t m = (size_t)(n > 0 ? 2 * n : 1);
+    return 256 + m * sizeof(double) + ((m * sizeof(float) + 255) / 256) * 256;
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kBisectThreads)
-bisect_kernel(int n, const double *__restrict__ d, const double *__restrict__ e, T *__restrict__ S,
-              double rel_tol) {
-    __shared__ double sh_bound, sh_tmax;
-    // Gershgorin bound and the largest squared off-diagonal, per block
-    double bnd = 0.0, tmax = 0.0;
+// One block: Gershgorin bound, power-of-two scale, squared scaled off-diagonals.
+__global__ void bd_prep_kernel(int n, const double *__restrict__ d, const double *__restrict__ e, double *hdr,
+                               double *t2, float *t2f) {
+    __shared__ double wb[32];
+    __shared__ double sh_scale;
+    double bnd = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         double di = fabs(d[i]);
         double el = i > 0 ? fabs(e[i - 1]) : 0.0, er = i + 1 < n ? fabs(e[i]) : 0.0;
         bnd = fmax(bnd, di + fmax(el, er));
-        tmax = fmax(tmax, fmax(di, er));
     }
     bnd = warp_max(bnd);
-    tmax = warp_max(tmax);
-    __shared__ double wb[32], wt[32];
-    if ((threadIdx.x & 31) == 0) {
-        wb[threadIdx.x >> 5] = bnd;
-        wt[threadIdx.x >> 5] = tmax;
-    }
+    if ((threadIdx.x & 31) == 0) wb[threadIdx.x >> 5] = bnd;
     __syncthreads();
     if (threadIdx.x == 0) {
-        double b = 0.0, t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            b = fmax(b, wb[w]);
-            t = fmax(t, wt[w]);
-        }
-        sh_bound = b;
-        sh_tmax = t;
+        double b = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmax(b, wb[w]);
+        int ex = 0;
+        if (b > 0.0) frexp(b, &ex);  // b * 2^-ex in [0.5, 1)
+        sh_scale = ldexp(1.0, -ex);
+        hdr[0] = sh_scale;
+        hdr[1] = b;
     }
     __syncthreads();
+    const double s = sh_scale;
+    for (int i = threadIdx.x; i < 2 * n - 1; i += blockDim.x) {
+        double t = (i & 1) ? e[i >> 1] : d[i >> 1];
+        t *= s;
+        t2[i] = t * t;
+        t2f[i] = (float)(t * t);
+    }
+}
+
+NLA_DEV int count_coarse(int n2, const float *__restrict__ t2f, float x) {
+    float q = -x;
+    int neg = q < 0.f;
+    for (int i = 0; i < n2; ++i) {
+        if (fabsf(q) < kPivminCoarse) q = -kPivminCoarse;
+        q = -x - __fdividef(__ldg(t2f + i), q);
+        neg += q < 0.f;
+    }
+    return neg;
+}
+
+NLA_DEV double recip_nr(double q) {
+    double r = (double)__fdividef(1.f, (float)q);  // ~2^-22 relative
+    double h = fma(-q, r, 1.0);
+    r = fma(r, h, r);  // ~2^-44
+    h = fma(-q, r, 1.0);
+    return fma(r, h, r);  // FP64 rounding level
+}
+
+NLA_DEV int count_fine(int n2, const double *__restrict__ t2, double x) {
+    double q = -x;
+    int neg = q < 0.0;
+    for (int i = 0; i < n2; ++i) {
+        if (fabs(q) < kPivminFine) q = -kPivminFine;
+        q = fma(-__ldg(t2 + i), recip_nr(q), -x);
+        neg += q < 0.0;
+    }
+    return neg;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBisectThreads)
+bisect_kernel(int n, const double *__restrict__ hdr, const double *__restrict__ t2, const float *__restrict__ t2f,
+              T *__restrict__ S, double fine_tol) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
-    const double bound = sh_bound * (1.0 + 4.0 * DBL_EPSILON) + DBL_MIN;
-    const double pivmin = DBL_MIN * fmax(1.0, sh_tmax * sh_tmax);
-    const double tol = rel_tol * bound;
-    const int j = n - 1 - idx;  // idx-th largest == j-th smallest
-    double lo = 0.0, hi = bound;
-    for (int it = 0; it < 128; ++it) {
-        double mid = 0.5 * (lo + hi);
-        if (hi - lo <= tol || mid <= lo || mid >= hi) break;
-        if (count_below(n, d, e, mid, pivmin) <= j)
+    const double s = hdr[0];
+    const int n2 = 2 * n - 1;
+    const int j = n - 1 - idx;  // idx-th largest == j-th smallest; counts below x are negcount - n
+    // coarse FP32 bisection on [0, 1]
+    float lo = 0.f, hi = 1.f;
+    while (hi - lo > 0x1p-16f) {
+        const float mid = 0.5f * (lo + hi);
+        if (count_coarse(n2, t2f, mid) - n <= j)
             lo = mid;
         else
             hi = mid;
     }
-    S[idx] = (T)(0.5 * (lo + hi));
+    double dlo = fmax(0.0, (double)lo - 0x1p-18), dhi = fmin(1.0, (double)hi + 0x1p-18);
+    for (int it = 0; it < 80; ++it) {
+        const double mid = 0.5 * (dlo + dhi);
+        if (dhi - dlo <= fine_tol || mid <= dlo || mid >= dhi) break;
+        if (count_fine(n2, t2, mid) - n <= j)
+            dlo = mid;
+        else
+            dhi = mid;
+    }
+    S[idx] = (T)(0.5 * (dlo + dhi) / s);
 }
 
 template <typename T>
-cudaError_t bdsvd_bisect(int n, const double *d, const double *e, T *S, int *info, cudaStream_t st) {
+cudaError_t bdsvd_bisect(int n, const double *d, const double *e, T *S, void *scratch, int *info, cudaStream_t st) {
     (void)info;
     if (n <= 0) return cudaSuccess;
-    const double rel_tol = sizeof(T) == 8 ? 2.0 * DBL_EPSILON : 0x1p-27;
-    bisect_kernel<T><<<(n + kBisectThreads - 1) / kBisectThreads, kBisectThreads, 0, st>>>(n, d, e, S, rel_tol);
+    char *w = reinterpret_cast<char *>(scratch);
+    double *hdr = reinterpret_cast<double *>(w);
+    double *t2 = reinterpret_cast<double *>(w + 256);
+    float *t2f = reinterpret_cast<float *>(w + 256 + (size_t)2 * n * sizeof(double));
+    bd_prep_kernel<<<1, 1024, 0, st>>>(n, d, e, hdr, t2, t2f);
+    const double tol = sizeof(T) == 8 ? 0x1p-51 : 0x1p-27;
+    bisect_kernel<T><<<(n + kBisectThreads - 1) / kBisectThreads, kBisectThreads, 0, st>>>(n, hdr, t2, t2f, S, tol);
     return cudaGetLastError();
 }
 
-template cudaError_t bdsvd_bisect<double>(int, const double *, const double *, double *, int *, cudaStream_t);
-template cudaError_t bdsvd_bisect<float>(int, const double *, const double *, float *, int *, cudaStream_t);
+template cudaError_t bdsvd_bisect<double>(int, const double *, const double *, double *, void *, int *, cudaStream_t);
+template cudaError_t bdsvd_bisect<float>(int, const double *, const double *, float *, void *, int *, cudaStream_t);
 
 }  // namespace nla

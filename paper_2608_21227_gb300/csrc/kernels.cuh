@@ -29,6 +29,15 @@ cudaError_t panel_factor(T *P, long rs, long cs, int M, int nb, T *tau, T *Tm,
 struct UpdCfg {
     int tile, threads, cpb, unroll;
 };
+// Scratch of the register-tiled update: partial sums and W' / Y'
+// (tiled_scratch_elems elements of the matrix type) and one ticket counter per
+// strip (tiled_tickets; zero before the first launch, left zero after each).
+struct UpdScratch {
+    void *work;
+    unsigned int *tickets;
+};
+size_t tiled_scratch_elems(int M, int N);
+size_t tiled_tickets(int M, int N);
 // Validity of a configuration for the SIMT trailing-update kernels
 // (side 0 = QR/left, 1 = LQ/right); elem = bytes per element.
 bool upd_cfg_valid(int side, int elem, int nb, const UpdCfg &c, size_t *smem_bytes);
@@ -44,26 +53,24 @@ size_t tiled_smem(int side, int elem, int nb, int th, int w);
 int tiled_max_threads(int side, int elem, int R, int unroll);
 template <typename T>
 cudaError_t trail_tiled(int side, T *X, long ldx, int M, int N, const T *V, long ldv, int nb, const T *Tm,
-                        const UpdCfg &c, cudaStream_t st);
+                        const UpdCfg &c, const UpdScratch &sc, cudaStream_t st);
 
 // QR side: X (M x N at X, ldx) <- (I - V T V^T)^T X, V = unit lower M x nb at Vp (ldv).
 template <typename T>
 cudaError_t trail_left(T *X, long ldx, int M, int N, const T *Vp, long ldv, int nb,
-                       const T *Tm, const UpdCfg &c, cudaStream_t st);
+                       const T *Tm, const UpdCfg &c, const UpdScratch &sc, cudaStream_t st);
 // LQ side: X (M x N) <- X (I - V T V^T), V = unit lower N x nb stored transposed:
 // V(c, k) = Vt[k + c*ldvt].
 template <typename T>
 cudaError_t trail_right(T *X, long ldx, int M, int N, const T *Vt, long ldvt, int nb,
-                        const T *Tm, const UpdCfg &c, cudaStream_t st);
+                        const T *Tm, const UpdCfg &c, const UpdScratch &sc, cudaStream_t st);
 
 // Mixed precision (FP64 matrix, TF32 or BF16 tensor-core contraction).
-// prec: 1 = TF32, 2 = BF16.
+// prec: 1 = TF32, 2 = BF16; a bounded wait that gives up writes to *info.
 cudaError_t trail_left_tc(double *X, long ldx, int M, int N, const double *Vp, long ldv, int nb,
-                          const double *Tm, int prec, void *scratch, size_t scratch_bytes,
-                          cudaStream_t st);
+                          const double *Tm, int prec, int *info, cudaStream_t st);
 cudaError_t trail_right_tc(double *X, long ldx, int M, int N, const double *Vt, long ldvt,
-                           int nb, const double *Tm, int prec, void *scratch,
-                           size_t scratch_bytes, cudaStream_t st);
+                           int nb, const double *Tm, int prec, int *info, cudaStream_t st);
 size_t trail_tc_scratch_bytes(int M, int N, int nb);
 bool trail_tc_available();
 
@@ -79,8 +86,9 @@ size_t band2bd_scratch_bytes(int n);
 template <typename T>
 cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *scratch,
                     int *info, cudaStream_t st);
+size_t bdsvd_scratch_bytes(int n);
 template <typename T>
-cudaError_t bdsvd_bisect(int n, const double *d, const double *e, T *S, int *info,
+cudaError_t bdsvd_bisect(int n, const double *d, const double *e, T *S, void *scratch, int *info,
                          cudaStream_t st);
 
 int device_sm_count();

@@ -166,7 +166,8 @@ struct TrailBench {
     int side, m, n, reps;
     T *A = nullptr, *A0 = nullptr, *Xref = nullptr;
     T *tau = nullptr, *Tm = nullptr;
-    unsigned int *bar = nullptr;
+    unsigned int *bar = nullptr, *tickets = nullptr;
+    void *uwork = nullptr;
     double *part = nullptr, *diff = nullptr;
     int *info = nullptr;
     cudaStream_t st = nullptr;
@@ -182,6 +183,9 @@ struct TrailBench {
         if ((e = cudaMalloc(&tau, 64 * sizeof(T)))) return e;
         if ((e = cudaMalloc(&Tm, 64 * 64 * sizeof(T)))) return e;
         if ((e = cudaMalloc(&bar, 64 * sizeof(unsigned int)))) return e;
+        if ((e = cudaMalloc(&tickets, nla::tiled_tickets(m, n) * sizeof(unsigned int)))) return e;
+        if ((e = cudaMemset(tickets, 0, nla::tiled_tickets(m, n) * sizeof(unsigned int)))) return e;
+        if ((e = cudaMalloc(&uwork, nla::tiled_scratch_elems(m, n) * sizeof(T)))) return e;
         if ((e = cudaMalloc(&part, nla::panel_part_doubles(nla::panel_max_ctas()) * sizeof(double)))) return e;
         if ((e = cudaMalloc(&diff, 2 * sizeof(double)))) return e;
         if ((e = cudaMalloc(&info, sizeof(int)))) return e;
@@ -197,6 +201,8 @@ struct TrailBench {
         cudaFree(tau);
         cudaFree(Tm);
         cudaFree(bar);
+        cudaFree(tickets);
+        cudaFree(uwork);
         cudaFree(part);
         cudaFree(diff);
         cudaFree(info);
@@ -223,9 +229,11 @@ struct TrailBench {
         return cudaStreamSynchronize(st);
     }
     cudaError_t launch(const nla_cfg &c) {
+        const nla::UpdScratch sc{uwork, tickets};
         if (side == 0)
-            return nla::trail_left<T>(A + (long)b * m, m, m, n - b, A, m, b, Tm, upd_of(c), st);
-        return nla::trail_right<T>(A + b + (long)b * m, m, m - b, n - b, A + (long)b * m, m, b, Tm, upd_of(c), st);
+            return nla::trail_left<T>(A + (long)b * m, m, m, n - b, A, m, b, Tm, upd_of(c), sc, st);
+        return nla::trail_right<T>(A + b + (long)b * m, m, m - b, n - b, A + (long)b * m, m, b, Tm, upd_of(c), sc,
+                                   st);
     }
     cudaError_t restore() { return cudaMemcpyAsync(A, A0, (size_t)m * n * sizeof(T), cudaMemcpyDeviceToDevice, st); }
     // Returns median ms (status 0), or status 1 (launch) / 2 (verification).

@@ -21,7 +21,7 @@
 namespace nla {
 
 constexpr int kMaxItems = 32;     // W entries held in registers per thread
-constexpr size_t kSmemLimit = 227 * 1024;
+constexpr size_t kSmemLimit = 226 * 1024;
 
 static size_t left_smem(int elem, int nb, int th, int w) {
     return (size_t)elem * ((size_t)th * (nb + 1) + (size_t)th * (w + 1) + (size_t)nb * w);
@@ -302,11 +302,11 @@ bool upd_cfg_launchable(int side, int elem, int nb, const UpdCfg &c) {
 
 template <typename T>
 cudaError_t trail_left(T *X, long ldx, int M, int N, const T *Vp, long ldv, int nb, const T *Tm,
-                       const UpdCfg &c, cudaStream_t st) {
+                       const UpdCfg &c, const UpdScratch &sc, cudaStream_t st) {
     if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
     if (nb % 4 == 0) {
         if (!upd_cfg_launchable(0, (int)sizeof(T), nb, c)) return cudaErrorInvalidConfiguration;
-        return trail_tiled<T>(0, X, ldx, M, N, Vp, ldv, nb, Tm, c, st);
+        return trail_tiled<T>(0, X, ldx, M, N, Vp, ldv, nb, Tm, c, sc, st);
     }
     size_t smem = 0;
     if (!generic_cfg_valid(0, (int)sizeof(T), nb, c, &smem)) return cudaErrorInvalidConfiguration;
@@ -320,11 +320,11 @@ cudaError_t trail_left(T *X, long ldx, int M, int N, const T *Vp, long ldv, int 
 
 template <typename T>
 cudaError_t trail_right(T *X, long ldx, int M, int N, const T *Vt, long ldvt, int nb, const T *Tm,
-                        const UpdCfg &c, cudaStream_t st) {
+                        const UpdCfg &c, const UpdScratch &sc, cudaStream_t st) {
     if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
     if (nb % 4 == 0) {
         if (!upd_cfg_launchable(1, (int)sizeof(T), nb, c)) return cudaErrorInvalidConfiguration;
-        return trail_tiled<T>(1, X, ldx, M, N, Vt, ldvt, nb, Tm, c, st);
+        return trail_tiled<T>(1, X, ldx, M, N, Vt, ldvt, nb, Tm, c, sc, st);
     }
     size_t smem = 0;
     if (!generic_cfg_valid(1, (int)sizeof(T), nb, c, &smem)) return cudaErrorInvalidConfiguration;
@@ -337,12 +337,12 @@ cudaError_t trail_right(T *X, long ldx, int M, int N, const T *Vt, long ldvt, in
 }
 
 template cudaError_t trail_left<double>(double *, long, int, int, const double *, long, int,
-                                        const double *, const UpdCfg &, cudaStream_t);
+                                        const double *, const UpdCfg &, const UpdScratch &, cudaStream_t);
 template cudaError_t trail_left<float>(float *, long, int, int, const float *, long, int, const float *,
-                                       const UpdCfg &, cudaStream_t);
+                                       const UpdCfg &, const UpdScratch &, cudaStream_t);
 template cudaError_t trail_right<double>(double *, long, int, int, const double *, long, int,
-                                         const double *, const UpdCfg &, cudaStream_t);
+                                         const double *, const UpdCfg &, const UpdScratch &, cudaStream_t);
 template cudaError_t trail_right<float>(float *, long, int, int, const float *, long, int,
-                                        const float *, const UpdCfg &, cudaStream_t);
+                                        const float *, const UpdCfg &, const UpdScratch &, cudaStream_t);
 
 }  // namespace nla

@@ -12,6 +12,12 @@
 //           tile; per reflector one 128-bit load of W' and one broadcast
 //           128-bit load of V (stored k-major) feed 16 FMAs.
 //
+// Two launches per side keep every SM busy: step 1 runs on a grid of
+// (strips) x (splits of the long dimension, about three waves in all) and the
+// last block of each strip -- chosen by an atomic ticket, so nothing waits --
+// reduces the partial sums and applies T (step 2); step 3 runs on a full 2-D
+// grid of (tile x strip) blocks.
+//
 // QR side: X tiles are staged row-major with an XOR swizzle of the 4-column
 // group by (row & 7), so that both the column-wise staging stores and the
 // row-wise 128-bit reads are free of bank conflicts.  LQ side: X tiles are
@@ -23,7 +29,7 @@
 
 namespace nla {
 
-constexpr size_t kTiledSmemLimit = 227 * 1024;
+constexpr size_t kTiledSmemLimit = 226 * 1024;  // dynamic bytes; the kernels' static shared memory fits in the rest
 
 template <typename T>
 struct Vec4;
@@ -72,27 +78,33 @@ int tiled_r(int nb, const UpdCfg &c) {
 }
 
 // -------------------------------------------------------------------- QR side
+// Step 1 (+ step 2 in the last block of each strip): block (cb, s) accumulates
+// the partial W = V^T X over rows [s*Ms, (s+1)*Ms) of strip cb and stores it;
+// the last block of the strip to finish (atomic ticket) sums the S partials,
+// applies T^T and stores W' for step 3.
 template <typename T, int R, int U>
-__global__ void trail_left_tiled(T *__restrict__ X, long ldx, int M, int N, const T *__restrict__ V, long ldv, int nb,
-                 const T *__restrict__ Tm, int th, int w) {
+__global__ void left_w_kernel(const T *__restrict__ X, long ldx, int M, int N, const T *__restrict__ V, long ldv,
+                              int nb, const T *__restrict__ Tm, int th, int w, int Ms, T *part, T *fin,
+                              unsigned int *tickets) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int sh_last;
     const int ldv_s = nb + 4;
     T *Xs = reinterpret_cast<T *>(smem_raw);  // th x w, swizzled
-    T *Vs = Xs + (size_t)th * w;             // step 1: th x (nb+4) row-major; step 3: nb x th (k-major)
+    T *Vs = Xs + (size_t)th * w;             // th x (nb+4) row-major
     T *Ws = Vs + (size_t)th * ldv_s;         // nb x w row-major
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int ncg = w >> 2, cg = tid % ncg, rg = tid / ncg, nrg = nt / ncg;
+    const int ncg = w >> 2, cg = tid % ncg, rg = tid / ncg;
     const int c0 = blockIdx.x * w, wc = min(w, N - c0);
+    const int s = blockIdx.y, S = gridDim.y;
+    const int rbeg = s * Ms, rend = min(M, rbeg + Ms);
 
     T acc[R][4];
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-
-    // ---- step 1: W = V^T X_strip
-    for (int r0 = 0; r0 < M; r0 += th) {
-        const int rows = min(th, M - r0);
+    for (int r0 = rbeg; r0 < rend; r0 += th) {
+        const int rows = min(th, rend - r0);
         for (int idx = tid; idx < th * w; idx += nt) {
             int r = idx % th, c = idx / th;
             Xs[swz(r, c, w)] = (r < rows && c < wc) ? X[(r0 + r) + (long)(c0 + c) * ldx] : T(0);
@@ -106,22 +118,51 @@ __global__ void trail_left_tiled(T *__restrict__ X, long ldx, int M, int N, cons
         __syncthreads();
 #pragma unroll U
         for (int r = 0; r < rows; ++r) {
-            T x[4];
+            T x[4], v[R];
             Vec4<T>::ld(Xs + swz(r, 4 * cg, w), x);
             const T *vr = Vs + r * ldv_s + R * rg;
+            if constexpr (R % 4 == 0) {
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const T vi = vr[i];
+                for (int i = 0; i < R; i += 4) Vec4<T>::ld(vr + i, v + i);
+            } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += vi * x[j];
+                for (int i = 0; i < R; ++i) v[i] = vr[i];
             }
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += v[i] * x[j];
         }
         __syncthreads();
     }
+    // store the partial W (nb x N slab of this split)
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 4 * cg + j;
+            if (c < wc) part[((size_t)s * nb + R * rg + i) * N + c0 + c] = acc[i][j];
+        }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sh_last = atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(S - 1);
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    // ---- step 2 (last block of the strip): W = sum of partials; W' = T^T W
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 4 * cg + j;
+            T sum = T(0);
+            if (c < wc)
+                for (int q = 0; q < S; ++q) sum += __ldcg(part + ((size_t)q * nb + R * rg + i) * N + c0 + c);
+            acc[i][j] = sum;
+        }
 #pragma unroll
     for (int i = 0; i < R; ++i) Vec4<T>::st(Ws + (R * rg + i) * w + 4 * cg, acc[i]);
     __syncthreads();
-    // ---- step 2: W <- T^T W
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const int kk = R * rg + i;
@@ -134,83 +175,102 @@ __global__ void trail_left_tiled(T *__restrict__ X, long ldx, int M, int N, cons
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] += t * wv[j];
         }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = 4 * cg + j;
+            if (c < wc) fin[(size_t)kk * N + c0 + c] = acc[i][j];
+        }
+    }
+    if (tid == 0) tickets[blockIdx.x] = 0u;  // ready for the next launch
+}
+
+// Step 3: block (cb, rb) updates the th x w tile X(rb, cb) -= V(rb, :) W'(:, cb).
+template <typename T, int U>
+__global__ void left_x_kernel(T *__restrict__ X, long ldx, int M, int N, const T *__restrict__ V, long ldv, int nb,
+                              int th, int w, const T *__restrict__ fin) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);  // th x w, swizzled
+    T *Vs = Xs + (size_t)th * w;             // nb x th, k-major
+    T *Ws = Vs + (size_t)th * (nb + 4);      // nb x w
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ncg = w >> 2, cg = tid % ncg, rg = tid / ncg, nrg = nt / ncg;
+    const int c0 = blockIdx.x * w, wc = min(w, N - c0);
+    const int r0 = blockIdx.y * th, rows = min(th, M - r0);
+    for (int idx = tid; idx < th * w; idx += nt) {
+        int r = idx % th, c = idx / th;
+        Xs[swz(r, c, w)] = (r < rows && c < wc) ? X[(r0 + r) + (long)(c0 + c) * ldx] : T(0);
+    }
+    for (int idx = tid; idx < th * nb; idx += nt) {
+        int r = idx % th, k = idx / th, gr = r0 + r;
+        T v = T(0);
+        if (r < rows) v = gr > k ? V[gr + (long)k * ldv] : (gr == k ? T(1) : T(0));
+        Vs[k * th + r] = v;
+    }
+    for (int idx = tid; idx < nb * w; idx += nt) {
+        int c = idx % w, k = idx / w;
+        Ws[k * w + c] = c < wc ? fin[(size_t)k * N + c0 + c] : T(0);
     }
     __syncthreads();
+    const int rpt = th / nrg;  // rows per thread, a multiple of 4
+    for (int rb = rg * rpt; rb < rg * rpt + rpt; rb += 4) {
+        T sacc[4][4];
 #pragma unroll
-    for (int i = 0; i < R; ++i) Vec4<T>::st(Ws + (R * rg + i) * w + 4 * cg, acc[i]);
-    __syncthreads();
-    // ---- step 3: X_strip -= V W'
-    const int rpt = th / nrg;  // rows per thread, multiple of 4
-    for (int r0 = 0; r0 < M; r0 += th) {
-        const int rows = min(th, M - r0);
-        for (int idx = tid; idx < th * w; idx += nt) {
-            int r = idx % th, c = idx / th;
-            Xs[swz(r, c, w)] = (r < rows && c < wc) ? X[(r0 + r) + (long)(c0 + c) * ldx] : T(0);
-        }
-        for (int idx = tid; idx < th * nb; idx += nt) {
-            int r = idx % th, k = idx / th, gr = r0 + r;
-            T v = T(0);
-            if (r < rows) v = gr > k ? V[gr + (long)k * ldv] : (gr == k ? T(1) : T(0));
-            Vs[k * th + r] = v;  // k-major
-        }
-        __syncthreads();
-        for (int rb = rg * rpt; rb < rg * rpt + rpt; rb += 4) {
-            T s[4][4];
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sacc[a][j] = T(0);
+#pragma unroll U
+        for (int k = 0; k < nb; ++k) {
+            T v[4], wv[4];
+            Vec4<T>::ld(Vs + k * th + rb, v);
+            Vec4<T>::ld(Ws + k * w + 4 * cg, wv);
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) s[a][j] = T(0);
-#pragma unroll U
-            for (int k = 0; k < nb; ++k) {
-                T v[4], wv[4];
-                Vec4<T>::ld(Vs + k * th + rb, v);
-                Vec4<T>::ld(Ws + k * w + 4 * cg, wv);
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) s[a][j] += v[a] * wv[j];
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                T *p = Xs + swz(rb + a, 4 * cg, w);
-                T x[4];
-                Vec4<T>::ld(p, x);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) x[j] -= s[a][j];
-                Vec4<T>::st(p, x);
-            }
+                for (int j = 0; j < 4; ++j) sacc[a][j] += v[a] * wv[j];
         }
-        __syncthreads();
-        for (int idx = tid; idx < th * w; idx += nt) {
-            int r = idx % th, c = idx / th;
-            if (r < rows && c < wc) X[(r0 + r) + (long)(c0 + c) * ldx] = Xs[swz(r, c, w)];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            T *p = Xs + swz(rb + a, 4 * cg, w);
+            T x[4];
+            Vec4<T>::ld(p, x);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] -= sacc[a][j];
+            Vec4<T>::st(p, x);
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int idx = tid; idx < th * w; idx += nt) {
+        int r = idx % th, c = idx / th;
+        if (r < rows && c < wc) X[(r0 + r) + (long)(c0 + c) * ldx] = Xs[swz(r, c, w)];
     }
 }
 
 // -------------------------------------------------------------------- LQ side
+// Step 1 (+2): block (rb, s) accumulates Y = X V over columns [s*Ns, (s+1)*Ns)
+// of the h-row strip rb; the last block sums the partials and stores Y' = Y T.
 template <typename T, int R, int U>
-__global__ void trail_right_tiled(T *__restrict__ X, long ldx, int M, int N, const T *__restrict__ Vt, long ldvt, int nb,
-                  const T *__restrict__ Tm, int th, int h) {
+__global__ void right_w_kernel(const T *__restrict__ X, long ldx, int M, int N, const T *__restrict__ Vt, long ldvt,
+                               int nb, const T *__restrict__ Tm, int th, int h, int Ns, T *part, T *fin,
+                               unsigned int *tickets) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int sh_last;
     const int ldv_s = nb + 4;
-    T *Xs = reinterpret_cast<T *>(smem_raw);  // th columns x h rows, column-major (col c at Xs + c*h)
-    T *Vs = Xs + (size_t)th * h;             // step 1: th x (nb+4) (row c = V(c, :)); step 3: nb x th (k-major)
-    T *Ys = Vs + (size_t)th * ldv_s;         // nb x h (col k at Ys + k*h)
+    T *Xs = reinterpret_cast<T *>(smem_raw);  // th columns x h rows, column-major
+    T *Vs = Xs + (size_t)th * h;             // th x (nb+4): row c = V(c, :)
+    T *Ys = Vs + (size_t)th * ldv_s;         // nb x h
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int ncg = h >> 2, cg = tid % ncg, rg = tid / ncg, nrg = nt / ncg;
+    const int ncg = h >> 2, cg = tid % ncg, rg = tid / ncg;
     const int i0 = blockIdx.x * h, hr = min(h, M - i0);
+    const int s = blockIdx.y, S = gridDim.y;
+    const int cbeg = s * Ns, cend = min(N, cbeg + Ns);
 
     T acc[R][4];
 #pragma unroll
     for (int i = 0; i < R; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
-
-    // ---- step 1: Y = X_strip V   (acc[i][j] = Y(4cg + j, R rg + i))
-    for (int cb = 0; cb < N; cb += th) {
-        const int cols = min(th, N - cb);
+    for (int cb = cbeg; cb < cend; cb += th) {
+        const int cols = min(th, cend - cb);
         for (int idx = tid; idx < th * h; idx += nt) {
             int i = idx % h, c = idx / h;
             Xs[c * h + i] = (i < hr && c < cols) ? X[(i0 + i) + (long)(cb + c) * ldx] : T(0);
@@ -224,22 +284,49 @@ __global__ void trail_right_tiled(T *__restrict__ X, long ldx, int M, int N, con
         __syncthreads();
 #pragma unroll U
         for (int c = 0; c < cols; ++c) {
-            T x[4];
+            T x[4], v[R];
             Vec4<T>::ld(Xs + c * h + 4 * cg, x);
             const T *vc = Vs + c * ldv_s + R * rg;
+            if constexpr (R % 4 == 0) {
 #pragma unroll
-            for (int i = 0; i < R; ++i) {
-                const T vi = vc[i];
+                for (int i = 0; i < R; i += 4) Vec4<T>::ld(vc + i, v + i);
+            } else {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += vi * x[j];
+                for (int i = 0; i < R; ++i) v[i] = vc[i];
             }
+#pragma unroll
+            for (int i = 0; i < R; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += v[i] * x[j];
         }
         __syncthreads();
     }
 #pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = 4 * cg + j;
+            if (r < hr) part[((size_t)s * nb + R * rg + i) * M + i0 + r] = acc[i][j];
+        }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sh_last = atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(S - 1);
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = 4 * cg + j;
+            T sum = T(0);
+            if (r < hr)
+                for (int q = 0; q < S; ++q) sum += __ldcg(part + ((size_t)q * nb + R * rg + i) * M + i0 + r);
+            acc[i][j] = sum;
+        }
+#pragma unroll
     for (int i = 0; i < R; ++i) Vec4<T>::st(Ys + (R * rg + i) * h + 4 * cg, acc[i]);
     __syncthreads();
-    // ---- step 2: Y <- Y T : Y'(r, kk) = sum_{k <= kk} Y(r, k) T(k, kk)
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         const int kk = R * rg + i;
@@ -252,121 +339,181 @@ __global__ void trail_right_tiled(T *__restrict__ X, long ldx, int M, int N, con
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] += t * yv[j];
         }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = 4 * cg + j;
+            if (r < hr) fin[(size_t)kk * M + i0 + r] = acc[i][j];
+        }
+    }
+    if (tid == 0) tickets[blockIdx.x] = 0u;
+}
+
+// Step 3: block (rb, cbk) updates the h x th tile X(rb, cbk) -= Y'(rb, :) V(cbk, :)^T.
+template <typename T, int U>
+__global__ void right_x_kernel(T *__restrict__ X, long ldx, int M, int N, const T *__restrict__ Vt, long ldvt, int nb,
+                               int th, int h, const T *__restrict__ fin) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *Xs = reinterpret_cast<T *>(smem_raw);  // th columns x h rows
+    T *Vs = Xs + (size_t)th * h;             // nb x th, k-major
+    T *Ys = Vs + (size_t)th * (nb + 4);      // nb x h
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int ncg = h >> 2, cg = tid % ncg, rg = tid / ncg, nrg = nt / ncg;
+    const int i0 = blockIdx.x * h, hr = min(h, M - i0);
+    const int cb = blockIdx.y * th, cols = min(th, N - cb);
+    for (int idx = tid; idx < th * h; idx += nt) {
+        int i = idx % h, c = idx / h;
+        Xs[c * h + i] = (i < hr && c < cols) ? X[(i0 + i) + (long)(cb + c) * ldx] : T(0);
+    }
+    for (int idx = tid; idx < th * nb; idx += nt) {
+        int k = idx % nb, c = idx / nb, gc = cb + c;
+        T v = T(0);
+        if (c < cols) v = gc > k ? Vt[k + (long)gc * ldvt] : (gc == k ? T(1) : T(0));
+        Vs[k * th + c] = v;
+    }
+    for (int idx = tid; idx < nb * h; idx += nt) {
+        int i = idx % h, k = idx / h;
+        Ys[k * h + i] = i < hr ? fin[(size_t)k * M + i0 + i] : T(0);
     }
     __syncthreads();
-#pragma unroll
-    for (int i = 0; i < R; ++i) Vec4<T>::st(Ys + (R * rg + i) * h + 4 * cg, acc[i]);
-    __syncthreads();
-    // ---- step 3: X_strip -= Y' V^T  (thread: rows 4cg..4cg+3, columns rg*cpt .. +cpt)
     const int cpt = th / nrg;
-    for (int cb = 0; cb < N; cb += th) {
-        const int cols = min(th, N - cb);
-        for (int idx = tid; idx < th * h; idx += nt) {
-            int i = idx % h, c = idx / h;
-            Xs[c * h + i] = (i < hr && c < cols) ? X[(i0 + i) + (long)(cb + c) * ldx] : T(0);
-        }
-        for (int idx = tid; idx < th * nb; idx += nt) {
-            int k = idx % nb, c = idx / nb, gc = cb + c;
-            T v = T(0);
-            if (c < cols) v = gc > k ? Vt[k + (long)gc * ldvt] : (gc == k ? T(1) : T(0));
-            Vs[k * th + c] = v;  // k-major
-        }
-        __syncthreads();
-        for (int cbl = rg * cpt; cbl < rg * cpt + cpt; cbl += 4) {
-            T s[4][4];  // s[column a][row j]
+    for (int cbl = rg * cpt; cbl < rg * cpt + cpt; cbl += 4) {
+        T sacc[4][4];  // [column a][row j]
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sacc[a][j] = T(0);
+#pragma unroll U
+        for (int k = 0; k < nb; ++k) {
+            T v[4], yv[4];
+            Vec4<T>::ld(Vs + k * th + cbl, v);
+            Vec4<T>::ld(Ys + k * h + 4 * cg, yv);
 #pragma unroll
             for (int a = 0; a < 4; ++a)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) s[a][j] = T(0);
-#pragma unroll U
-            for (int k = 0; k < nb; ++k) {
-                T v[4], yv[4];
-                Vec4<T>::ld(Vs + k * th + cbl, v);
-                Vec4<T>::ld(Ys + k * h + 4 * cg, yv);
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) s[a][j] += v[a] * yv[j];
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                T *p = Xs + (cbl + a) * h + 4 * cg;
-                T x[4];
-                Vec4<T>::ld(p, x);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) x[j] -= s[a][j];
-                Vec4<T>::st(p, x);
-            }
+                for (int j = 0; j < 4; ++j) sacc[a][j] += v[a] * yv[j];
         }
-        __syncthreads();
-        for (int idx = tid; idx < th * h; idx += nt) {
-            int i = idx % h, c = idx / h;
-            if (i < hr && c < cols) X[(i0 + i) + (long)(cb + c) * ldx] = Xs[c * h + i];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            T *p = Xs + (cbl + a) * h + 4 * cg;
+            T x[4];
+            Vec4<T>::ld(p, x);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) x[j] -= sacc[a][j];
+            Vec4<T>::st(p, x);
         }
-        __syncthreads();
+    }
+    __syncthreads();
+    for (int idx = tid; idx < th * h; idx += nt) {
+        int i = idx % h, c = idx / h;
+        if (i < hr && c < cols) X[(i0 + i) + (long)(cb + c) * ldx] = Xs[c * h + i];
     }
 }
 
 // -------------------------------------------------------------------- dispatch
+constexpr int kMaxSplit = 8;
+
+size_t tiled_scratch_elems(int M, int N) { return (size_t)(kMaxSplit + 1) * 64 * (size_t)std::max(std::max(M, N), 1); }
+size_t tiled_tickets(int M, int N) { return (size_t)std::max(M, N) / 32 + 2; }
+
+// number of splits of the long dimension L for `nblk` strips: about three waves
+static int split_count(int L, int th, int nblk) {
+    int S = (3 * device_sm_count() + nblk - 1) / std::max(nblk, 1);
+    S = std::max(1, std::min({S, kMaxSplit, (L + th - 1) / th}));
+    return S;
+}
+
+// Allow the kernel the opt-in shared-memory maximum minus its static shared memory.
+template <typename K>
+static void set_smem_attr(K kernel, bool &done) {
+    if (!done) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa;
+        size_t stat = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)optin - stat));
+        cudaGetLastError();
+        done = true;
+    }
+}
+
 template <typename T, int R, int U>
 static cudaError_t run_tiled(int side, T *X, long ldx, int M, int N, const T *V, long ldv, int nb, const T *Tm,
-                             const UpdCfg &c, size_t smem, cudaStream_t st) {
-    const int w = 32 * c.cpb;
+                             const UpdCfg &c, size_t smem, const UpdScratch &sc, cudaStream_t st) {
+    const int w = 32 * c.cpb, th = c.tile;
+    T *part = reinterpret_cast<T *>(sc.work);
+    T *fin = part + (size_t)kMaxSplit * 64 * std::max(M, N);
     if (side == 0) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(trail_left_tiled<T, R, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kTiledSmemLimit);
-            attr = true;
-        }
-        trail_left_tiled<T, R, U><<<(N + w - 1) / w, c.threads, smem, st>>>(X, ldx, M, N, V, ldv, nb, Tm, c.tile, w);
+        static bool a1 = false, a3 = false;
+        set_smem_attr(left_w_kernel<T, R, U>, a1);
+        set_smem_attr(left_x_kernel<T, U>, a3);
+        const int nblk = (N + w - 1) / w;
+        int S = split_count(M, th, nblk);
+        const int Ms = ((M + S - 1) / S + th - 1) / th * th;
+        S = (M + Ms - 1) / Ms;
+        left_w_kernel<T, R, U><<<dim3(nblk, S), c.threads, smem, st>>>(X, ldx, M, N, V, ldv, nb, Tm, th, w, Ms, part,
+                                                                       fin, sc.tickets);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        left_x_kernel<T, U><<<dim3(nblk, (M + th - 1) / th), c.threads, smem, st>>>(X, ldx, M, N, V, ldv, nb, th, w,
+                                                                                   fin);
     } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(trail_right_tiled<T, R, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kTiledSmemLimit);
-            attr = true;
-        }
-        trail_right_tiled<T, R, U><<<(M + w - 1) / w, c.threads, smem, st>>>(X, ldx, M, N, V, ldv, nb, Tm, c.tile, w);
+        static bool a1 = false, a3 = false;
+        set_smem_attr(right_w_kernel<T, R, U>, a1);
+        set_smem_attr(right_x_kernel<T, U>, a3);
+        const int nblk = (M + w - 1) / w;
+        int S = split_count(N, th, nblk);
+        const int Ns = ((N + S - 1) / S + th - 1) / th * th;
+        S = (N + Ns - 1) / Ns;
+        right_w_kernel<T, R, U><<<dim3(nblk, S), c.threads, smem, st>>>(X, ldx, M, N, V, ldv, nb, Tm, th, w, Ns, part,
+                                                                        fin, sc.tickets);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        right_x_kernel<T, U><<<dim3(nblk, (N + th - 1) / th), c.threads, smem, st>>>(X, ldx, M, N, V, ldv, nb, th, w,
+                                                                                    fin);
     }
     return cudaGetLastError();
 }
 
 template <typename T, int R>
 static cudaError_t run_tiled_u(int side, T *X, long ldx, int M, int N, const T *V, long ldv, int nb, const T *Tm,
-                               const UpdCfg &c, size_t smem, cudaStream_t st) {
+                               const UpdCfg &c, size_t smem, const UpdScratch &sc, cudaStream_t st) {
     switch (c.unroll) {
-        case 1: return run_tiled<T, R, 1>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, st);
-        case 2: return run_tiled<T, R, 2>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, st);
-        default: return run_tiled<T, R, 4>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, st);
+        case 1: return run_tiled<T, R, 1>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, sc, st);
+        case 2: return run_tiled<T, R, 2>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, sc, st);
+        default: return run_tiled<T, R, 4>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, sc, st);
     }
 }
 
 template <typename T>
 cudaError_t trail_tiled(int side, T *X, long ldx, int M, int N, const T *V, long ldv, int nb, const T *Tm,
-                        const UpdCfg &c, cudaStream_t st) {
+                        const UpdCfg &c, const UpdScratch &sc, cudaStream_t st) {
     const int R = tiled_r(nb, c);
-    if (!R) return cudaErrorInvalidConfiguration;
+    if (!R || !sc.work || !sc.tickets) return cudaErrorInvalidConfiguration;
     const size_t smem = tiled_smem(side, (int)sizeof(T), nb, c.tile, 32 * c.cpb);
     if (smem > kTiledSmemLimit) return cudaErrorInvalidConfiguration;
     switch (R) {
-        case 1: return run_tiled_u<T, 1>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, st);
-        case 2: return run_tiled_u<T, 2>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, st);
-        case 4: return run_tiled_u<T, 4>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, st);
-        default: return run_tiled_u<T, 8>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, st);
+        case 1: return run_tiled_u<T, 1>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, sc, st);
+        case 2: return run_tiled_u<T, 2>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, sc, st);
+        case 4: return run_tiled_u<T, 4>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, sc, st);
+        default: return run_tiled_u<T, 8>(side, X, ldx, M, N, V, ldv, nb, Tm, c, smem, sc, st);
     }
 }
 
-template <typename T, int R, int U>
-static int max_threads_one(int side) {
+template <typename K>
+static int kernel_max_threads(K kernel) {
     cudaFuncAttributes fa;
-    cudaError_t e = side == 0 ? cudaFuncGetAttributes(&fa, trail_left_tiled<T, R, U>)
-                              : cudaFuncGetAttributes(&fa, trail_right_tiled<T, R, U>);
-    if (e != cudaSuccess) {
+    if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
     return fa.maxThreadsPerBlock;
+}
+
+template <typename T, int R, int U>
+static int max_threads_one(int side) {
+    if (side == 0) return std::min(kernel_max_threads(left_w_kernel<T, R, U>), kernel_max_threads(left_x_kernel<T, U>));
+    return std::min(kernel_max_threads(right_w_kernel<T, R, U>), kernel_max_threads(right_x_kernel<T, U>));
 }
 
 template <typename T, int R>
@@ -398,8 +545,8 @@ int tiled_max_threads(int side, int elem, int R, int unroll) {
 }
 
 template cudaError_t trail_tiled<double>(int, double *, long, int, int, const double *, long, int, const double *,
-                                         const UpdCfg &, cudaStream_t);
+                                         const UpdCfg &, const UpdScratch &, cudaStream_t);
 template cudaError_t trail_tiled<float>(int, float *, long, int, int, const float *, long, int, const float *,
-                                        const UpdCfg &, cudaStream_t);
+                                        const UpdCfg &, const UpdScratch &, cudaStream_t);
 
 }  // namespace nla

@@ -59,14 +59,15 @@ _popts = ctypes.POINTER(Opts)
 _SIGNATURES = {
     "nla_gesvd_vals_workspace": [_i, _i, _i, _popts, _psz],
     "nla_gesvd_vals": [_i, _i, _i, _vp, _i, _vp, _vp, _sz, _vp, _popts, _vp],
-    "nla_gesvd_vals_batched_workspace": [_i, _i, _vp, _vp, _psz],
-    "nla_gesvd_vals_batched": [_i, _i, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp, _popts, _vp],
+    "nla_gesvd_vals_batched_workspace": [_i, _i, _i, _i, _psz],
+    "nla_gesvd_vals_batched": [_i, _i, _vp, _vp, _vp, _vp, _vp, _i, _i, _vp, _sz, _vp, _popts, _vp],
     "nla_gebrd_band_workspace": [_i, _i, _i, _i, _popts, _psz],
     "nla_gebrd_band": [_i, _i, _i, _i, _vp, _i, _vp, _vp, _vp, _sz, _vp, _popts, _vp],
     "nla_band_extract": [_i, _i, _i, _vp, _i, _vp, _i, _vp],
     "nla_band2bd_workspace": [_i, _i, _i, _psz],
     "nla_band2bd": [_i, _i, _i, _vp, _i, _vp, _vp, _vp, _sz, _vp, _popts, _vp],
-    "nla_bdsvd_vals": [_i, _vp, _vp, _vp, _i, _vp, _vp],
+    "nla_bdsvd_vals_workspace": [_i, _psz],
+    "nla_bdsvd_vals": [_i, _vp, _vp, _vp, _i, _vp, _sz, _vp, _vp],
 }
 
 
@@ -172,6 +173,41 @@ def gesvd_vals(A, update=UPD_NATIVE, cfg=None, preserve_a=False, work=None, S=No
     return S, info
 
 
+class Batch:
+    """Device-side description of a batch of FP32 matrices for gesvd_vals_batched.
+
+    ``mats`` is a list of CUDA float32 tensors; each is handed over as the
+    column-major matrix it holds in memory (see col_major_view)."""
+
+    def __init__(self, mats, device="cuda"):
+        import torch
+
+        views = [col_major_view(a) for a in mats]
+        self.mats = mats
+        self.m = torch.tensor([v[0] for v in views], dtype=torch.int32, device=device)
+        self.n = torch.tensor([v[1] for v in views], dtype=torch.int32, device=device)
+        self.lda = torch.tensor([v[2] for v in views], dtype=torch.int32, device=device)
+        self.ptrs = torch.tensor([a.data_ptr() for a in mats], dtype=torch.int64, device=device)
+        self.S = [torch.empty(min(v[0], v[1]), dtype=torch.float32, device=device) for v in views]
+        self.sptrs = torch.tensor([s.data_ptr() for s in self.S], dtype=torch.int64, device=device)
+        self.info = torch.zeros(len(mats), dtype=torch.int32, device=device)
+        self.max_m = max([max(v[0], v[1]) for v in views] + [1])  # bounds max(m_i, n_i)
+        self.max_n = max([min(v[0], v[1]) for v in views] + [1])  # bounds min(m_i, n_i)
+        need = ctypes.c_size_t(0)
+        _check(lib().nla_gesvd_vals_batched_workspace(len(mats), F32, self.max_m, self.max_n, ctypes.byref(need)))
+        self.work = workspace(need.value, device)
+
+
+def gesvd_vals_batched(batch, stream=None):
+    """Singular values of every matrix of a Batch (one persistent launch); returns (list of S, info)."""
+    _check(lib().nla_gesvd_vals_batched(len(batch.mats), F32, _vp(batch.m.data_ptr()), _vp(batch.n.data_ptr()),
+                                        _vp(batch.lda.data_ptr()), _vp(batch.ptrs.data_ptr()),
+                                        _vp(batch.sptrs.data_ptr()), batch.max_m, batch.max_n,
+                                        _vp(batch.work.data_ptr()), batch.work.numel(), _vp(batch.info.data_ptr()),
+                                        None, _stream_ptr(stream)))
+    return batch.S, batch.info
+
+
 def gebrd_band(A, band, update=UPD_NATIVE, cfg=None, work=None, stream=None):
     """Stage 1 in place on the column-major m x n matrix A (m >= n).  Returns (tauq, taup, info)."""
     import torch
@@ -233,8 +269,11 @@ def bdsvd_vals(d, e, dtype=None, stream=None):
     info = torch.zeros(1, dtype=torch.int32, device=d.device)
     dt = F64 if dtype == torch.float64 else F32
     e_ptr = e.data_ptr() if e.numel() else d.data_ptr()
-    _check(lib().nla_bdsvd_vals(n, _vp(d.data_ptr()), _vp(e_ptr), _vp(S.data_ptr()), dt, _vp(info.data_ptr()),
-                                _stream_ptr(stream)))
+    need = ctypes.c_size_t(0)
+    _check(lib().nla_bdsvd_vals_workspace(n, ctypes.byref(need)))
+    work = workspace(need.value, d.device)
+    _check(lib().nla_bdsvd_vals(n, _vp(d.data_ptr()), _vp(e_ptr), _vp(S.data_ptr()), dt, _vp(work.data_ptr()),
+                                work.numel(), _vp(info.data_ptr()), _stream_ptr(stream)))
     return S[:n], info
 
 
