@@ -151,6 +151,23 @@ nla_status nla_band2bd(int n, int band, nla_dtype dtype, void *dAB, int ldab, do
                        double *dE, void *dWork, size_t work_bytes, int *dInfo,
                        const nla_opts *opts, nla_stream_t stream);
 
+/* nla_band2bd without a workspace, for callers that cannot allocate device
+ * memory: code issuing work while its stream is captured into a CUDA graph
+ * (cudaMalloc cannot be captured), code that must never synchronise the
+ * device, and programs whose memory manager owns all device memory.  The paper
+ * has no counterpart; this is a library convenience.  Same arguments, layout
+ * and results as nla_band2bd, but the sweep-progress scratch is a fixed
+ * array inside the library (65536 ints = 256 KiB per GPU that loads the
+ * library, held until the process exits), so n may not exceed 65536
+ * (NLA_ERR_UNSUPPORTED otherwise).  It allocates nothing: the first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current -- make that first call before any stream capture.  Every
+ * call clears the counters it uses on its stream; all calls share the one
+ * array, so calls that could overlap on the GPU (unordered streams) race and
+ * must not be issued. */
+nla_status nla_band2bd_noalloc(int n, int band, nla_dtype dtype, void *dAB, int ldab, double *dD,
+                               double *dE, int *dInfo, nla_stream_t stream);
+
 /* Stage 3: singular values of the upper bidiagonal (dD, dE) by bisection on
  * Sturm counts of the Golub-Kahan tridiagonal (coarse steps with FP32 counts,
  * final steps with FP64 counts); dS receives n values descending, converted to
