@@ -86,12 +86,13 @@ nla_status kt_tune(const kt_problem *problem, kt_strategy strategy, double budge
 
 /* Install a table of best configurations written by kt_write_table (or by
  * hand); nla_gesvd_vals consults it whenever opts->cfg is NULL, matching
- * dtype, update precision and side and taking the entry nearest in log size.
- * path NULL clears the table. */
+ * dtype, update precision and side and taking the entry nearest in log size;
+ * side-2 entries set the batched kernel's threads per matrix (cfg.band) for
+ * size bucket m (0..4).  path NULL clears the table. */
 nla_status kt_load_config(const char *path);
 
 /* Append the best configuration of a finished tuning to a table file:
- * side 0 = QR-side update, 1 = LQ-side update. */
+ * side 0 = QR-side update, 1 = LQ-side update, 2 = batched bucket m. */
 nla_status kt_write_table(const char *path, int side, int m, int n, nla_dtype dtype,
                           nla_update update, const nla_cfg *cfg, double ms);
 

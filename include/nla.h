@@ -121,6 +121,11 @@ nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *dM, con
                                   int max_m, int max_n, void *dWork, size_t work_bytes, int *dInfo,
                                   const nla_opts *opts, nla_stream_t stream);
 
+/* The launch configuration nla_gesvd_vals would use for this problem (after
+ * opts->cfg overrides, the tuned table and the defaults, and the adjustment
+ * to the band width actually used); side 0 = QR-side update, 1 = LQ side. */
+nla_status nla_plan_cfg(int m, int n, nla_dtype dtype, const nla_opts *opts, int side, nla_cfg *out);
+
 /* ---------------------------------------------------------------- stages */
 
 /* Stage 1 (Algorithm 1): reduce the column-major m x n matrix dA (m >= n) to

@@ -148,7 +148,7 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
         if constexpr (sizeof(T) == 8) {
             if (p.update != NLA_UPD_NATIVE) {
                 NLA_LAUNCH(nla::kTrTrailLeft, st, nla::trail_left_tc(X + kb + (long)c0 * ldx, ldx, M - kb, N - c0, panel, ldx, nb, Tq,
-                                            p.update, dInfo, st),
+                                            p.update, usc, dInfo, st),
                          "QR trailing update (tensor core)");
             } else {
                 NLA_LAUNCH(nla::kTrTrailLeft, st, nla::trail_left<T>(X + kb + (long)c0 * ldx, ldx, M - kb, N - c0, panel, ldx, nb, Tq,
@@ -167,7 +167,7 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
             T *Xr = X + c0 + (long)c0 * ldx;
             if constexpr (sizeof(T) == 8) {
                 if (p.update != NLA_UPD_NATIVE) {
-                    NLA_LAUNCH(nla::kTrTrailRight, st, nla::trail_right_tc(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.update, dInfo, st),
+                    NLA_LAUNCH(nla::kTrTrailRight, st, nla::trail_right_tc(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.update, usc, dInfo, st),
                              "LQ trailing update (tensor core)");
                     continue;
                 }
@@ -329,6 +329,18 @@ nla_status nla_gesvd_vals(int m, int n, nla_dtype dtype, void *dA, int lda, void
     if (dtype == NLA_F64)
         return gesvd_impl<double>(m, n, dtype, (double *)dA, lda, (double *)dS, L, p, opts, dInfo, st);
     return gesvd_impl<float>(m, n, dtype, (float *)dA, lda, (float *)dS, L, p, opts, dInfo, st);
+}
+
+nla_status nla_plan_cfg(int m, int n, nla_dtype dtype, const nla_opts *opts, int side, nla_cfg *out) {
+    if (!out || (side != 0 && side != 1)) return fail(NLA_ERR_ARG, "bad arguments");
+    nla_status s = check_common(dtype, opts);
+    if (s != NLA_OK) return s;
+    if (m < 0 || n < 0) return fail(NLA_ERR_ARG, "negative size");
+    const int M = std::max(m, n), N = std::min(m, n);
+    Stage1Plan p = make_plan(M, N, dtype, opts, 0);
+    const nla::UpdCfg &u = side == 0 ? p.left : p.right;
+    *out = nla_cfg{p.b, u.tile, u.threads, u.cpb, u.unroll};
+    return NLA_OK;
 }
 
 nla_status nla_gebrd_band_workspace(int m, int n, int band, nla_dtype dtype, const nla_opts *opts,

@@ -238,6 +238,192 @@ band2bd_kernel(T *AB, long ldab, int n, int b, int *progress, int *info) {
     }
 }
 
+// ------------------------------------------------------------------ grouped bulge chasing
+// A block runs a group of G consecutive sweeps s0 .. s0+G-1, one warp per
+// sweep, on a window of band columns held in shared memory (columns stored
+// circularly, the same 3b+1 storage rows per column).  At wavefront step tau,
+// warp i performs block step k = tau - 3i of its sweep: the footprints of the
+// G warps are disjoint and each warp trails the previous one by the three
+// steps the dependency needs, so one __syncthreads per tau orders them.
+// Columns that no sweep of the group will touch again are written back to
+// global memory and announced in done[group] ("every column < value is
+// final"); the next group waits (bounded spin) until the columns it loads are
+// final.  The window spans at most (3G-1) b + G + 1 columns.
+template <typename T>
+struct Win {
+    T *w;
+    int ldw, wc, b2;
+    NLA_DEV T &at(int i, int j) const { return w[(b2 + i - j) + (j % wc) * ldw]; }
+};
+
+// One block step (right + left reflector) of sweep s at position k by one warp.
+template <typename T>
+NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) {
+    const int lane = threadIdx.x & 31;
+    const int c0 = s + k * b + 1;
+    const int tr = (k == 0) ? s : s + (k - 1) * b + 1;
+    const int c1 = min(s + (k + 1) * b, n - 1);
+    const int cend = min(s + (k + 2) * b, n - 1);
+    const int L = c1 - c0 + 1;
+    if (L < 2) return;
+    // ---- right reflector on columns c0..c1 from row tr, applied to rows tr+1..c1
+    T part = T(0);
+    for (int c = 1 + lane; c < L; c += 32) {
+        T x = W.at(tr, c0 + c);
+        part += x * x;
+    }
+    T xn2 = warp_sum(part);
+    T alpha = W.at(tr, c0);
+    T tau = T(0), beta = alpha, scale = T(0);
+    if (xn2 > T(0)) {
+        T r = sqrt(alpha * alpha + xn2);
+        beta = alpha >= T(0) ? -r : r;
+        tau = (beta - alpha) / beta;
+        scale = T(1) / (alpha - beta);
+    }
+    if (tau != T(0)) {
+        for (int c = lane; c < L; c += 32) v[c] = c == 0 ? T(1) : W.at(tr, c0 + c) * scale;
+        __syncwarp();
+        for (int c = lane; c < L; c += 32) W.at(tr, c0 + c) = c == 0 ? beta : T(0);
+        for (int i = tr + 1 + lane; i <= c1; i += 32) {  // one lane per row
+            T w = T(0);
+            for (int c = 0; c < L; ++c) w += W.at(i, c0 + c) * v[c];
+            w *= tau;
+            for (int c = 0; c < L; ++c) W.at(i, c0 + c) -= w * v[c];
+        }
+        __syncwarp();
+    }
+    // ---- left reflector on rows c0..c1 from column c0, applied to columns c0+1..cend
+    part = T(0);
+    for (int r = 1 + lane; r < L; r += 32) {
+        T x = W.at(c0 + r, c0);
+        part += x * x;
+    }
+    xn2 = warp_sum(part);
+    alpha = W.at(c0, c0);
+    tau = T(0), beta = alpha, scale = T(0);
+    if (xn2 > T(0)) {
+        T r = sqrt(alpha * alpha + xn2);
+        beta = alpha >= T(0) ? -r : r;
+        tau = (beta - alpha) / beta;
+        scale = T(1) / (alpha - beta);
+    }
+    if (tau != T(0)) {
+        for (int r = lane; r < L; r += 32) v[r] = r == 0 ? T(1) : W.at(c0 + r, c0) * scale;
+        __syncwarp();
+        for (int r = lane; r < L; r += 32) W.at(c0 + r, c0) = r == 0 ? beta : T(0);
+        for (int j = c0 + 1 + lane; j <= cend; j += 32) {  // one lane per column
+            T w = T(0);
+            for (int r = 0; r < L; ++r) w += v[r] * W.at(c0 + r, j);
+            w *= tau;
+            for (int r = 0; r < L; ++r) W.at(c0 + r, j) -= w * v[r];
+        }
+        __syncwarp();
+    }
+}
+
+// Window of the group [s0, s0+g) at wavefront step tau: columns [lo, hi].  lo
+// is the first column any unfinished sweep will still touch (a sweep that has
+// not started yet will start at column s+1), hi the last column a running
+// sweep touches now.  active = some sweep of the group is unfinished.
+NLA_DEV void group_need(int n, int b, int s0, int g, int tau, int &lo, int &hi, bool &active) {
+    lo = n;
+    hi = -1;
+    active = false;
+    for (int i = 0; i < g; ++i) {
+        const int s = s0 + i, k = tau - 3 * i;
+        if (s >= n - 2) continue;
+        if (k < 0) {  // not started yet
+            active = true;
+            lo = min(lo, s + 1);
+            continue;
+        }
+        const int c0 = s + k * b + 1;
+        if (c0 > n - 1) continue;  // finished
+        active = true;
+        lo = min(lo, c0);
+        hi = max(hi, min(s + (k + 2) * b, n - 1));
+    }
+}
+
+template <typename T>
+__global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int wc, int *done, int *info) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int sh_fail;
+    const int ldw = (3 * b + 2) & ~1;  // even: lanes walking a row hit distinct banks
+    Win<T> W{reinterpret_cast<T *>(smem_raw), ldw, wc, 2 * b};
+    T *vbase = W.w + (size_t)wc * ldw;  // 64 entries per warp
+    const int tid = threadIdx.x, warp = tid >> 5;
+    T *v = vbase + warp * 64;
+    Band<T> A{AB, ldab, 2 * b};
+    const int nsweeps = n - 2;
+    const int ngroups = (nsweeps + G - 1) / G;
+    if (tid == 0) sh_fail = 0;
+    __syncthreads();
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int s0 = grp * G, g = min(G, nsweeps - s0);
+        int loaded_hi = -1, flushed_lo = -1;  // window holds columns [flushed_lo+1 .. loaded_hi]
+        for (int tau = 0;; ++tau) {
+            int lo, hi;
+            bool active;
+            group_need(n, b, s0, g, tau, lo, hi, active);
+            if (!active) break;
+            if (flushed_lo < 0) flushed_lo = lo - 1, loaded_hi = lo - 1;  // first step: nothing cached yet
+            // write back columns the group no longer touches, then announce them
+            if (lo - 1 > flushed_lo) {
+                for (int j = flushed_lo + 1; j < lo; ++j)
+                    for (int q = tid; q < 3 * b + 1; q += blockDim.x) {
+                        const int i = j + q - 2 * b;
+                        if (i >= 0 && i < n) __stcg(A.at(i, j), W.at(i, j));
+                    }
+                flushed_lo = lo - 1;
+                __threadfence();
+                __syncthreads();
+                if (tid == 0) st_release(&done[grp], lo);
+            }
+            // load newly needed columns once the previous group has finished with them
+            if (hi > loaded_hi) {
+                if (grp > 0) {
+                    if (tid == 0 && !spin_until_geq(&done[grp - 1], hi + 1, info, 64)) sh_fail = 1;
+                    __syncthreads();
+                    if (sh_fail) return;
+                }
+                for (int j = loaded_hi + 1; j <= hi; ++j)
+                    for (int q = tid; q < 3 * b + 1; q += blockDim.x) {
+                        const int i = j + q - 2 * b;
+                        if (i >= 0 && i < n) W.at(i, j) = __ldcg(A.at(i, j));
+                    }
+                loaded_hi = hi;
+            }
+            __syncthreads();
+            if (warp < g) {
+                const int s = s0 + warp, k = tau - 3 * warp;
+                if (s < nsweeps && k >= 0 && s + k * b + 1 <= n - 1) warp_chase_step<T>(W, n, b, s, k, v);
+            }
+            __syncthreads();
+        }
+        // flush what is left and release the whole band to the next group
+        for (int j = flushed_lo + 1; j <= loaded_hi; ++j)
+            for (int q = tid; q < 3 * b + 1; q += blockDim.x) {
+                const int i = j + q - 2 * b;
+                if (i >= 0 && i < n) __stcg(A.at(i, j), W.at(i, j));
+            }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) st_release(&done[grp], INT_MAX);
+    }
+}
+
+// Sweeps per block group that fit the shared-memory window, or 0 if none.
+static int chase_group_size(int b, int elem, size_t budget) {
+    const size_t ldw = (size_t)((3 * b + 2) & ~1);
+    for (int G = 16; G >= 1; --G) {
+        const size_t wc = (size_t)(3 * G - 1) * b + G + 1;
+        if (wc * ldw * elem + (size_t)G * 64 * elem <= budget) return G;
+    }
+    return 0;
+}
+
 template <typename T>
 __global__ void bidiag_extract_kernel(const T *__restrict__ AB, long ldab, int n, int b, double *d, double *e) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -252,7 +438,34 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
     if (n <= 0) return cudaSuccess;
     int *progress = reinterpret_cast<int *>(scratch);
     const int nsweeps = n - 2;
-    if (nsweeps > 0 && b > 1) {
+    const size_t kGroupBudget = 200 * 1024;
+    const int G = chase_group_size(b, (int)sizeof(T), kGroupBudget);
+    if (nsweeps > 0 && b > 1 && G >= 1) {
+        const int ngroups = (nsweeps + G - 1) / G;
+        cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)ngroups, st);
+        if (err != cudaSuccess) return err;
+        static bool gattr = false;
+        if (!gattr) {
+            cudaFuncSetAttribute(band2bd_group_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kGroupBudget);
+            gattr = true;
+        }
+        const int wc = (3 * G - 1) * b + G + 1;
+        const size_t smem = (size_t)wc * ((3 * b + 2) & ~1) * sizeof(T) + (size_t)G * 64 * sizeof(T);
+        const int grid = std::min(ngroups, device_sm_count());
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(32 * G);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        err = cudaLaunchKernelEx(&cfg, band2bd_group_kernel<T>, AB, ldab, n, b, G, wc, progress, info);
+        if (err != cudaSuccess) return err;
+    } else if (nsweeps > 0 && b > 1) {
         cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)nsweeps, st);
         if (err != cudaSuccess) return err;
         static bool smem_attr = false;

@@ -129,12 +129,12 @@ __device__ int count_below_f(int n, const float *d, const float *e, float x, flo
     float q = -x;
     int neg = q < 0.f;
     for (int i = 0; i < n; ++i) {
-        if (fabsf(q) < pivmin) q = -pivmin;
         q = -x - d[i] * d[i] / q;
+        if (fabsf(q) < pivmin) q = -pivmin;  // floor first, then count the sign used
         neg += q < 0.f;
         if (i + 1 < n) {
-            if (fabsf(q) < pivmin) q = -pivmin;
             q = -x - e[i] * e[i] / q;
+            if (fabsf(q) < pivmin) q = -pivmin;
             neg += q < 0.f;
         }
     }

@@ -8,22 +8,28 @@
 // of singular values below x is negcount(TGK - x I) - n, where negcount counts
 // the negative pivots of the LDL^T factorisation of TGK - x I (Sylvester's law
 // of inertia): q_1 = -x, q_i = -x - t_{i-1}^2 / q_{i-1}; a pivot smaller than
-// pivmin in magnitude is replaced by -pivmin.
+// pivmin in magnitude is replaced by -pivmin before its sign is counted, so the
+// count stays monotone in x.
 //
 // GB300's FP64 pipe issues a small fraction of the FP32 rate, and an IEEE FP64
 // division costs many FP64 issue slots, so the search is split:
 //   prep:   B is scaled by a power of two so its Gershgorin bound is <= 1
 //           (exact), and the squares t_i^2 are stored once in FP64 and FP32;
-//   coarse: bisection with FP32 Sturm counts until the bracket is 2^-16 wide.
-//           An FP32 count is the exact count of a matrix whose entries differ
+//   coarse: multisection with FP32 Sturm counts.  A group of 8 lanes owns one
+//           value and counts at 8 interior points of its bracket per round, so
+//           a round shrinks the bracket 9-fold where bisection halves it.  An
+//           FP32 count is the exact count of a matrix whose entries differ
 //           relatively by a few FP32 rounding errors, so it can only misplace
-//           values within a few 2^-24 of x; the bracket is then widened by
-//           2^-18 on both sides, which keeps the value inside it;
-//   fine:   bisection with FP64 counts to the output resolution (2^-51 of the
-//           bound for FP64 output, 2^-27 for FP32).  The FP64 count forms
-//           1/q from an FP32 estimate and two Newton-Raphson corrections
-//           r <- r + r (1 - q r) (quadratic convergence: ~2^-22 -> 2^-44 ->
-//           below FP64 rounding), i.e. four FMAs instead of a division.
+//           values within a few 2^-24 of x (the scaled bound is 1).  For FP32
+//           output that is the answer: the reduction before it has the same
+//           absolute error level.  For FP64 output the coarse bracket stops at
+//           2^-16 and is widened by 2^-18 on both sides, which keeps the value
+//           inside it;
+//   fine:   (FP64 output) bisection with FP64 counts to 2^-51 of the bound, one
+//           thread per value.  The FP64 count forms 1/q from an FP32 estimate
+//           and two Newton-Raphson corrections r <- r + r (1 - q r) (quadratic
+//           convergence: ~2^-22 -> 2^-44 -> below FP64 rounding), i.e. four
+//           FMAs instead of a division.
 #include <cfloat>
 
 #include "common.cuh"
@@ -31,13 +37,15 @@
 
 namespace nla {
 
-constexpr int kBisectThreads = 128;
+constexpr int kBisectThreads = 32;  // fine phase: one warp per block spreads the FP64 work over all SMs
+constexpr int kMsLanes = 8;         // points per multisection round (one lane each)
+constexpr int kMsThreads = 128;
 constexpr double kPivminFine = 0x1p-100;   // pivot floor of the FP64 counts (scaled problem)
 constexpr float kPivminCoarse = 0x1p-60f;  // pivot floor of the FP32 counts
 
 size_t bdsvd_scratch_bytes(int n) {
     const size_t m = (size_t)(n > 0 ? 2 * n : 1);
-    return 256 + m * sizeof(double) + ((m * sizeof(float) + 255) / 256) * 256;
+    return 256 + m * sizeof(double) + ((m * sizeof(float) + 255) / 256) * 256 + (size_t)(n > 0 ? n : 1) * 8;
 }
 
 // One block: Gershgorin bound, power-of-two scale, squared scaled off-diagonals.
@@ -77,8 +85,8 @@ NLA_DEV int count_coarse(int n2, const float *__restrict__ t2f, float x) {
     float q = -x;
     int neg = q < 0.f;
     for (int i = 0; i < n2; ++i) {
-        if (fabsf(q) < kPivminCoarse) q = -kPivminCoarse;
         q = -x - __fdividef(__ldg(t2f + i), q);
+        if (fabsf(q) < kPivminCoarse) q = -kPivminCoarse;  // floor first, then count the sign used
         neg += q < 0.f;
     }
     return neg;
@@ -96,32 +104,61 @@ NLA_DEV int count_fine(int n2, const double *__restrict__ t2, double x) {
     double q = -x;
     int neg = q < 0.0;
     for (int i = 0; i < n2; ++i) {
-        if (fabs(q) < kPivminFine) q = -kPivminFine;
         q = fma(-__ldg(t2 + i), recip_nr(q), -x);
+        if (fabs(q) < kPivminFine) q = -kPivminFine;
         neg += q < 0.0;
     }
     return neg;
 }
 
+// Multisection with FP32 counts on [0, 1]: group g of kMsLanes lanes finds the
+// g-th largest value.  Invariant: count(lo) - n <= j < count(hi) - n, i.e. the
+// j-th smallest value lies in [lo, hi).  Each round every lane counts at its
+// own interior point; the bracket becomes the first interval of consecutive
+// points over which the count passes j.
+template <typename T>
+__global__ void __launch_bounds__(kMsThreads)
+coarse_kernel(int n, const double *__restrict__ hdr, const float *__restrict__ t2f, float stop,
+              float2 *__restrict__ br, T *__restrict__ S) {
+    const int idx = (blockIdx.x * blockDim.x + threadIdx.x) / kMsLanes;
+    const int l = threadIdx.x % kMsLanes;
+    const int gbase = (threadIdx.x & 31) & ~(kMsLanes - 1);
+    const unsigned gmask = ((1u << kMsLanes) - 1) << gbase;
+    if (idx >= n) return;  // uniform over the group
+    const int n2 = 2 * n - 1;
+    const int j = n - 1 - idx;
+    const float frac = (float)(l + 1) * (1.0f / (kMsLanes + 1));
+    float lo = 0.f, hi = 1.f;
+    for (int round = 0; round < 64 && hi - lo > stop; ++round) {
+        const float x = fmaf(hi - lo, frac, lo);
+        const bool below = count_coarse(n2, t2f, x) - n <= j;
+        const unsigned m = (__ballot_sync(gmask, below) >> gbase) & ((1u << kMsLanes) - 1);
+        const int f = __ffs(~m) - 1;  // first point whose count passes j; kMsLanes if none
+        const float xf = __shfl_sync(gmask, x, gbase + min(f, kMsLanes - 1));
+        const float xp = __shfl_sync(gmask, x, gbase + max(f - 1, 0));
+        if (f < kMsLanes) hi = xf;
+        if (f > 0) lo = xp;
+    }
+    if (l == 0) {
+        if (S)
+            S[idx] = (T)(0.5 * ((double)lo + (double)hi) / hdr[0]);
+        else
+            br[idx] = make_float2(lo, hi);
+    }
+}
+
+// FP64 bisection from the widened coarse bracket, one thread per value.
 template <typename T>
 __global__ void __launch_bounds__(kBisectThreads)
-bisect_kernel(int n, const double *__restrict__ hdr, const double *__restrict__ t2, const float *__restrict__ t2f,
-              T *__restrict__ S, double fine_tol) {
+fine_kernel(int n, const double *__restrict__ hdr, const double *__restrict__ t2, const float2 *__restrict__ br,
+            T *__restrict__ S, double fine_tol) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= n) return;
     const double s = hdr[0];
     const int n2 = 2 * n - 1;
     const int j = n - 1 - idx;  // idx-th largest == j-th smallest; counts below x are negcount - n
-    // coarse FP32 bisection on [0, 1]
-    float lo = 0.f, hi = 1.f;
-    while (hi - lo > 0x1p-16f) {
-        const float mid = 0.5f * (lo + hi);
-        if (count_coarse(n2, t2f, mid) - n <= j)
-            lo = mid;
-        else
-            hi = mid;
-    }
-    double dlo = fmax(0.0, (double)lo - 0x1p-18), dhi = fmin(1.0, (double)hi + 0x1p-18);
+    const float2 b = br[idx];
+    double dlo = fmax(0.0, (double)b.x - 0x1p-18), dhi = fmin(1.0, (double)b.y + 0x1p-18);
     for (int it = 0; it < 80; ++it) {
         const double mid = 0.5 * (dlo + dhi);
         if (dhi - dlo <= fine_tol || mid <= dlo || mid >= dhi) break;
@@ -141,9 +178,16 @@ cudaError_t bdsvd_bisect(int n, const double *d, const double *e, T *S, void *sc
     double *hdr = reinterpret_cast<double *>(w);
     double *t2 = reinterpret_cast<double *>(w + 256);
     float *t2f = reinterpret_cast<float *>(w + 256 + (size_t)2 * n * sizeof(double));
+    float2 *br = reinterpret_cast<float2 *>(w + 256 + (size_t)2 * n * sizeof(double) +
+                                            (((size_t)2 * n * sizeof(float) + 255) / 256) * 256);
     bd_prep_kernel<<<1, 1024, 0, st>>>(n, d, e, hdr, t2, t2f);
-    const double tol = sizeof(T) == 8 ? 0x1p-51 : 0x1p-27;
-    bisect_kernel<T><<<(n + kBisectThreads - 1) / kBisectThreads, kBisectThreads, 0, st>>>(n, hdr, t2, t2f, S, tol);
+    const int cblocks = (int)(((long)n * kMsLanes + kMsThreads - 1) / kMsThreads);
+    if (sizeof(T) == 4) {
+        coarse_kernel<T><<<cblocks, kMsThreads, 0, st>>>(n, hdr, t2f, 0x1p-23f, nullptr, S);
+        return cudaGetLastError();
+    }
+    coarse_kernel<T><<<cblocks, kMsThreads, 0, st>>>(n, hdr, t2f, 0x1p-16f, br, nullptr);
+    fine_kernel<T><<<(n + kBisectThreads - 1) / kBisectThreads, kBisectThreads, 0, st>>>(n, hdr, t2, br, S, 0x1p-51);
     return cudaGetLastError();
 }
 

@@ -40,8 +40,9 @@ NLA_DEV void st_release(int *p, int v) {
 }
 
 // Spin until *p >= target or the budget runs out.  Called by one thread.
-// Returns true on success; on timeout records kInfoTimeout in *info.
-NLA_DEV bool spin_until_geq(const unsigned int *p, unsigned int target, int *info) {
+// Returns true on success; on timeout records kInfoTimeout in *info.  The
+// sleep between polls doubles from 32 ns up to max_backoff_ns.
+NLA_DEV bool spin_until_geq(const unsigned int *p, unsigned int target, int *info, unsigned max_backoff_ns = 256) {
     if (ld_acquire(p) >= target) return true;
     unsigned long long t0 = global_ns();
     unsigned int backoff = 32;
@@ -53,11 +54,11 @@ NLA_DEV bool spin_until_geq(const unsigned int *p, unsigned int target, int *inf
             return false;
         }
         __nanosleep(backoff);
-        if (backoff < 256) backoff <<= 1;
+        if (backoff < max_backoff_ns) backoff <<= 1;
     }
 }
 
-NLA_DEV bool spin_until_geq(const int *p, int target, int *info) {
+NLA_DEV bool spin_until_geq(const int *p, int target, int *info, unsigned max_backoff_ns = 256) {
     if (ld_acquire(p) >= target) return true;
     unsigned long long t0 = global_ns();
     unsigned int backoff = 32;
@@ -69,7 +70,7 @@ NLA_DEV bool spin_until_geq(const int *p, int target, int *info) {
             return false;
         }
         __nanosleep(backoff);
-        if (backoff < 256) backoff <<= 1;
+        if (backoff < max_backoff_ns) backoff <<= 1;
     }
 }
 

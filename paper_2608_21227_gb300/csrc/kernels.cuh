@@ -68,9 +68,9 @@ cudaError_t trail_right(T *X, long ldx, int M, int N, const T *Vt, long ldvt, in
 // Mixed precision (FP64 matrix, TF32 or BF16 tensor-core contraction).
 // prec: 1 = TF32, 2 = BF16; a bounded wait that gives up writes to *info.
 cudaError_t trail_left_tc(double *X, long ldx, int M, int N, const double *Vp, long ldv, int nb,
-                          const double *Tm, int prec, int *info, cudaStream_t st);
+                          const double *Tm, int prec, const UpdScratch &sc, int *info, cudaStream_t st);
 cudaError_t trail_right_tc(double *X, long ldx, int M, int N, const double *Vt, long ldvt,
-                           int nb, const double *Tm, int prec, int *info, cudaStream_t st);
+                           int nb, const double *Tm, int prec, const UpdScratch &sc, int *info, cudaStream_t st);
 size_t trail_tc_scratch_bytes(int M, int N, int nb);
 bool trail_tc_available();
 

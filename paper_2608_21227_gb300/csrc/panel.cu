@@ -20,16 +20,20 @@
 // Householder convention (LAPACK-style): beta = -sign(alpha) ||[alpha; x]||,
 // sign(0) = +1, tau = (beta - alpha) / beta; a zero x gives tau = 0, H = I.
 // Norms and the cross-block sums are FP64 in every precision mode.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "common.cuh"
 #include "kernels.cuh"
 
+namespace cg = cooperative_groups;
+
 namespace nla {
 
 constexpr int kPanelThreads = 256;
 constexpr int kNbMax = 64;
-constexpr int kPanelRowsTarget = 128;  // rows per block when the panel is long enough
+constexpr int kPanelRowsTarget = 256;  // rows per block when the panel is long enough
 
 size_t panel_part_doubles(int P) {
     return (size_t)2 * P * (kNbMax + 1) + (size_t)P * kNbMax * kNbMax + 2 * kNbMax;
@@ -59,7 +63,7 @@ panel_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, T *__res
     double *Ts = Gs + (size_t)nb * nb;
     __shared__ double red[kNbMax + 1];
     __shared__ double rowv[kNbMax + 1];
-    __shared__ double wcoef[kNbMax + 1];
+    __shared__ T wcoef[kNbMax + 1];
     __shared__ double sh_tau, sh_beta, sh_scale;
     __shared__ int sh_fail;
 
@@ -98,13 +102,10 @@ panel_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, T *__res
         const T *xj = S + (size_t)j * R;
         for (int it = warp; it < nitem; it += nwarps) {
             if (it == 0) {
-                double s = 0.0;
-                for (int rr = rr_lo + lane; rr < nr; rr += 32) {
-                    double x = (double)xj[rr];
-                    s += x * x;
-                }
+                T s = T(0);
+                for (int rr = rr_lo + lane; rr < nr; rr += 32) s += xj[rr] * xj[rr];
                 s = warp_sum(s);
-                if (lane == 0) cp[0] = s;
+                if (lane == 0) cp[0] = (double)s;
             } else {
                 const T *ac = S + (size_t)(j + it) * R;
                 T s = T(0);
@@ -120,18 +121,28 @@ panel_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, T *__res
         __syncthreads();
         if (tid == 0) {
             atomicAdd(bar, 1u);
-            if (!spin_until_geq(bar, (unsigned)(j + 1) * (unsigned)nP, info)) sh_fail = 1;
+            if (!spin_until_geq(bar, (unsigned)(j + 1) * (unsigned)nP, info, 32)) sh_fail = 1;
             __threadfence();
         }
         __syncthreads();
         if (sh_fail) return;
 
-        // fixed-order sum of the partials: deterministic across runs
-        for (int it = tid; it < nitem; it += blockDim.x) {
+        // fixed-order sum of the partials (deterministic across runs): each item is
+        // split over `sub` threads whose independent loads are in flight together
+        {
+            const int sub = nitem <= 32 ? 8 : 4;  // 256 threads cover up to 64 items
+            const int it = tid / sub, part = tid % sub;
             double s = 0.0;
-            for (int q = 0; q < nP; ++q) s += ld_cg(colpart + ((size_t)buf * nP + q) * (kNbMax + 1) + it);
-            red[it] = s;
-            rowv[it] = ld_cg(rowbuf + buf * kNbMax + it);
+            if (it < nitem) {
+                const double *base = colpart + (size_t)buf * nP * (kNbMax + 1) + it;
+#pragma unroll 8
+                for (int q = part; q < nP; q += sub) s += ld_cg(base + (size_t)q * (kNbMax + 1));
+            }
+            for (int o = sub >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, sub);
+            if (it < nitem && part == 0) {
+                red[it] = s;
+                rowv[it] = ld_cg(rowbuf + buf * kNbMax + it);
+            }
         }
         __syncthreads();
         if (tid == 0) {
@@ -150,17 +161,17 @@ panel_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, T *__res
         }
         __syncthreads();
         const double tj = sh_tau, sc = sh_scale;
-        for (int it = 1 + tid; it < nitem; it += blockDim.x) wcoef[it] = tj * (rowv[it] + sc * red[it]);
+        for (int it = 1 + tid; it < nitem; it += blockDim.x) wcoef[it] = (T)(tj * (rowv[it] + sc * red[it]));
         __syncthreads();
         if (tj != 0.0) {
             const T scT = (T)sc;
             for (int rr = rr_lo + tid; rr < nr; rr += blockDim.x) {
                 T v = S[(size_t)j * R + rr] * scT;  // reflector entry v_r
-                for (int c = j + 1; c < nb; ++c) S[(size_t)c * R + rr] -= v * (T)wcoef[c - j];
+                for (int c = j + 1; c < nb; ++c) S[(size_t)c * R + rr] -= v * wcoef[c - j];
                 S[(size_t)j * R + rr] = v;
             }
             if (j >= r0 && j < r0 + nr) {  // row j itself: v_j = 1
-                for (int c = j + 1 + tid; c < nb; c += blockDim.x) S[(size_t)c * R + (j - r0)] -= (T)wcoef[c - j];
+                for (int c = j + 1 + tid; c < nb; c += blockDim.x) S[(size_t)c * R + (j - r0)] -= wcoef[c - j];
                 if (tid == 0) S[(size_t)j * R + (j - r0)] = (T)sh_beta;
             }
         }
@@ -186,16 +197,15 @@ panel_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, T *__res
     for (int it = warp; it < nb * nb; it += nwarps) {
         int i = it / nb, k = it % nb;
         if (i >= k || k >= kmax) continue;
-        double s = 0.0;
-        for (int rr = lane; rr < nr; rr += 32) {
-            int r = r0 + rr;
+        T s = T(0);
+        for (int rr = (k > r0 ? ((k - r0) & ~31) : 0) + lane; rr < nr; rr += 32) {  // rows below k only
+            const int r = r0 + rr;
             if (r < k) continue;
-            double vk = (r == k) ? 1.0 : (double)S[(size_t)k * R + rr];
-            double vi = (double)S[(size_t)i * R + rr];  // r >= k > i: stored tail
-            s += vi * vk;
+            const T vk = (r == k) ? T(1) : S[(size_t)k * R + rr];
+            s += S[(size_t)i * R + rr] * vk;  // r >= k > i: stored tail
         }
         s = warp_sum(s);
-        if (lane == 0) gp[i * kNbMax + k] = s;
+        if (lane == 0) gp[i * kNbMax + k] = (double)s;
     }
     __threadfence();
     __syncthreads();
@@ -242,11 +252,246 @@ panel_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, T *__res
     }
 }
 
+// ------------------------------------------------------------------ cluster variant
+// Same algorithm with the panel spread over one thread-block cluster (up to 16
+// blocks on one GPC): the per-column partial sums live in each block's shared
+// memory, are read by every block through distributed shared memory, and the
+// hardware cluster barrier replaces the global counter barrier.
+template <typename T>
+__global__ void __launch_bounds__(kPanelThreads)
+panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, T *__restrict__ tau,
+                     T *__restrict__ Tm) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cg::cluster_group cluster = cg::this_cluster();
+    const int p = (int)cluster.block_rank(), nP = (int)cluster.num_blocks();
+    T *S = reinterpret_cast<T *>(smem_raw);  // R x nb
+    double *Gs = reinterpret_cast<double *>(smem_raw + (((size_t)R * nb * sizeof(T) + 15) & ~(size_t)15));
+    double *Ts = Gs + (size_t)nb * nb;
+    __shared__ double cpart[2][kNbMax + 1];  // this block's partial sums, double-buffered by column parity
+    __shared__ double rowb[2][kNbMax + 1];   // row j (owner block only)
+    __shared__ double red[kNbMax + 1], rowv[kNbMax + 1];
+    __shared__ T wcoef[kNbMax + 1];
+    __shared__ double sh_tau, sh_beta, sh_scale;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int r0 = p * R;
+    const int nr = max(0, min(M, r0 + R) - r0);
+    const int kmax = min(nb, M);
+    if (p == 0)
+        for (int j = kmax + tid; j < nb; j += blockDim.x) tau[j] = T(0);
+    if (cs == 1) {
+        for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
+            int c = idx % nb, rr = idx / nb;
+            S[(size_t)c * R + rr] = P[(long)(r0 + rr) * rs + c];
+        }
+    } else {
+        for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
+            int rr = idx % nr, c = idx / nr;
+            S[(size_t)c * R + rr] = P[(long)(r0 + rr) * rs + (long)c * cs];
+        }
+    }
+    __syncthreads();
+    for (int j = 0; j < kmax; ++j) {
+        const int buf = j & 1;
+        const int nitem = nb - j;
+        const int rr_lo = max(0, j + 1 - r0);
+        const T *xj = S + (size_t)j * R;
+        for (int it = warp; it < nitem; it += nwarps) {
+            double sacc;
+            if (it == 0) {
+                T s2 = T(0);
+                for (int rr = rr_lo + lane; rr < nr; rr += 32) s2 += xj[rr] * xj[rr];
+                sacc = (double)warp_sum(s2);
+            } else {
+                const T *ac = S + (size_t)(j + it) * R;
+                T s1 = T(0);
+                for (int rr = rr_lo + lane; rr < nr; rr += 32) s1 += xj[rr] * ac[rr];
+                sacc = (double)warp_sum(s1);
+            }
+            if (lane == 0) cpart[buf][it] = sacc;
+        }
+        const int owner = j / R;
+        if (p == owner)
+            for (int c = j + tid; c < nb; c += blockDim.x) rowb[buf][c - j] = (double)S[(size_t)c * R + (j - r0)];
+        cluster.sync();
+        // fixed-order sum over the cluster's blocks (deterministic)
+        for (int it = tid; it < nitem; it += blockDim.x) {
+            double sum = 0.0;
+            for (int q = 0; q < nP; ++q) sum += cluster.map_shared_rank(&cpart[buf][0], q)[it];
+            red[it] = sum;
+            rowv[it] = cluster.map_shared_rank(&rowb[buf][0], owner)[it];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double alpha = rowv[0], xn2 = red[0];
+            double tj = 0.0, beta = alpha, scale = 0.0;
+            if (xn2 > 0.0) {
+                double r = sqrt(alpha * alpha + xn2);
+                beta = alpha >= 0.0 ? -r : r;
+                tj = (beta - alpha) / beta;
+                scale = 1.0 / (alpha - beta);
+            }
+            sh_tau = tj;
+            sh_beta = beta;
+            sh_scale = scale;
+            if (p == 0) tau[j] = (T)tj;
+        }
+        __syncthreads();
+        const double tj = sh_tau, sc = sh_scale;
+        for (int it = 1 + tid; it < nitem; it += blockDim.x) wcoef[it] = (T)(tj * (rowv[it] + sc * red[it]));
+        __syncthreads();
+        if (tj != 0.0) {
+            const T scT = (T)sc;
+            for (int rr = rr_lo + tid; rr < nr; rr += blockDim.x) {
+                T v = S[(size_t)j * R + rr] * scT;
+                for (int c = j + 1; c < nb; ++c) S[(size_t)c * R + rr] -= v * wcoef[c - j];
+                S[(size_t)j * R + rr] = v;
+            }
+            if (p == owner) {
+                for (int c = j + 1 + tid; c < nb; c += blockDim.x) S[(size_t)c * R + (j - r0)] -= wcoef[c - j];
+                if (tid == 0) S[(size_t)j * R + (j - r0)] = (T)sh_beta;
+            }
+        }
+        __syncthreads();
+    }
+    if (cs == 1) {
+        for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
+            int c = idx % nb, rr = idx / nb;
+            P[(long)(r0 + rr) * rs + c] = S[(size_t)c * R + rr];
+        }
+    } else {
+        for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
+            int rr = idx % nr, c = idx / nr;
+            P[(long)(r0 + rr) * rs + (long)c * cs] = S[(size_t)c * R + rr];
+        }
+    }
+    // partial Gram matrix of this block's rows into its own Gs
+    for (int it = warp; it < nb * nb; it += nwarps) {
+        int i = it / nb, k = it % nb;
+        T sacc = T(0);
+        if (i < k && k < kmax) {
+            for (int rr = (k > r0 ? ((k - r0) & ~31) : 0) + lane; rr < nr; rr += 32) {  // rows below k only
+                const int r = r0 + rr;
+                if (r < k) continue;
+                const T vk = (r == k) ? T(1) : S[(size_t)k * R + rr];
+                sacc += S[(size_t)i * R + rr] * vk;
+            }
+            sacc = warp_sum(sacc);
+        }
+        if (lane == 0) Gs[i * nb + k] = (double)sacc;
+    }
+    cluster.sync();
+    if (p == 0) {
+        for (int it = tid; it < nb * nb; it += blockDim.x) {
+            int i = it / nb, k = it % nb;
+            double sum = 0.0;
+            if (i < k && k < kmax)
+                for (int q = 0; q < nP; ++q) sum += cluster.map_shared_rank(Gs, q)[it];
+            Ts[it] = sum;  // the summed Gram matrix (read below as G)
+        }
+    }
+    cluster.sync();  // every remote read is done: blocks may leave after this point
+    if (p != 0) return;
+    // T from G = Ts (summed Gram), built in Gs (no longer read remotely)
+    for (int it = tid; it < nb * nb; it += blockDim.x) Gs[it] = 0.0;
+    __syncthreads();
+    for (int k = 0; k < nb; ++k) {
+        double tk = (k < kmax) ? (double)tau[k] : 0.0;
+        double t = 0.0;
+        if (tid < k)
+            for (int q = tid; q < k; ++q) t += Gs[tid * nb + q] * Ts[q * nb + k];
+        __syncthreads();
+        if (tid < k) Gs[tid * nb + k] = -tk * t;
+        if (tid == k) Gs[k * nb + k] = tk;
+        __syncthreads();
+    }
+    for (int it = tid; it < nb * nb; it += blockDim.x) {
+        int i = it % nb, k = it / nb;
+        Tm[i + (size_t)k * nb] = (T)Gs[i * nb + k];
+    }
+}
+
+// Cluster size and rows per block for an M x nb panel, or 0 if it does not fit one cluster.
+// Which cluster sizes the device can schedule (one block per SM at the largest
+// dynamic shared memory) is asked once; smaller allocations schedule as well.
+template <typename T>
+static int cluster_plan(int M, int nb, int &R, size_t &dyn) {
+    static bool init = false;
+    static size_t max_dyn = 0;
+    static bool sched[5] = {false, false, false, false, false};  // cluster sizes 1, 2, 4, 8, 16
+    if (!init) {
+        init = true;
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, panel_cluster_kernel<T>) == cudaSuccess && (size_t)optin > fa.sharedSizeBytes)
+            max_dyn = (size_t)optin - fa.sharedSizeBytes;
+        if (cudaFuncSetAttribute(panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dyn) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(panel_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                cudaSuccess)
+            max_dyn = 0;
+        for (int k = 0; k < 5 && max_dyn > 0; ++k) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(1u << k);
+            cfg.blockDim = dim3(kPanelThreads);
+            cfg.dynamicSmemBytes = max_dyn;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 1u << k;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int ncl = 0;
+            sched[k] = cudaOccupancyMaxActiveClusters(&ncl, panel_cluster_kernel<T>, &cfg) == cudaSuccess && ncl >= 1;
+        }
+        cudaGetLastError();
+    }
+    int k0 = 0;
+    while (k0 < 4 && (1 << k0) * kPanelRowsTarget < M) ++k0;  // smallest size with <= 256 rows per block
+    int best = 0;
+    for (int k = 0; k < 5; ++k) {
+        if (!sched[k]) continue;
+        const int C = 1 << k;
+        const int r = (M + C - 1) / C;
+        const size_t d = (((size_t)r * nb * sizeof(T) + 15) & ~(size_t)15) + (size_t)2 * nb * nb * sizeof(double);
+        if (d > max_dyn) continue;
+        best = C;
+        R = r;
+        dyn = d;
+        if (k >= k0) break;  // the smallest fitting size at or above the target, else the largest that fits
+    }
+    return best;
+}
+
 template <typename T>
 cudaError_t panel_factor(T *P, long rs, long cs, int M, int nb, T *tau, T *Tm, const PanelCtl &ctl,
                          cudaStream_t st) {
     if (M <= 0 || nb <= 0) return cudaSuccess;
     if (nb > kNbMax) return cudaErrorInvalidValue;
+    {  // preferred: one thread-block cluster, no global barrier
+        int R = 0;
+        size_t dyn = 0;
+        const int C = cluster_plan<T>(M, nb, R, dyn);
+        if (C > 0) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(C);
+            cfg.blockDim = dim3(kPanelThreads);
+            cfg.dynamicSmemBytes = dyn;
+            cfg.stream = st;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = C;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            cudaError_t e = cudaLaunchKernelEx(&cfg, panel_cluster_kernel<T>, P, rs, cs, M, nb, R, tau, Tm);
+            if (e == cudaSuccess) return e;
+            cudaGetLastError();  // fall back to the grid-wide version
+        }
+    }
     static size_t max_dyn = 0;
     static bool attr_set = false;
     if (!attr_set) {

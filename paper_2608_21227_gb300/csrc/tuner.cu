@@ -280,6 +280,7 @@ struct TrailBench {
 // ------------------------------------------------------------------ MLP inference hook (mlp.cu)
 namespace nla {
 nla_status mlp_predict_host(const char *model_path, const float *X, int rows, float *y);
+extern int g_batched_group[5];  // batched.cu: threads per matrix per size bucket (0 = default)
 }
 
 namespace {
@@ -563,7 +564,7 @@ nla_status kt_tune(const kt_problem *p, kt_strategy strategy, double budget_frac
 
 nla_status kt_write_table(const char *path, int side, int m, int n, nla_dtype dtype, nla_update update,
                           const nla_cfg *cfg, double ms) {
-    if (!path || !cfg || (side != 0 && side != 1)) return terr(NLA_ERR_ARG, "bad arguments");
+    if (!path || !cfg || side < 0 || side > 2) return terr(NLA_ERR_ARG, "bad arguments");
     FILE *f = fopen(path, "a");
     if (!f) return terr(NLA_ERR_ARG, std::string("cannot open ") + path);
     if (ftell(f) == 0) fprintf(f, "# side m n dtype update band tile threads cpb unroll ms\n");
@@ -589,6 +590,12 @@ nla_status kt_load_config(const char *path) {
         fclose(f);
         if (t.empty()) return terr(NLA_ERR_ARG, std::string("no entries in ") + path);
     }
+    // side-2 entries carry the batched kernel's group size per size bucket:
+    // m = bucket index, band field = threads per matrix
+    int groups[5] = {0, 0, 0, 0, 0};
+    for (const TableEntry &e : t)
+        if (e.side == 2 && e.m >= 0 && e.m < 5) groups[e.m] = e.cfg.band;
+    for (int b = 0; b < 5; ++b) nla::g_batched_group[b] = groups[b];
     std::lock_guard<std::mutex> lk(g_table_mu);
     g_table.swap(t);
     return NLA_OK;

@@ -3,7 +3,10 @@
 // power-of-two scaling of the converted operands (the trailing update of
 // Algorithm 2 with the mixed-precision form of the contraction).
 //
-// QR side (one block per 128-column strip of X):
+// Two launches per side (as in the SIMT path): step 1 on a grid of
+// (128-wide strips) x (splits of the reduction dimension), the last block of a
+// strip applying T; step 3 on a 2-D grid of 128 x 128 output tiles.
+// QR side (strips of 128 columns of X):
 //   1. W^T (128 x nbp) = X_strip^T V, accumulated over 32-row tiles.  Each tile
 //      of X is scaled per column by 2^-e (e = exponent of the column's largest
 //      magnitude in that tile), rounded to TF32/BF16 and multiplied on the
@@ -45,7 +48,7 @@ namespace {
 constexpr int kTcThreads = 256;   // 8 warps
 constexpr int kStrip = 128;       // strip width = UMMA M
 constexpr int kKt = 32;           // rows (QR) / columns (LQ) of X per step-1 tile
-constexpr int kTmemCols = 256;    // D1 x 2 (64 columns each) + D3 (128 columns)
+constexpr int kTmemCols = 256;    // self-test accumulator columns
 
 template <int PREC>
 struct Prec;
@@ -159,253 +162,93 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(const float *A, const 
     if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
 }
 
-// ---------------------------------------------------------------- QR side
-template <int PREC>
-__global__ void __launch_bounds__(kTcThreads, 1)
-trail_left_tc_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__restrict__ V, long ldv, int nb,
-                     int nbp, const double *__restrict__ Tm, int *info) {
+// ---------------------------------------------------------------- step 1 (both sides)
+// Block (strip, split) accumulates the partial W^T (QR side: strip columns x
+// reflectors, reduction over rows [sbeg, send)) or Y (LQ side: strip rows x
+// reflectors, reduction over columns) from 32-wide tiles scaled per strip
+// line by 2^-e, rounded and multiplied on the tensor cores; the previous
+// tile's TMEM accumulator is read back (unscaled) into FP32 registers while
+// the next multiply runs.  The last block of the strip (atomic ticket) sums
+// the partials and applies T (QR: W' = T^T W; LQ: Y' = Y T), storing FP32.
+template <int PREC, int SIDE>
+__global__ void __launch_bounds__(kTcThreads)
+tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *__restrict__ V, long ldv, int nb,
+            int nbp, const double *__restrict__ Tm, int Ls, float *part, float *fin, unsigned int *tickets,
+            int *info) {
     using P = Prec<PREC>;
     extern __shared__ __align__(1024) unsigned char sm[];
-    const int es = P::es;
-    const int rb1 = kKt * es;     // step-1 operand row bytes (K = 32 rows of X)
-    const int rb3 = nbp * es;     // step-3 operand row bytes (K = nbp reflectors)
-    unsigned char *A1 = sm;                                  // 2 x [128 x kKt]   X^T tiles
-    unsigned char *B1 = A1 + 2 * kStrip * rb1;               // 2 x [nbp x kKt]   V tiles (as B^T)
-    unsigned char *A3 = B1 + 2 * 64 * rb1;                   // [128 x nbp]       V row tile
-    unsigned char *B3 = A3 + kStrip * rb3;                   // [128 x nbp]       W'^T (as B^T)
-    float *Wsh = reinterpret_cast<float *>(B3 + kStrip * rb3);  // nbp x 128
-    float *Tsh = Wsh + 64 * kStrip;                          // nbp x nbp (column-major)
-    int *ex1 = reinterpret_cast<int *>(Tsh + 64 * 64);       // 2 x 128 tile-column exponents
-    int *ex3 = ex1 + 2 * kStrip;                             // 128 W' column exponents
-    double *cmax = reinterpret_cast<double *>(ex3 + kStrip); // 2 x 128 partial maxima
-    TcShared *sh = reinterpret_cast<TcShared *>(cmax + 2 * kStrip);
-
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q = warp & 3, hh = warp >> 2;  // TMEM lane quarter, column half
-    const int c0 = blockIdx.x * kStrip, wc = min(kStrip, N - c0);
-    if (warp == 0) {
-        tc::tmem_alloc(&sh->tmem_base, kTmemCols);
-        tc::tmem_relinquish();
-    }
-    if (tid == 0) {
-        for (int i = 0; i < 3; ++i) tc::mbar_init(&sh->mbar[i], 1);
-        sh->fail = 0;
-        sh->last_bar = -1;
-    }
-    for (int idx = tid; idx < nbp * nbp; idx += blockDim.x) {
-        int i = idx % nbp, k = idx / nbp;
-        Tsh[idx] = (i < nb && k < nb) ? (float)Tm[i + (long)k * nb] : 0.f;
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    const uint32_t tbase = sh->tmem_base;
-    const uint32_t id1 = tc::idesc(P::fmt, 128, nbp), id3 = tc::idesc(P::fmt, 128, 128);
-    const int half = nbp / 2;  // accumulator columns per thread
-
-    // ---------------- step 1: W^T = X_strip^T V
-    float acc[32];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) acc[i] = 0.f;
-    const int m = tid & (kStrip - 1), h = tid >> 7;  // loader: strip column m, rows h*16 .. h*16+15
-    const int ntiles = (M + kKt - 1) / kKt;
-    for (int t = 0; t <= ntiles; ++t) {
-        const int buf = t & 1;
-        if (t < ntiles) {
-            const int r0 = t * kKt;
-            double xv[16];
-            double mx = 0.0;
-#pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int r = r0 + h * 16 + i;
-                xv[i] = (m < wc && r < M) ? X[r + (long)(c0 + m) * ldx] : 0.0;
-                mx = fmax(mx, fabs(xv[i]));
-            }
-            cmax[h * kStrip + m] = mx;
-            for (int idx = tid; idx < nbp * kKt; idx += blockDim.x) {
-                const int k = idx % kKt, n = idx / kKt, gr = r0 + k;
-                double v = 0.0;
-                if (n < nb && gr < M) v = gr > n ? V[gr + (long)n * ldv] : (gr == n ? 1.0 : 0.0);
-                P::put(B1 + buf * 64 * rb1, tc::kmajor_off(n, k, es, rb1), (float)v);
-            }
-            __syncthreads();
-            const int e = scale_exp(fmax(cmax[m], cmax[kStrip + m]));
-            if (h == 0) ex1[buf * kStrip + m] = e;
-#pragma unroll
-            for (int i = 0; i < 16; ++i)
-                P::put(A1 + buf * kStrip * rb1, tc::kmajor_off(m, h * 16 + i, es, rb1), (float)ldexp(xv[i], -e));
-            tc::fence_async_smem();
-            tc::fence_before_sync();
-            __syncthreads();
-            tc::fence_after_sync();
-            if (tid == 0) {
-                issue<PREC>(tbase + buf * 64, A1 + buf * kStrip * rb1, rb1, B1 + buf * 64 * rb1, rb1, rb1, id1, false);
-                tc::mma_commit(&sh->mbar[buf]);
-                sh->last_bar = buf;
-                sh->last_parity = (t >> 1) & 1;
-            }
-        }
-        if (t > 0) {  // drain tile t-1 while tile t multiplies
-            const int pb = (t - 1) & 1;
-            const bool ok = tc::mbar_wait_warp(&sh->mbar[pb], ((t - 1) >> 1) & 1, info);
-            if (!ok && lane == 0) sh->fail = 1;
-            tc::fence_after_sync();
-            const int col = 32 * q + lane;
-            const float sc = ldexpf(1.f, ex1[pb * kStrip + col]);
-            for (int c = 0; ok && c < half; c += 16) {
-                float v[16];
-                tc::tmem_ld16(tbase + pb * 64 + hh * half + c + ((uint32_t)(32 * q) << 16), v);
-                tc::tmem_wait_ld();
-#pragma unroll
-                for (int i = 0; i < 16; ++i) acc[c + i] += v[i] * sc;
-            }
-            tc::fence_before_sync();
-        }
-        __syncthreads();
-        if (sh->fail) break;
-    }
-    // ---------------- step 2: W' = T^T W (per strip column), scale, round
-    const int col = 32 * q + lane;
-    if (!sh->fail) {
-        for (int i = 0; i < half; ++i) Wsh[(hh * half + i) * kStrip + col] = acc[i];
-        __syncthreads();
-        double mx = 0.0;
-        for (int i = 0; i < half; ++i) {
-            const int kk = hh * half + i;
-            float s = 0.f;
-            for (int k = 0; k <= kk; ++k) s += Tsh[k + kk * nbp] * Wsh[k * kStrip + col];
-            acc[i] = s;
-            mx = fmax(mx, fabs((double)s));
-        }
-        cmax[hh * kStrip + col] = mx;
-        __syncthreads();
-        const int e = scale_exp(fmax(cmax[col], cmax[kStrip + col]));
-        if (hh == 0) ex3[col] = e;
-        for (int i = 0; i < half; ++i)
-            P::put(B3, tc::kmajor_off(col, hh * half + i, es, rb3), ldexpf(acc[i], -e));
-    }
-    __syncthreads();
-    // ---------------- step 3: X_strip -= V W', 128 rows at a time
-    const int nrt = (M + kStrip - 1) / kStrip;
-    for (int t = 0; t < nrt && !sh->fail; ++t) {
-        const int r0 = t * kStrip;
-        for (int idx = tid; idx < kStrip * nbp; idx += blockDim.x) {
-            const int r = idx % kStrip, k = idx / kStrip, gr = r0 + r;
-            double v = 0.0;
-            if (k < nb && gr < M) v = gr > k ? V[gr + (long)k * ldv] : (gr == k ? 1.0 : 0.0);
-            P::put(A3, tc::kmajor_off(r, k, es, rb3), (float)v);
-        }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
-        __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) {
-            issue<PREC>(tbase + 128, A3, rb3, B3, rb3, rb3, id3, false);
-            tc::mma_commit(&sh->mbar[2]);
-            sh->last_bar = 2;
-            sh->last_parity = t & 1;
-        }
-        if (!tc::mbar_wait_warp(&sh->mbar[2], t & 1, info)) {
-            if (lane == 0) sh->fail = 1;
-        } else {
-            tc::fence_after_sync();
-            const int r = r0 + 32 * q + lane;
-            for (int c = 0; c < 64; c += 16) {
-                float v[16];
-                tc::tmem_ld16(tbase + 128 + hh * 64 + c + ((uint32_t)(32 * q) << 16), v);
-                tc::tmem_wait_ld();
-                if (r < M) {
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int cc = hh * 64 + c + i;
-                        if (cc < wc) {
-                            double *px = X + r + (long)(c0 + cc) * ldx;
-                            *px -= ldexp((double)v[i], ex3[cc]);
-                        }
-                    }
-                }
-            }
-        }
-        tc::fence_before_sync();
-        __syncthreads();
-    }
-    tc::fence_before_sync();
-    __syncthreads();
-    if (tid == 0) drain_after_failure(sh);
-    __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
-}
-
-// ---------------------------------------------------------------- LQ side
-template <int PREC>
-__global__ void __launch_bounds__(kTcThreads, 1)
-trail_right_tc_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__restrict__ Vt, long ldvt, int nb,
-                      int nbp, const double *__restrict__ Tm, int *info) {
-    using P = Prec<PREC>;
-    extern __shared__ __align__(1024) unsigned char sm[];
-    const int es = P::es;
-    const int rb1 = kKt * es, rb3 = nbp * es;
-    unsigned char *A1 = sm;                                  // 2 x [128 x kKt]   X tiles (rows x cols)
-    unsigned char *B1 = A1 + 2 * kStrip * rb1;               // 2 x [nbp x kKt]   V tiles (as B^T)
-    unsigned char *A3 = B1 + 2 * 64 * rb1;                   // [128 x nbp]       Y' (rows x reflectors)
-    unsigned char *B3 = A3 + kStrip * rb3;                   // [128 x nbp]       V tile (as B^T = V rows)
-    float *Ysh = reinterpret_cast<float *>(B3 + kStrip * rb3);  // nbp x 128
-    float *Tsh = Ysh + 64 * kStrip;
-    int *ex1 = reinterpret_cast<int *>(Tsh + 64 * 64);
-    int *ex3 = ex1 + 2 * kStrip;
-    double *rmax = reinterpret_cast<double *>(ex3 + kStrip);
-    TcShared *sh = reinterpret_cast<TcShared *>(rmax + 2 * kStrip);
-
+    __shared__ int sh_last;
+    const int es = P::es, rb1 = kKt * es;
+    unsigned char *A1 = sm;                                  // 2 x [128 x kKt]  X tile (strip line x K)
+    unsigned char *B1 = A1 + 2 * kStrip * rb1;               // 2 x [64 x kKt]   V tile (reflector x K)
+    int *ex1 = reinterpret_cast<int *>(B1 + 2 * 64 * rb1);   // 2 x 128
+    double *lmax = reinterpret_cast<double *>(ex1 + 2 * kStrip);  // 2 x 128
+    TcShared *sh = reinterpret_cast<TcShared *>(lmax + 2 * kStrip);
+    float *Wsh = reinterpret_cast<float *>(sm);              // reused after the MMAs: nbp x 128
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q = warp & 3, hh = warp >> 2;
-    const int i0 = blockIdx.x * kStrip, hr = min(kStrip, M - i0);
+    // strip lines: QR -> columns of X, LQ -> rows of X; reduction dimension: the other one
+    const int L0 = blockIdx.x * kStrip;
+    const int Lext = SIDE == 0 ? N : M, Kext = SIDE == 0 ? M : N;
+    const int lw = min(kStrip, Lext - L0);
+    const int s = blockIdx.y, S = gridDim.y;
+    const int kbeg = s * Ls, kend = min(Kext, kbeg + Ls);
     if (warp == 0) {
-        tc::tmem_alloc(&sh->tmem_base, kTmemCols);
+        tc::tmem_alloc(&sh->tmem_base, 128);
         tc::tmem_relinquish();
     }
     if (tid == 0) {
-        for (int i = 0; i < 3; ++i) tc::mbar_init(&sh->mbar[i], 1);
+        tc::mbar_init(&sh->mbar[0], 1);
+        tc::mbar_init(&sh->mbar[1], 1);
         sh->fail = 0;
         sh->last_bar = -1;
-    }
-    for (int idx = tid; idx < nbp * nbp; idx += blockDim.x) {
-        int i = idx % nbp, k = idx / nbp;
-        Tsh[idx] = (i < nb && k < nb) ? (float)Tm[i + (long)k * nb] : 0.f;
     }
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = sh->tmem_base;
-    const uint32_t id1 = tc::idesc(P::fmt, 128, nbp), id3 = tc::idesc(P::fmt, 128, 128);
+    const uint32_t id1 = tc::idesc(P::fmt, 128, nbp);
     const int half = nbp / 2;
-
-    // ---------------- step 1: Y = X_strip V
     float acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0.f;
-    const int m = tid & (kStrip - 1), h = tid >> 7;  // loader: strip row m, columns h*16 .. h*16+15
-    const int ntiles = (N + kKt - 1) / kKt;
+    const int m = tid & (kStrip - 1), h = tid >> 7;  // loader: strip line m, K entries h*16 .. h*16+15
+    const int ntiles = (kend - kbeg + kKt - 1) / kKt;
     for (int t = 0; t <= ntiles; ++t) {
         const int buf = t & 1;
         if (t < ntiles) {
-            const int cb = t * kKt;
+            const int k0 = kbeg + t * kKt;
             double xv[16];
             double mx = 0.0;
 #pragma unroll
             for (int i = 0; i < 16; ++i) {
-                const int c = cb + h * 16 + i;
-                xv[i] = (m < hr && c < N) ? X[(i0 + m) + (long)c * ldx] : 0.0;
-                mx = fmax(mx, fabs(xv[i]));
-            }
-            rmax[h * kStrip + m] = mx;
-            for (int idx = tid; idx < nbp * kKt; idx += blockDim.x) {
-                const int n = idx % nbp, k = idx / nbp, gc = cb + k;
+                const int kk = k0 + h * 16 + i;
                 double v = 0.0;
-                if (n < nb && gc < N) v = gc > n ? Vt[n + (long)gc * ldvt] : (gc == n ? 1.0 : 0.0);
+                if (m < lw && kk < kend)
+                    v = SIDE == 0 ? X[kk + (long)(L0 + m) * ldx] : X[(L0 + m) + (long)kk * ldx];
+                xv[i] = v;
+                mx = fmax(mx, fabs(v));
+            }
+            lmax[h * kStrip + m] = mx;
+            for (int idx = tid; idx < nbp * kKt; idx += blockDim.x) {
+                int n, k;
+                if (SIDE == 0) {
+                    k = idx % kKt, n = idx / kKt;
+                } else {
+                    n = idx % nbp, k = idx / nbp;
+                }
+                const int g = k0 + k;
+                double v = 0.0;
+                if (n < nb && g < kend) {
+                    if (SIDE == 0)
+                        v = g > n ? V[g + (long)n * ldv] : (g == n ? 1.0 : 0.0);
+                    else
+                        v = g > n ? V[n + (long)g * ldv] : (g == n ? 1.0 : 0.0);
+                }
                 P::put(B1 + buf * 64 * rb1, tc::kmajor_off(n, k, es, rb1), (float)v);
             }
             __syncthreads();
-            const int e = scale_exp(fmax(rmax[m], rmax[kStrip + m]));
+            const int e = scale_exp(fmax(lmax[m], lmax[kStrip + m]));
             if (h == 0) ex1[buf * kStrip + m] = e;
 #pragma unroll
             for (int i = 0; i < 16; ++i)
@@ -426,8 +269,7 @@ trail_right_tc_kernel(double *__restrict__ X, long ldx, int M, int N, const doub
             const bool ok = tc::mbar_wait_warp(&sh->mbar[pb], ((t - 1) >> 1) & 1, info);
             if (!ok && lane == 0) sh->fail = 1;
             tc::fence_after_sync();
-            const int row = 32 * q + lane;
-            const float sc = ldexpf(1.f, ex1[pb * kStrip + row]);
+            const float sc = ldexpf(1.f, ex1[pb * kStrip + 32 * q + lane]);
             for (int c = 0; ok && c < half; c += 16) {
                 float v[16];
                 tc::tmem_ld16(tbase + pb * 64 + hh * half + c + ((uint32_t)(32 * q) << 16), v);
@@ -440,129 +282,224 @@ trail_right_tc_kernel(double *__restrict__ X, long ldx, int M, int N, const doub
         __syncthreads();
         if (sh->fail) break;
     }
-    // ---------------- step 2: Y' = Y T (per strip row), scale, round
-    const int row = 32 * q + lane;
-    if (!sh->fail) {
-        for (int i = 0; i < half; ++i) Ysh[(hh * half + i) * kStrip + row] = acc[i];
-        __syncthreads();
-        double mx = 0.0;
-        for (int i = 0; i < half; ++i) {
-            const int kk = hh * half + i;
-            float s = 0.f;
-            for (int k = 0; k <= kk; ++k) s += Ysh[k * kStrip + row] * Tsh[k + kk * nbp];
-            acc[i] = s;
-            mx = fmax(mx, fabs((double)s));
-        }
-        rmax[hh * kStrip + row] = mx;
-        __syncthreads();
-        const int e = scale_exp(fmax(rmax[row], rmax[kStrip + row]));
-        if (hh == 0) ex3[row] = e;
-        for (int i = 0; i < half; ++i)
-            P::put(A3, tc::kmajor_off(row, hh * half + i, es, rb3), ldexpf(acc[i], -e));
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0) drain_after_failure(sh);
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tbase, 128);
+    if (sh->fail) return;
+    // ---- partial of this split; the last block of the strip finishes
+    const int line = 32 * q + lane;
+    for (int i = 0; i < half; ++i)
+        if (line < lw) part[((size_t)s * nbp + hh * half + i) * Lext + L0 + line] = acc[i];
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) sh_last = atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(S - 1);
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    for (int idx = tid; idx < nbp * kStrip; idx += blockDim.x) {
+        const int l = idx % kStrip, k = idx / kStrip;
+        float sum = 0.f;
+        if (l < lw)
+            for (int qq = 0; qq < S; ++qq) sum += __ldcg(part + ((size_t)qq * nbp + k) * Lext + L0 + l);
+        Wsh[k * kStrip + l] = sum;
     }
     __syncthreads();
-    // ---------------- step 3: X_strip -= Y' V^T, 128 columns at a time
-    const int nct = (N + kStrip - 1) / kStrip;
-    for (int t = 0; t < nct && !sh->fail; ++t) {
-        const int cb = t * kStrip;
-        for (int idx = tid; idx < kStrip * nbp; idx += blockDim.x) {
-            const int k = idx % nbp, n = idx / nbp, gc = cb + n;
-            double v = 0.0;
-            if (k < nb && gc < N) v = gc > k ? Vt[k + (long)gc * ldvt] : (gc == k ? 1.0 : 0.0);
-            P::put(B3, tc::kmajor_off(n, k, es, rb3), (float)v);
-        }
-        tc::fence_async_smem();
-        tc::fence_before_sync();
+    for (int i = 0; i < half; ++i) {
+        const int kk = hh * half + i;
+        float v = 0.f;
+        // QR: W'(kk) = sum_{k <= kk} T(k, kk) W(k);  LQ: Y'(kk) = sum_{k <= kk} Y(k) T(k, kk) -- same form
+        if (kk < nb)
+            for (int k = 0; k <= kk; ++k) v += (float)Tm[k + (long)kk * nb] * Wsh[k * kStrip + line];
+        if (line < lw) fin[(size_t)kk * Lext + L0 + line] = v;
+    }
+    if (tid == 0) tickets[blockIdx.x] = 0u;
+}
+
+// ---------------------------------------------------------------- step 3 (both sides)
+// Block (strip, tile) forms one 128 x 128 product on the tensor cores and
+// subtracts it from X in FP64.  QR: D = V(rows) W'(strip columns); LQ:
+// D = Y'(strip rows) V(columns)^T.  W' / Y' are scaled per strip line by a
+// power of two before rounding; the scale is undone in the epilogue.
+template <int PREC, int SIDE>
+__global__ void __launch_bounds__(kTcThreads)
+tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__restrict__ V, long ldv, int nb, int nbp,
+            const float *__restrict__ fin, int *info) {
+    using P = Prec<PREC>;
+    extern __shared__ __align__(1024) unsigned char sm[];
+    const int es = P::es, rb3 = nbp * es;
+    unsigned char *Aop = sm;                         // [128 x nbp]
+    unsigned char *Bop = Aop + kStrip * rb3;         // [128 x nbp]
+    int *exs = reinterpret_cast<int *>(Bop + kStrip * rb3);   // 128 strip-line exponents
+    float *lmax = reinterpret_cast<float *>(exs + kStrip);    // 2 x 128
+    TcShared *sh = reinterpret_cast<TcShared *>(lmax + 2 * kStrip);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int q = warp & 3, hh = warp >> 2;
+    const int Lext = SIDE == 0 ? N : M;
+    const int L0 = blockIdx.x * kStrip, lw = min(kStrip, Lext - L0);  // strip lines
+    const int T0 = blockIdx.y * kStrip;                               // tile along the other dimension
+    const int Text = SIDE == 0 ? M : N, tw = min(kStrip, Text - T0);
+    if (warp == 0) {
+        tc::tmem_alloc(&sh->tmem_base, 128);
+        tc::tmem_relinquish();
+    }
+    if (tid == 0) {
+        tc::mbar_init(&sh->mbar[0], 1);
+        sh->fail = 0;
+        sh->last_bar = -1;
+    }
+    // W' / Y' strip block: line l, reflector k; scale per line
+    {
+        const int l = tid & (kStrip - 1), hf = tid >> 7;
+        float mx = 0.f;
+        for (int k = hf; k < nbp; k += 2) mx = fmaxf(mx, fabsf(l < lw && k < nb ? fin[(size_t)k * Lext + L0 + l] : 0.f));
+        lmax[hf * kStrip + l] = mx;
         __syncthreads();
-        tc::fence_after_sync();
-        if (tid == 0) {
-            issue<PREC>(tbase + 128, A3, rb3, B3, rb3, rb3, id3, false);
-            tc::mma_commit(&sh->mbar[2]);
-            sh->last_bar = 2;
-            sh->last_parity = t & 1;
+        const int e = scale_exp((double)fmaxf(lmax[l], lmax[kStrip + l]));
+        if (hf == 0) exs[l] = e;
+        // QR: B operand rows = strip columns (N dim), K = reflectors; LQ: A operand rows = strip rows
+        unsigned char *dst = SIDE == 0 ? Bop : Aop;
+        for (int k = hf; k < nbp; k += 2) {
+            const float v = (l < lw && k < nb) ? fin[(size_t)k * Lext + L0 + l] : 0.f;
+            P::put(dst, tc::kmajor_off(l, k, es, rb3), ldexpf(v, -e));
         }
-        if (!tc::mbar_wait_warp(&sh->mbar[2], t & 1, info)) {
-            if (lane == 0) sh->fail = 1;
+    }
+    // V block of this tile: QR -> rows T0.. of V (A operand); LQ -> V(T0 + n, k) (B operand)
+    for (int idx = tid; idx < kStrip * nbp; idx += blockDim.x) {
+        int r, k;
+        if (SIDE == 0) {
+            r = idx % kStrip, k = idx / kStrip;
         } else {
-            tc::fence_after_sync();
-            const int r = i0 + row;
-            const int e = ex3[row];
-            for (int c = 0; c < 64; c += 16) {
-                float v[16];
-                tc::tmem_ld16(tbase + 128 + hh * 64 + c + ((uint32_t)(32 * q) << 16), v);
-                tc::tmem_wait_ld();
-                if (row < hr) {
+            k = idx % nbp, r = idx / nbp;
+        }
+        const int g = T0 + r;
+        double v = 0.0;
+        if (k < nb && r < tw) {
+            if (SIDE == 0)
+                v = g > k ? V[g + (long)k * ldv] : (g == k ? 1.0 : 0.0);
+            else
+                v = g > k ? V[k + (long)g * ldv] : (g == k ? 1.0 : 0.0);
+        }
+        P::put(SIDE == 0 ? Aop : Bop, tc::kmajor_off(r, k, es, rb3), (float)v);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = sh->tmem_base;
+    if (tid == 0) {
+        issue<PREC>(tbase, Aop, rb3, Bop, rb3, rb3, tc::idesc(P::fmt, 128, 128), false);
+        tc::mma_commit(&sh->mbar[0]);
+        sh->last_bar = 0;
+        sh->last_parity = 0;
+    }
+    const bool ok = tc::mbar_wait_warp(&sh->mbar[0], 0, info);
+    if (!ok && lane == 0) sh->fail = 1;
+    tc::fence_after_sync();
+    if (ok) {
+        // D row = MMA row (QR: X row T0 + row; LQ: strip row L0 + row); D column = MMA column
+        const int row = 32 * q + lane;
+        for (int c = 0; c < 64; c += 16) {
+            float v[16];
+            tc::tmem_ld16(tbase + hh * 64 + c + ((uint32_t)(32 * q) << 16), v);
+            tc::tmem_wait_ld();
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) {
-                        const int cc = cb + hh * 64 + c + i;
-                        if (cc < N) {
-                            double *px = X + r + (long)cc * ldx;
-                            *px -= ldexp((double)v[i], e);
-                        }
+            for (int i = 0; i < 16; ++i) {
+                const int col = hh * 64 + c + i;
+                if (SIDE == 0) {
+                    if (row < tw && col < lw) {
+                        double *px = X + (T0 + row) + (long)(L0 + col) * ldx;
+                        *px -= ldexp((double)v[i], exs[col]);
+                    }
+                } else {
+                    if (row < lw && col < tw) {
+                        double *px = X + (L0 + row) + (long)(T0 + col) * ldx;
+                        *px -= ldexp((double)v[i], exs[row]);
                     }
                 }
             }
         }
-        tc::fence_before_sync();
-        __syncthreads();
     }
     tc::fence_before_sync();
     __syncthreads();
     if (tid == 0) drain_after_failure(sh);
     __syncthreads();
-    if (warp == 0) tc::tmem_dealloc(tbase, kTmemCols);
+    if (warp == 0) tc::tmem_dealloc(tbase, 128);
 }
 
-size_t tc_smem_bytes(int es, int nbp) {
-    const size_t rb1 = (size_t)kKt * es, rb3 = (size_t)nbp * es;
-    return 2 * kStrip * rb1 + 2 * 64 * rb1 + 2 * kStrip * rb3 + (size_t)64 * kStrip * 4 + 64 * 64 * 4 +
-           3 * kStrip * 4 + 2 * kStrip * 8 + sizeof(TcShared) + 64;
+size_t tc_w_smem(int es) {
+    const size_t rb1 = (size_t)kKt * es;
+    return std::max((size_t)2 * kStrip * rb1 + 2 * 64 * rb1 + 2 * kStrip * 4 + 2 * kStrip * 8 + sizeof(TcShared) + 64,
+                    (size_t)64 * kStrip * 4 + 64);
+}
+size_t tc_x_smem(int es, int nbp) {
+    return (size_t)2 * kStrip * nbp * es + kStrip * 4 + 2 * kStrip * 4 + sizeof(TcShared) + 64;
 }
 
-template <int PREC>
-cudaError_t launch_tc(int side, double *X, long ldx, int M, int N, const double *V, long ldv, int nb,
-                      const double *Tm, int *info, cudaStream_t st) {
-    const int nbp = nb <= 32 ? 32 : 64;
-    const size_t smem = tc_smem_bytes(Prec<PREC>::es, nbp);
-    if (side == 0) {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(trail_left_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-            attr = true;
-        }
-        trail_left_tc_kernel<PREC><<<(N + kStrip - 1) / kStrip, kTcThreads, smem, st>>>(X, ldx, M, N, V, ldv, nb, nbp,
-                                                                                        Tm, info);
-    } else {
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(trail_right_tc_kernel<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-            attr = true;
-        }
-        trail_right_tc_kernel<PREC><<<(M + kStrip - 1) / kStrip, kTcThreads, smem, st>>>(X, ldx, M, N, V, ldv, nb, nbp,
-                                                                                         Tm, info);
+template <typename K>
+void allow_smem(K kernel, bool &done) {
+    if (!done) {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa;
+        size_t stat = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)optin - stat));
+        cudaGetLastError();
+        done = true;
     }
+}
+
+template <int PREC, int SIDE>
+cudaError_t launch_tc(double *X, long ldx, int M, int N, const double *V, long ldv, int nb, const double *Tm,
+                      const UpdScratch &sc, int *info, cudaStream_t st) {
+    const int nbp = nb <= 32 ? 32 : 64;
+    const int es = Prec<PREC>::es;
+    static bool a1 = false, a3 = false;
+    allow_smem(tc_w_kernel<PREC, SIDE>, a1);
+    allow_smem(tc_x_kernel<PREC, SIDE>, a3);
+    const int Lext = SIDE == 0 ? N : M, Kext = SIDE == 0 ? M : N;
+    const int nblk = (Lext + kStrip - 1) / kStrip;
+    int S = (3 * device_sm_count() + nblk - 1) / nblk;
+    S = std::max(1, std::min({S, 8, (Kext + kKt - 1) / kKt}));
+    int Ls = ((Kext + S - 1) / S + kKt - 1) / kKt * kKt;
+    S = (Kext + Ls - 1) / Ls;
+    float *part = reinterpret_cast<float *>(sc.work);
+    float *fin = part + (size_t)8 * 64 * std::max(M, N);
+    tc_w_kernel<PREC, SIDE><<<dim3(nblk, S), kTcThreads, tc_w_smem(es), st>>>(X, ldx, M, N, V, ldv, nb, nbp, Tm, Ls,
+                                                                             part, fin, sc.tickets, info);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int Text = SIDE == 0 ? M : N;
+    tc_x_kernel<PREC, SIDE><<<dim3(nblk, (Text + kStrip - 1) / kStrip), kTcThreads, tc_x_smem(es, nbp), st>>>(
+        X, ldx, M, N, V, ldv, nb, nbp, fin, info);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t trail_tc(int side, double *X, long ldx, int M, int N, const double *V, long ldv, int nb, const double *Tm,
-                     int prec, int *info, cudaStream_t st) {
+                     int prec, const UpdScratch &sc, int *info, cudaStream_t st) {
     if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
-    if (nb > 64) return cudaErrorInvalidValue;
-    if (prec == NLA_UPD_TF32) return launch_tc<NLA_UPD_TF32>(side, X, ldx, M, N, V, ldv, nb, Tm, info, st);
-    if (prec == NLA_UPD_BF16) return launch_tc<NLA_UPD_BF16>(side, X, ldx, M, N, V, ldv, nb, Tm, info, st);
+    if (nb > 64 || !sc.work || !sc.tickets) return cudaErrorInvalidValue;
+    if (prec == NLA_UPD_TF32)
+        return side == 0 ? launch_tc<NLA_UPD_TF32, 0>(X, ldx, M, N, V, ldv, nb, Tm, sc, info, st)
+                         : launch_tc<NLA_UPD_TF32, 1>(X, ldx, M, N, V, ldv, nb, Tm, sc, info, st);
+    if (prec == NLA_UPD_BF16)
+        return side == 0 ? launch_tc<NLA_UPD_BF16, 0>(X, ldx, M, N, V, ldv, nb, Tm, sc, info, st)
+                         : launch_tc<NLA_UPD_BF16, 1>(X, ldx, M, N, V, ldv, nb, Tm, sc, info, st);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t trail_left_tc(double *X, long ldx, int M, int N, const double *Vp, long ldv, int nb, const double *Tm,
-                          int prec, int *info, cudaStream_t st) {
-    return trail_tc(0, X, ldx, M, N, Vp, ldv, nb, Tm, prec, info, st);
+                          int prec, const UpdScratch &sc, int *info, cudaStream_t st) {
+    return trail_tc(0, X, ldx, M, N, Vp, ldv, nb, Tm, prec, sc, info, st);
 }
 
 cudaError_t trail_right_tc(double *X, long ldx, int M, int N, const double *Vt, long ldvt, int nb, const double *Tm,
-                           int prec, int *info, cudaStream_t st) {
-    return trail_tc(1, X, ldx, M, N, Vt, ldvt, nb, Tm, prec, info, st);
+                           int prec, const UpdScratch &sc, int *info, cudaStream_t st) {
+    return trail_tc(1, X, ldx, M, N, Vt, ldvt, nb, Tm, prec, sc, info, st);
 }
 
 }  // namespace nla

@@ -143,6 +143,17 @@ def gesvd_vals_workspace(m, n, dtype_code, update=UPD_NATIVE, cfg=None, preserve
     return int(b.value)
 
 
+def plan_cfg(m, n, dtype_code, side=0, update=UPD_NATIVE, cfg=None):
+    """(band, tile, threads, cols_per_block, unroll) that gesvd_vals would use."""
+    L = lib()
+    L.nla_plan_cfg.argtypes = [_i, _i, _i, _popts, _i, ctypes.POINTER(Cfg)]
+    L.nla_plan_cfg.restype = ctypes.c_int
+    o = _opts(update, cfg)
+    out = Cfg()
+    _check(L.nla_plan_cfg(int(m), int(n), int(dtype_code), ctypes.byref(o), int(side), ctypes.byref(out)))
+    return out.as_tuple()
+
+
 def workspace(nbytes, device="cuda"):
     import torch
 
