@@ -134,7 +134,7 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
                       T *tauq_all, T *taup_all, int *dInfo, cudaStream_t st) {
     const int b = p.b;
     nla::PanelCtl ctl{bufs.bar, bufs.part, dInfo};
-    const nla::UpdScratch usc{bufs.upd_work, bufs.tickets};
+    const nla::UpdScratch usc{bufs.upd_work, bufs.tickets, dInfo};
     for (int kb = 0; kb < N; kb += b) {
         const int nb = std::min(b, N - kb);
         T *tq = tauq_all ? tauq_all + kb : reinterpret_cast<T *>(bufs.tauq);

@@ -21,6 +21,7 @@
 // one per block, each waiting (bounded spin) until its predecessor has
 // finished three more steps.
 #include <algorithm>
+#include <cstdlib>
 #include <climits>
 
 #include "common.cuh"
@@ -439,7 +440,14 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
     int *progress = reinterpret_cast<int *>(scratch);
     const int nsweeps = n - 2;
     const size_t kGroupBudget = 200 * 1024;
-    const int G = chase_group_size(b, (int)sizeof(T), kGroupBudget);
+    int G = chase_group_size(b, (int)sizeof(T), kGroupBudget);
+    {  // NLA_CHASE_GROUP caps the sweeps per block (0: one sweep per block, global-memory band)
+        static const int cap = [] {
+            const char *v = getenv("NLA_CHASE_GROUP");
+            return v ? atoi(v) : -1;
+        }();
+        if (cap >= 0) G = std::min(G, cap);
+    }
     if (nsweeps > 0 && b > 1 && G >= 1) {
         const int ngroups = (nsweeps + G - 1) / G;
         cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)ngroups, st);

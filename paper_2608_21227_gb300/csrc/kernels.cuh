@@ -35,6 +35,7 @@ struct UpdCfg {
 struct UpdScratch {
     void *work;
     unsigned int *tickets;
+    int *info = nullptr;  // device info word: a bounded wait that gives up records a timeout here
 };
 size_t tiled_scratch_elems(int M, int N);
 size_t tiled_tickets(int M, int N);
@@ -54,6 +55,17 @@ int tiled_max_threads(int side, int elem, int R, int unroll);
 template <typename T>
 cudaError_t trail_tiled(int side, T *X, long ldx, int M, int N, const T *V, long ldv, int nb, const T *Tm,
                         const UpdCfg &c, const UpdScratch &sc, cudaStream_t st);
+
+// TMA-streamed FP32 kernels (update_tma.cu): band widths 16, 32, 64; X, V
+// 16-byte aligned with leading dimensions divisible by 4; same scratch as the
+// register-tiled path.  side 0 = QR (V column-major at V, ld ldv), side 1 = LQ
+// (V(c, k) at V[k + c*ldv]).  Their configuration reads (tile, threads, cpb,
+// unroll) as (stage depth, consumer threads, pipeline stages, waves of blocks).
+bool tma_cfg_valid(int nb, const UpdCfg &c);
+size_t tma_cfg_smem(int nb, const UpdCfg &c);
+bool trail_tma_eligible(const float *X, long ldx, const float *V, long ldv, int nb, const UpdScratch &sc);
+cudaError_t trail_tma(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb, const float *Tm,
+                      const UpdCfg &c, const UpdScratch &sc, cudaStream_t st);
 
 // QR side: X (M x N at X, ldx) <- (I - V T V^T)^T X, V = unit lower M x nb at Vp (ldv).
 template <typename T>

@@ -50,7 +50,16 @@ static bool generic_cfg_valid(int side, int elem, int nb, const UpdCfg &c, size_
 
 // Band widths divisible by 4 use the register-tiled kernels (update_tiled.cu);
 // others the generic kernels here.
+// FP32 at band widths 16, 32, 64 runs the TMA-streamed kernels; everything
+// else the register-tiled (nb % 4 == 0) or generic SIMT kernels.
+bool tma_band(int elem, int nb) { return elem == 4 && (nb == 16 || nb == 32 || nb == 64); }
+
 bool upd_cfg_valid(int side, int elem, int nb, const UpdCfg &c, size_t *smem_bytes) {
+    if (tma_band(elem, nb)) {
+        if (!tma_cfg_valid(nb, c)) return false;
+        if (smem_bytes) *smem_bytes = tma_cfg_smem(nb, c);
+        return true;
+    }
     if (nb % 4 == 0) {
         if (!tiled_r(nb, c)) return false;
         size_t sm = tiled_smem(side, elem, nb, c.tile, 32 * c.cpb);
@@ -295,15 +304,41 @@ static int max_threads(int side, int unroll) {
 bool upd_cfg_launchable(int side, int elem, int nb, const UpdCfg &c) {
     size_t sm;
     if (!upd_cfg_valid(side, elem, nb, c, &sm)) return false;
+    if (tma_band(elem, nb)) return true;  // <= 288 threads, within the kernels' launch bounds
     if (nb % 4 == 0) return c.threads <= tiled_max_threads(side, elem, tiled_r(nb, c), c.unroll);
     int mt = elem == 8 ? max_threads<double>(side, c.unroll) : max_threads<float>(side, c.unroll);
     return c.threads <= mt;
+}
+
+// A launchable register-tiled configuration (nb % 4 == 0) for FP32 calls whose
+// buffers do not meet the TMA alignment rules.
+static UpdCfg tiled_for(int side, int elem, int nb, const UpdCfg &c) {
+    if (tiled_r(nb, c) && tiled_smem(side, elem, nb, c.tile, 32 * c.cpb) <= kSmemLimit &&
+        c.threads <= tiled_max_threads(side, elem, tiled_r(nb, c), c.unroll))
+        return c;
+    const int tiles[] = {64, 32, 128, 16};
+    for (int cpb : {2, 1, 4})
+        for (int threads = 128; threads <= 512; threads += 64)
+            for (int tile : tiles) {
+                const UpdCfg t{tile, threads, cpb, 1};
+                if (tiled_r(nb, t) && tiled_smem(side, elem, nb, tile, 32 * cpb) <= kSmemLimit &&
+                    threads <= tiled_max_threads(side, elem, tiled_r(nb, t), 1))
+                    return t;
+            }
+    return c;
 }
 
 template <typename T>
 cudaError_t trail_left(T *X, long ldx, int M, int N, const T *Vp, long ldv, int nb, const T *Tm,
                        const UpdCfg &c, const UpdScratch &sc, cudaStream_t st) {
     if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        if (tma_band(4, nb)) {
+            if (!tma_cfg_valid(nb, c)) return cudaErrorInvalidConfiguration;
+            if (trail_tma_eligible(X, ldx, Vp, ldv, nb, sc)) return trail_tma(0, X, ldx, M, N, Vp, ldv, nb, Tm, c, sc, st);
+            return trail_tiled<T>(0, X, ldx, M, N, Vp, ldv, nb, Tm, tiled_for(0, 4, nb, c), sc, st);
+        }
+    }
     if (nb % 4 == 0) {
         if (!upd_cfg_launchable(0, (int)sizeof(T), nb, c)) return cudaErrorInvalidConfiguration;
         return trail_tiled<T>(0, X, ldx, M, N, Vp, ldv, nb, Tm, c, sc, st);
@@ -322,6 +357,14 @@ template <typename T>
 cudaError_t trail_right(T *X, long ldx, int M, int N, const T *Vt, long ldvt, int nb, const T *Tm,
                         const UpdCfg &c, const UpdScratch &sc, cudaStream_t st) {
     if (M <= 0 || N <= 0 || nb <= 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        if (tma_band(4, nb)) {
+            if (!tma_cfg_valid(nb, c)) return cudaErrorInvalidConfiguration;
+            if (trail_tma_eligible(X, ldx, Vt, ldvt, nb, sc))
+                return trail_tma(1, X, ldx, M, N, Vt, ldvt, nb, Tm, c, sc, st);
+            return trail_tiled<T>(1, X, ldx, M, N, Vt, ldvt, nb, Tm, tiled_for(1, 4, nb, c), sc, st);
+        }
+    }
     if (nb % 4 == 0) {
         if (!upd_cfg_launchable(1, (int)sizeof(T), nb, c)) return cudaErrorInvalidConfiguration;
         return trail_tiled<T>(1, X, ldx, M, N, Vt, ldvt, nb, Tm, c, sc, st);

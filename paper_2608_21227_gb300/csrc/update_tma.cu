@@ -1,0 +1,695 @@
+// update_tma.cu -- FP32 trailing update (Algorithm 2, both sides) streamed
+// through the Tensor Memory Accelerator.
+//
+// At band widths 16-64 an FP32 update pass reads (and the last one writes) the
+// whole trailing matrix for 2*nb flops per element, so it is bound by HBM and
+// by how many bytes each SM keeps in flight.  Every kernel here is one
+// producer warp that streams tiles of X into a ring of shared-memory stages
+// with TMA (completion on an mbarrier per stage) and consumer warps that work
+// on each stage as it lands:
+//
+//   qr_proj       W = V^T X (QR side, reduction over rows).  A lane owns 4
+//                 columns of a 128-column strip and 16 reflectors; per 4-row
+//                 chunk, one 128-bit load of X per column and 16 broadcast
+//                 128-bit loads of V feed 256 FMAs.
+//   lq_proj       Y = X V (LQ side, reduction over columns).  A lane owns
+//                 64/nb rows and all nb reflectors; per column, one load of X
+//                 and nb/4 broadcast loads of V(c, :) feed 64 FMAs.
+//   strip_update  X -= P Q^T (QR: P = V, Q = W'^T; LQ: P = Y', Q = V).  A lane
+//                 keeps P(its 64/nb rows, :) in registers and streams columns;
+//                 the producer writes each finished stage back with a TMA store.
+//
+// The projections are split over the long dimension; the last block of each
+// strip (atomic ticket, nobody waits) sums the partials in a fixed order and
+// applies T (step 2 of Algorithm 2).
+//
+// X tiles are boxes of 32 rows (128 bytes) by `tc` columns with the 128-byte
+// swizzle: column j of a box is a 128-byte row whose 16-byte chunk q is stored
+// at chunk q ^ (j & 7), so a quarter warp reading chunk q of 8 consecutive
+// columns, or chunks 0..7 of one column, touches 8 distinct bank groups.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tma.cuh"
+
+namespace nla {
+
+// ------------------------------------------------------------------ host: tensor maps
+bool tma_encode_2d(CUtensorMap *map, const void *base, int elem_bytes, uint64_t dim0, uint64_t dim1,
+                   uint64_t stride_bytes, uint32_t box0, uint32_t box1, bool swizzle128) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static bool init = false;
+    if (!init) {
+        init = true;
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        cudaGetLastError();
+    }
+    if (!encode || dim0 == 0 || dim1 == 0) return false;
+    if (reinterpret_cast<uintptr_t>(base) % 16 || stride_bytes % 16) return false;
+    const cuuint64_t dims[2] = {dim0, dim1};
+    const cuuint64_t strides[1] = {stride_bytes};
+    const cuuint32_t box[2] = {box0, box1};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = encode(map, elem_bytes == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                              2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+namespace {
+
+constexpr int kBoxRows = 32;       // rows of an X box: 128 bytes of FP32
+constexpr int kMaxStages = 8;
+constexpr int kMaxSplitTma = 8;    // partial slabs (matches the tiled path's scratch layout)
+constexpr int kMaxThreads = 288;   // producer + up to 8 consumer warps
+constexpr size_t kTmaSmemLimit = 226 * 1024;  // dynamic bytes (the kernels' static shared memory is < 1 KB)
+
+// Reflector entry of a unit lower-trapezoidal V: 1 on the diagonal, 0 above it.
+NLA_DEV float unit_lower(int r, int k, float v) { return r > k ? v : (r == k ? 1.f : 0.f); }
+
+NLA_DEV unsigned char *align1k(unsigned char *p) {
+    return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
+}
+
+// Named barrier over the consumer warps (ids 1..; 0 is __syncthreads).
+NLA_DEV void consumers_sync(int nc) { asm volatile("bar.sync 1, %0;" ::"r"(nc * 32) : "memory"); }
+
+// Producer exit path: wait (bounded) until the last load issued into every
+// stage has landed, so no copy is in flight when the block leaves.
+NLA_DEV void drain_loads(uint64_t *full, int issued, int S, int *info) {
+    for (int t = max(0, issued - S); t < issued; ++t) tc::mbar_wait(&full[t % S], (uint32_t)((t / S) & 1), info);
+}
+
+// Lane's RL floats of column j of a 32*RL-row X stage (RL boxes of 32 rows, tc
+// columns each, 128-byte swizzle): rows RL*lane .. RL*lane + RL - 1.
+template <int RL>
+NLA_DEV float *xptr_rows(unsigned char *xs, int tcols, int j, int lane) {
+    const int row = RL * lane, box = row >> 5, rib = row & 31;
+    return reinterpret_cast<float *>(xs + (size_t)box * tcols * 128 + j * 128 + ((((rib >> 2) ^ (j & 7))) << 4) +
+                                     (rib & 3) * 4);
+}
+template <int RL>
+NLA_DEV void ld_rows(const float *p, float x[RL]) {
+    if constexpr (RL == 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+    } else if constexpr (RL == 2) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        x[0] = v.x, x[1] = v.y;
+    } else {
+        x[0] = *p;
+    }
+}
+template <int RL>
+NLA_DEV void st_rows(float *p, const float x[RL]) {
+    if constexpr (RL == 4)
+        *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+    else if constexpr (RL == 2)
+        *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+    else
+        *p = x[0];
+}
+
+// ------------------------------------------------------------------ qr_proj
+// Block (strip, s): partial W(:, strip) = V(rows of split s, :)^T X(rows, strip)
+// over `nt` stages of BR*32 rows; last block of the strip: W' = T^T W -> fin
+// (column-major by strip column: fin[c*NB + k]).
+template <int NB>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int M, int N,
+               const float *__restrict__ Tm, int BR, int RW, int S, int Ms, float *part, float *fin,
+               unsigned int *tickets, int *info) {
+    constexpr int RG = NB / 16;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kMaxStages], done[kMaxStages];
+    __shared__ int sh_last, sh_abort;
+    unsigned char *base = align1k(smem_raw);
+    const int NC = RG * RW;
+    const int xbytes = 128 * 128, vbytes = NB * 128;  // one 32-row box of X (128 columns) and of V
+    const int stage = BR * (xbytes + vbytes);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c0 = blockIdx.x * 128, wc = min(128, N - c0);
+    const int s = blockIdx.y, nsplit = gridDim.y;
+    const int rbeg = s * Ms, rend = min(M, rbeg + Ms);
+    const int th = BR * kBoxRows;
+    const int nt = (rend - rbeg + th - 1) / th;
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&done[i], NC);
+        }
+        sh_abort = 0;
+        tma::fence_init();
+        tma::prefetch_map(&tmX);
+        tma::prefetch_map(&tmV);
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int t = 0; t < nt; ++t) {
+                const int st = t % S;
+                if (t >= S && !tc::mbar_wait(&done[st], (uint32_t)(((t / S) - 1) & 1), info)) {
+                    sh_abort = 1;
+                    break;
+                }
+                unsigned char *sb = base + (size_t)st * stage;
+                tma::expect_tx(&full[st], (uint32_t)stage);
+                const int r0 = rbeg + t * th;
+                for (int bx = 0; bx < BR; ++bx) {
+                    tma::load_2d(sb + bx * xbytes, &tmX, r0 + bx * kBoxRows, c0, &full[st]);
+                    tma::load_2d(sb + BR * xbytes + bx * vbytes, &tmV, r0 + bx * kBoxRows, 0, &full[st]);
+                }
+                issued = t + 1;
+            }
+            drain_loads(full, issued, S, info);
+        }
+    } else {
+        const int cw = warp - 1, rg = cw % RG, rw = cw / RG;
+        float acc[16][4];
+#pragma unroll
+        for (int a = 0; a < 16; ++a)
+#pragma unroll
+            for (int i = 0; i < 4; ++i) acc[a][i] = 0.f;
+        for (int t = 0; t < nt; ++t) {
+            const int st = t % S;
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
+            const unsigned char *sb = base + (size_t)st * stage;
+            const int r0 = rbeg + t * th;  // trailing-matrix row of the stage's first row
+            for (int q = rw; q < 8 * BR; q += RW) {
+                const int bx = q >> 3, qq = q & 7;
+                const unsigned char *xb = sb + bx * xbytes;
+                float4 x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    x[i] = *reinterpret_cast<const float4 *>(xb + (lane + 32 * i) * 128 + ((qq ^ (lane & 7)) << 4));
+                const float *vb = reinterpret_cast<const float *>(sb + BR * xbytes + bx * vbytes) + (16 * rg) * 32 + 4 * qq;
+                const int rq = r0 + bx * kBoxRows + 4 * qq;
+                const bool diag = rq < NB;  // the chunk meets V's unit diagonal
+#pragma unroll
+                for (int a = 0; a < 16; ++a) {
+                    float4 v = *reinterpret_cast<const float4 *>(vb + a * 32);
+                    if (diag) {
+                        const int k = 16 * rg + a;
+                        v.x = unit_lower(rq, k, v.x), v.y = unit_lower(rq + 1, k, v.y);
+                        v.z = unit_lower(rq + 2, k, v.z), v.w = unit_lower(rq + 3, k, v.w);
+                    }
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float s4 = acc[a][i];
+                        s4 = fmaf(v.x, x[i].x, s4);
+                        s4 = fmaf(v.y, x[i].y, s4);
+                        s4 = fmaf(v.z, x[i].z, s4);
+                        acc[a][i] = fmaf(v.w, x[i].w, s4);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) tma::arrive(&done[st]);
+        }
+        // reduce the RW row groups in a fixed order into red[NB][128] (stage memory is free now)
+        float *red = reinterpret_cast<float *>(base);
+        consumers_sync(NC);
+        for (int g = 0; g < RW; ++g) {
+            if (rw == g) {
+#pragma unroll
+                for (int a = 0; a < 16; ++a)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        float *p = red + (16 * rg + a) * 128 + lane + 32 * i;
+                        *p = g == 0 ? acc[a][i] : *p + acc[a][i];
+                    }
+            }
+            consumers_sync(NC);
+        }
+        for (int idx = tid - 32; idx < NB * 128; idx += NC * 32) {
+            const int k = idx >> 7, c = idx & 127;
+            if (c < wc) part[((size_t)s * NB + k) * N + c0 + c] = red[idx];
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (sh_abort) return;
+    if (tid == 0) sh_last = atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(nsplit - 1);
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    float *W = reinterpret_cast<float *>(base);
+    for (int idx = tid; idx < NB * 128; idx += blockDim.x) {
+        const int k = idx >> 7, c = idx & 127;
+        float sum = 0.f;
+        if (c < wc)
+            for (int q = 0; q < nsplit; ++q) sum += __ldcg(part + ((size_t)q * NB + k) * N + c0 + c);
+        W[idx] = sum;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NB * wc; idx += blockDim.x) {
+        const int k = idx % NB, c = idx / NB;
+        float sum = 0.f;
+        for (int j = 0; j <= k; ++j) sum = fmaf(Tm[j + (size_t)k * NB], W[j * 128 + c], sum);
+        fin[(size_t)(c0 + c) * NB + k] = sum;
+    }
+    if (tid == 0) tickets[blockIdx.x] = 0u;
+}
+
+// ------------------------------------------------------------------ lq_proj
+// Block (strip, s): partial Y(strip rows, :) = X(strip rows, columns of split s) V
+// over stages of tc columns; last block of the strip: Y' = Y T -> fin[k*M + i].
+template <int NB>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int M, int N,
+               const float *__restrict__ Tm, int tcols, int NC, int S, int Ns, float *part, float *fin,
+               unsigned int *tickets, int *info) {
+    constexpr int RL = 64 / NB, H = 32 * RL;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kMaxStages], done[kMaxStages];
+    __shared__ int sh_last, sh_abort;
+    unsigned char *base = align1k(smem_raw);
+    const int xbytes = tcols * 128, qbytes = tcols * NB * 4;
+    const int stage = RL * xbytes + qbytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.x * H, hr = min(H, M - i0);
+    const int s = blockIdx.y, nsplit = gridDim.y;
+    const int cbeg = s * Ns, cend = min(N, cbeg + Ns);
+    const int nt = (cend - cbeg + tcols - 1) / tcols;
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&done[i], NC);
+        }
+        sh_abort = 0;
+        tma::fence_init();
+        tma::prefetch_map(&tmX);
+        tma::prefetch_map(&tmQ);
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int t = 0; t < nt; ++t) {
+                const int st = t % S;
+                if (t >= S && !tc::mbar_wait(&done[st], (uint32_t)(((t / S) - 1) & 1), info)) {
+                    sh_abort = 1;
+                    break;
+                }
+                unsigned char *sb = base + (size_t)st * stage;
+                tma::expect_tx(&full[st], (uint32_t)stage);
+                const int cb = cbeg + t * tcols;
+                for (int bx = 0; bx < RL; ++bx) tma::load_2d(sb + bx * xbytes, &tmX, i0 + bx * kBoxRows, cb, &full[st]);
+                tma::load_2d(sb + RL * xbytes, &tmQ, 0, cb, &full[st]);
+                issued = t + 1;
+            }
+            drain_loads(full, issued, S, info);
+        }
+    } else {
+        const int cw = warp - 1;
+        float acc[RL][NB];
+#pragma unroll
+        for (int a = 0; a < RL; ++a)
+#pragma unroll
+            for (int k = 0; k < NB; ++k) acc[a][k] = 0.f;
+        for (int t = 0; t < nt; ++t) {
+            const int st = t % S;
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
+            unsigned char *sb = base + (size_t)st * stage;
+            const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
+            const int cb = cbeg + t * tcols;
+            for (int j = cw; j < tcols; j += NC) {
+                float x[RL];
+                ld_rows<RL>(xptr_rows<RL>(sb, tcols, j, lane), x);
+                const int c = cb + j;
+                const bool diag = c < NB;
+#pragma unroll
+                for (int k4 = 0; k4 < NB; k4 += 4) {
+                    float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
+                    if (diag) {
+                        q.x = unit_lower(c, k4, q.x), q.y = unit_lower(c, k4 + 1, q.y);
+                        q.z = unit_lower(c, k4 + 2, q.z), q.w = unit_lower(c, k4 + 3, q.w);
+                    }
+#pragma unroll
+                    for (int a = 0; a < RL; ++a) {
+                        acc[a][k4] = fmaf(x[a], q.x, acc[a][k4]);
+                        acc[a][k4 + 1] = fmaf(x[a], q.y, acc[a][k4 + 1]);
+                        acc[a][k4 + 2] = fmaf(x[a], q.z, acc[a][k4 + 2]);
+                        acc[a][k4 + 3] = fmaf(x[a], q.w, acc[a][k4 + 3]);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) tma::arrive(&done[st]);
+        }
+        // reduce the NC column groups in a fixed order into red[NB][H]
+        float *red = reinterpret_cast<float *>(base);
+        consumers_sync(NC);
+        for (int g = 0; g < NC; ++g) {
+            if (cw == g) {
+#pragma unroll
+                for (int a = 0; a < RL; ++a)
+#pragma unroll
+                    for (int k = 0; k < NB; ++k) {
+                        float *p = red + k * H + RL * lane + a;
+                        *p = g == 0 ? acc[a][k] : *p + acc[a][k];
+                    }
+            }
+            consumers_sync(NC);
+        }
+        for (int idx = tid - 32; idx < NB * H; idx += NC * 32) {
+            const int k = idx / H, i = idx % H;
+            if (i < hr) part[((size_t)s * NB + k) * M + i0 + i] = red[idx];
+        }
+    }
+    __threadfence();
+    __syncthreads();
+    if (sh_abort) return;
+    if (tid == 0) sh_last = atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(nsplit - 1);
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    float *Y = reinterpret_cast<float *>(base);
+    for (int idx = tid; idx < NB * H; idx += blockDim.x) {
+        const int k = idx / H, i = idx % H;
+        float sum = 0.f;
+        if (i < hr)
+            for (int q = 0; q < nsplit; ++q) sum += __ldcg(part + ((size_t)q * NB + k) * M + i0 + i);
+        Y[idx] = sum;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NB * H; idx += blockDim.x) {
+        const int k = idx / H, i = idx % H;
+        if (i >= hr) continue;
+        float sum = 0.f;
+        for (int j = 0; j <= k; ++j) sum = fmaf(Y[j * H + i], Tm[j + (size_t)k * NB], sum);
+        fin[(size_t)k * M + i0 + i] = sum;
+    }
+    if (tid == 0) tickets[blockIdx.x] = 0u;
+}
+
+// ------------------------------------------------------------------ strip_update
+// Block (strip, cs): X(strip rows, columns of split cs) -= P(strip rows, :) Q(cols, :)^T.
+// SIDE 0 (QR): P = V (unit lower, column-major at Pv, ld ldp), Q = W'^T from
+// fin[c*NB + k].  SIDE 1 (LQ): P = Y' at Pv[k*M + i] (ldp unused), Q = V
+// stored by rows (unit lower in (c, k)).
+template <int NB, int SIDE>
+__global__ void __launch_bounds__(kMaxThreads, 1)
+strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int M, int N,
+                    const float *__restrict__ Pv, long ldp, int tcols, int NC, int S, int Ns, int *info) {
+    constexpr int RL = 64 / NB, H = 32 * RL;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kMaxStages], done[kMaxStages];
+    __shared__ int sh_abort;
+    unsigned char *base = align1k(smem_raw);
+    const int xbytes = tcols * 128, qbytes = tcols * NB * 4;
+    const int stage = RL * xbytes + qbytes;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.x * H;
+    const int cbeg = blockIdx.y * Ns, cend = min(N, cbeg + Ns);
+    const int nt = (cend - cbeg + tcols - 1) / tcols;
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&done[i], NC);
+        }
+        sh_abort = 0;
+        tma::fence_init();
+        tma::prefetch_map(&tmX);
+        tma::prefetch_map(&tmQ);
+    }
+    __syncthreads();
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0, stored = 0;
+            bool ok = true;
+            for (int t = 0; t < nt && ok; ++t) {
+                const int st = t % S;
+                unsigned char *sb = base + (size_t)st * stage;
+                if (t >= S) {
+                    // write back the tile that used this stage, then reuse it
+                    if (!tc::mbar_wait(&done[st], (uint32_t)(((t / S) - 1) & 1), info)) {
+                        sh_abort = 1;
+                        ok = false;
+                        break;
+                    }
+                    const int cbo = cbeg + (t - S) * tcols;
+                    for (int bx = 0; bx < RL; ++bx) tma::store_2d(&tmX, i0 + bx * kBoxRows, cbo, sb + bx * xbytes);
+                    tma::commit();
+                    stored = t - S + 1;
+                    tma::wait_read_all();
+                }
+                tma::expect_tx(&full[st], (uint32_t)stage);
+                const int cb = cbeg + t * tcols;
+                for (int bx = 0; bx < RL; ++bx) tma::load_2d(sb + bx * xbytes, &tmX, i0 + bx * kBoxRows, cb, &full[st]);
+                tma::load_2d(sb + RL * xbytes, &tmQ, 0, cb, &full[st]);
+                issued = t + 1;
+            }
+            for (int t = stored; ok && t < issued; ++t) {
+                const int st = t % S;
+                if (!tc::mbar_wait(&done[st], (uint32_t)((t / S) & 1), info)) {
+                    sh_abort = 1;
+                    ok = false;
+                    break;
+                }
+                const int cbo = cbeg + t * tcols;
+                for (int bx = 0; bx < RL; ++bx)
+                    tma::store_2d(&tmX, i0 + bx * kBoxRows, cbo, base + (size_t)st * stage + bx * xbytes);
+                tma::commit();
+            }
+            if (!ok) drain_loads(full, issued, S, info);
+            tma::wait_all();
+        }
+    } else {
+        const int cw = warp - 1;
+        // P(lane's rows, :) in registers
+        float p[RL][NB];
+#pragma unroll
+        for (int a = 0; a < RL; ++a) {
+            const int i = i0 + RL * lane + a;
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                float v = 0.f;
+                if (i < M) {
+                    if constexpr (SIDE == 0)
+                        v = unit_lower(i, k, i > k ? __ldg(Pv + i + (long)k * ldp) : 0.f);
+                    else
+                        v = __ldg(Pv + (size_t)k * M + i);
+                }
+                p[a][k] = v;
+            }
+        }
+        for (int t = 0; t < nt; ++t) {
+            const int st = t % S;
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
+            unsigned char *sb = base + (size_t)st * stage;
+            const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
+            const int cb = cbeg + t * tcols;
+            for (int j = cw; j < tcols; j += NC) {
+                float *xp = xptr_rows<RL>(sb, tcols, j, lane);
+                float x[RL];
+                ld_rows<RL>(xp, x);
+                const int c = cb + j;
+                const bool diag = SIDE == 1 && c < NB;
+#pragma unroll
+                for (int k4 = 0; k4 < NB; k4 += 4) {
+                    float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
+                    if (diag) {
+                        q.x = unit_lower(c, k4, q.x), q.y = unit_lower(c, k4 + 1, q.y);
+                        q.z = unit_lower(c, k4 + 2, q.z), q.w = unit_lower(c, k4 + 3, q.w);
+                    }
+#pragma unroll
+                    for (int a = 0; a < RL; ++a) {
+                        x[a] = fmaf(-p[a][k4], q.x, x[a]);
+                        x[a] = fmaf(-p[a][k4 + 1], q.y, x[a]);
+                        x[a] = fmaf(-p[a][k4 + 2], q.z, x[a]);
+                        x[a] = fmaf(-p[a][k4 + 3], q.w, x[a]);
+                    }
+                }
+                st_rows<RL>(xp, x);
+            }
+            tc::fence_async_smem();  // this lane's shared-memory writes -> visible to the TMA store
+            __syncwarp();
+            if (lane == 0) tma::arrive(&done[st]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host launch
+template <typename K>
+void set_smem(K kernel, bool &done) {
+    if (done) return;
+    done = true;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    const size_t stat = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)optin - stat));
+    cudaGetLastError();
+}
+
+int splits_for(int nstrip, int units, int waves) {
+    const int target = waves * device_sm_count();
+    return std::max(1, std::min({(target + nstrip - 1) / std::max(nstrip, 1), kMaxSplitTma, units}));
+}
+
+// Launch shape of the TMA kernels, read from a trailing-update configuration:
+//   tile    -> stage depth: 32-row boxes of the QR projection (tile / 32) and
+//              columns per stage of the column-streaming kernels (tile);
+//   threads -> consumer threads (the producer warp comes on top);
+//   cpb     -> pipeline stages;
+//   unroll  -> waves of blocks the long-dimension splits aim for.
+struct TmaShape {
+    int br, rw;  // qr_proj: 32-row boxes per stage, row-group warps
+    int tc, nc;  // columns per stage, consumer warps
+    int stages, waves;
+};
+
+int stage_bytes_qr(int nb, int tile) { return (tile / kBoxRows) * (128 * 128 + nb * 128); }
+int stage_bytes_cols(int nb, int tile) { return (64 / nb) * tile * 128 + tile * nb * 4; }
+
+TmaShape shape_of(int nb, const UpdCfg &c) {
+    TmaShape sh;
+    sh.br = c.tile / kBoxRows;
+    sh.nc = c.threads / 32;
+    sh.rw = sh.nc / (nb / 16);
+    sh.tc = c.tile;
+    sh.stages = c.cpb;
+    sh.waves = c.unroll;
+    return sh;
+}
+
+template <int NB>
+cudaError_t left_nb(float *X, long ldx, int M, int N, const float *V, long ldv, const float *Tm, const TmaShape &sh,
+                    const UpdScratch &sc, cudaStream_t st) {
+    float *part = reinterpret_cast<float *>(sc.work);
+    float *fin = part + (size_t)kMaxSplitTma * 64 * std::max(M, N);
+    CUtensorMap mX, mV, mX2, mQ;
+    if (!tma_encode_2d(&mX, X, 4, M, N, ldx * 4, kBoxRows, 128, true) ||
+        !tma_encode_2d(&mV, V, 4, M, NB, ldv * 4, kBoxRows, NB, false) ||
+        !tma_encode_2d(&mX2, X, 4, M, N, ldx * 4, kBoxRows, sh.tc, true) ||
+        !tma_encode_2d(&mQ, fin, 4, NB, N, NB * 4, NB, sh.tc, false))
+        return cudaErrorInvalidValue;
+    // pass 1 (+ step 2): W' = T^T V^T X
+    {
+        static bool attr = false;
+        set_smem(qr_proj_kernel<NB>, attr);
+        const int th = sh.br * kBoxRows;
+        const int stage = stage_bytes_qr(NB, th);
+        const int nstrip = (N + 127) / 128;
+        int nsplit = splits_for(nstrip, (M + th - 1) / th, sh.waves);
+        const int Ms = ((M + nsplit - 1) / nsplit + th - 1) / th * th;
+        nsplit = (M + Ms - 1) / Ms;
+        const size_t smem = (size_t)sh.stages * stage + 1024;
+        qr_proj_kernel<NB><<<dim3(nstrip, nsplit), 32 * (sh.nc + 1), smem, st>>>(
+            mX, mV, M, N, Tm, sh.br, sh.rw, sh.stages, Ms, part, fin, sc.tickets, sc.info);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // pass 2: X -= V W'
+    {
+        static bool attr = false;
+        set_smem(strip_update_kernel<NB, 0>, attr);
+        constexpr int H = 32 * (64 / NB);
+        const int stage = stage_bytes_cols(NB, sh.tc);
+        const int nstrip = (M + H - 1) / H;
+        int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (N + sh.tc - 1) / sh.tc));
+        const int Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
+        ncs = (N + Ns - 1) / Ns;
+        const size_t smem = (size_t)sh.stages * stage + 1024;
+        strip_update_kernel<NB, 0><<<dim3(nstrip, ncs), 32 * (sh.nc + 1), smem, st>>>(mX2, mQ, M, N, V, ldv, sh.tc,
+                                                                                    sh.nc, sh.stages, Ns, sc.info);
+    }
+    return cudaGetLastError();
+}
+
+template <int NB>
+cudaError_t right_nb(float *X, long ldx, int M, int N, const float *Vt, long ldvt, const float *Tm,
+                     const TmaShape &sh, const UpdScratch &sc, cudaStream_t st) {
+    float *part = reinterpret_cast<float *>(sc.work);
+    float *fin = part + (size_t)kMaxSplitTma * 64 * std::max(M, N);
+    CUtensorMap mX, mQ;
+    if (!tma_encode_2d(&mX, X, 4, M, N, ldx * 4, kBoxRows, sh.tc, true) ||
+        !tma_encode_2d(&mQ, Vt, 4, NB, N, ldvt * 4, NB, sh.tc, false))
+        return cudaErrorInvalidValue;
+    constexpr int H = 32 * (64 / NB);
+    const int stage = stage_bytes_cols(NB, sh.tc);
+    const int nstrip = (M + H - 1) / H;
+    const size_t smem = (size_t)sh.stages * stage + 1024;
+    // pass 1 (+ step 2): Y' = X V T
+    {
+        static bool attr = false;
+        set_smem(lq_proj_kernel<NB>, attr);
+        int nsplit = splits_for(nstrip, (N + sh.tc - 1) / sh.tc, sh.waves);
+        const int Ns = ((N + nsplit - 1) / nsplit + sh.tc - 1) / sh.tc * sh.tc;
+        nsplit = (N + Ns - 1) / Ns;
+        lq_proj_kernel<NB><<<dim3(nstrip, nsplit), 32 * (sh.nc + 1), smem, st>>>(
+            mX, mQ, M, N, Tm, sh.tc, sh.nc, sh.stages, Ns, part, fin, sc.tickets, sc.info);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // pass 2: X -= Y' V^T
+    {
+        static bool attr = false;
+        set_smem(strip_update_kernel<NB, 1>, attr);
+        int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (N + sh.tc - 1) / sh.tc));
+        const int Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
+        ncs = (N + Ns - 1) / Ns;
+        strip_update_kernel<NB, 1><<<dim3(nstrip, ncs), 32 * (sh.nc + 1), smem, st>>>(mX, mQ, M, N, fin, 0, sh.tc,
+                                                                                    sh.nc, sh.stages, Ns, sc.info);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t tma_cfg_smem(int nb, const UpdCfg &c) {
+    return (size_t)c.cpb * std::max(stage_bytes_qr(nb, c.tile), stage_bytes_cols(nb, c.tile)) + 1024;
+}
+
+bool tma_cfg_valid(int nb, const UpdCfg &c) {
+    if (nb != 16 && nb != 32 && nb != 64) return false;
+    if (c.tile != 32 && c.tile != 64 && c.tile != 128) return false;
+    if (c.threads != 64 && c.threads != 128 && c.threads != 256) return false;
+    if ((c.threads / 32) % (nb / 16)) return false;  // qr_proj: whole reflector groups of 16
+    if (c.cpb != 2 && c.cpb != 4 && c.cpb != 8) return false;
+    if (c.unroll != 1 && c.unroll != 2 && c.unroll != 4) return false;
+    return tma_cfg_smem(nb, c) <= kTmaSmemLimit;
+}
+
+bool trail_tma_eligible(const float *X, long ldx, const float *V, long ldv, int nb, const UpdScratch &sc) {
+    if (nb != 16 && nb != 32 && nb != 64) return false;
+    if (!sc.work || !sc.tickets) return false;
+    if (reinterpret_cast<uintptr_t>(X) % 16 || reinterpret_cast<uintptr_t>(V) % 16) return false;
+    return ldx % 4 == 0 && ldv % 4 == 0;
+}
+
+cudaError_t trail_tma(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb, const float *Tm,
+                      const UpdCfg &c, const UpdScratch &sc, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    if (!trail_tma_eligible(X, ldx, V, ldv, nb, sc) || !tma_cfg_valid(nb, c)) return cudaErrorInvalidConfiguration;
+    const TmaShape sh = shape_of(nb, c);
+    if (side == 0) {
+        switch (nb) {
+            case 16: return left_nb<16>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+            case 32: return left_nb<32>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+            default: return left_nb<64>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+        }
+    }
+    switch (nb) {
+        case 16: return right_nb<16>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+        case 32: return right_nb<32>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+        default: return right_nb<64>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+    }
+}
+
+}  // namespace nla
