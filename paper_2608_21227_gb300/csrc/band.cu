@@ -255,6 +255,14 @@ struct Win {
     T *w;
     int ldw, wc, b2;
     NLA_DEV T &at(int i, int j) const { return w[(b2 + i - j) + (j % wc) * ldw]; }
+    // Column j's storage shifted so that element (i, j) is col(j)[i].
+    NLA_DEV T *col(int j) const { return w + (size_t)(j % wc) * ldw + b2 - j; }
+    // Column j0 + c from j0's slot (0 <= c < wc): one compare instead of a division.
+    NLA_DEV T *col_from(int slot0, int j0, int c) const {
+        int sl = slot0 + c;
+        sl -= sl >= wc ? wc : 0;
+        return w + (size_t)sl * ldw + b2 - (j0 + c);
+    }
 };
 
 // One block step (right + left reflector) of sweep s at position k by one warp.
@@ -267,14 +275,15 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) 
     const int cend = min(s + (k + 2) * b, n - 1);
     const int L = c1 - c0 + 1;
     if (L < 2) return;
+    const int sl0 = c0 % W.wc;
     // ---- right reflector on columns c0..c1 from row tr, applied to rows tr+1..c1
     T part = T(0);
     for (int c = 1 + lane; c < L; c += 32) {
-        T x = W.at(tr, c0 + c);
+        T x = W.col_from(sl0, c0, c)[tr];
         part += x * x;
     }
     T xn2 = warp_sum(part);
-    T alpha = W.at(tr, c0);
+    T alpha = W.col_from(sl0, c0, 0)[tr];
     T tau = T(0), beta = alpha, scale = T(0);
     if (xn2 > T(0)) {
         T r = sqrt(alpha * alpha + xn2);
@@ -283,25 +292,29 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) 
         scale = T(1) / (alpha - beta);
     }
     if (tau != T(0)) {
-        for (int c = lane; c < L; c += 32) v[c] = c == 0 ? T(1) : W.at(tr, c0 + c) * scale;
+        for (int c = lane; c < L; c += 32) {
+            T *cp = W.col_from(sl0, c0, c);
+            v[c] = c == 0 ? T(1) : cp[tr] * scale;
+        }
         __syncwarp();
-        for (int c = lane; c < L; c += 32) W.at(tr, c0 + c) = c == 0 ? beta : T(0);
+        for (int c = lane; c < L; c += 32) W.col_from(sl0, c0, c)[tr] = c == 0 ? beta : T(0);
         for (int i = tr + 1 + lane; i <= c1; i += 32) {  // one lane per row
             T w = T(0);
-            for (int c = 0; c < L; ++c) w += W.at(i, c0 + c) * v[c];
+            for (int c = 0; c < L; ++c) w += W.col_from(sl0, c0, c)[i] * v[c];
             w *= tau;
-            for (int c = 0; c < L; ++c) W.at(i, c0 + c) -= w * v[c];
+            for (int c = 0; c < L; ++c) W.col_from(sl0, c0, c)[i] -= w * v[c];
         }
         __syncwarp();
     }
     // ---- left reflector on rows c0..c1 from column c0, applied to columns c0+1..cend
+    const T *cl = W.col_from(sl0, c0, 0);
     part = T(0);
     for (int r = 1 + lane; r < L; r += 32) {
-        T x = W.at(c0 + r, c0);
+        T x = cl[c0 + r];
         part += x * x;
     }
     xn2 = warp_sum(part);
-    alpha = W.at(c0, c0);
+    alpha = cl[c0];
     tau = T(0), beta = alpha, scale = T(0);
     if (xn2 > T(0)) {
         T r = sqrt(alpha * alpha + xn2);
@@ -310,14 +323,16 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) 
         scale = T(1) / (alpha - beta);
     }
     if (tau != T(0)) {
-        for (int r = lane; r < L; r += 32) v[r] = r == 0 ? T(1) : W.at(c0 + r, c0) * scale;
+        T *clw = W.col_from(sl0, c0, 0);
+        for (int r = lane; r < L; r += 32) v[r] = r == 0 ? T(1) : clw[c0 + r] * scale;
         __syncwarp();
-        for (int r = lane; r < L; r += 32) W.at(c0 + r, c0) = r == 0 ? beta : T(0);
+        for (int r = lane; r < L; r += 32) clw[c0 + r] = r == 0 ? beta : T(0);
         for (int j = c0 + 1 + lane; j <= cend; j += 32) {  // one lane per column
+            T *cj = W.col_from(sl0, c0, j - c0);
             T w = T(0);
-            for (int r = 0; r < L; ++r) w += v[r] * W.at(c0 + r, j);
+            for (int r = 0; r < L; ++r) w += v[r] * cj[c0 + r];
             w *= tau;
-            for (int r = 0; r < L; ++r) W.at(c0 + r, j) -= w * v[r];
+            for (int r = 0; r < L; ++r) cj[c0 + r] -= w * v[r];
         }
         __syncwarp();
     }
@@ -372,11 +387,13 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
             if (flushed_lo < 0) flushed_lo = lo - 1, loaded_hi = lo - 1;  // first step: nothing cached yet
             // write back columns the group no longer touches, then announce them
             if (lo - 1 > flushed_lo) {
-                for (int j = flushed_lo + 1; j < lo; ++j)
+                for (int j = flushed_lo + 1; j < lo; ++j) {
+                    const T *cw = W.col(j);
                     for (int q = tid; q < 3 * b + 1; q += blockDim.x) {
                         const int i = j + q - 2 * b;
-                        if (i >= 0 && i < n) __stcg(A.at(i, j), W.at(i, j));
+                        if (i >= 0 && i < n) __stcg(A.at(i, j), cw[i]);
                     }
+                }
                 flushed_lo = lo - 1;
                 __threadfence();
                 __syncthreads();
@@ -389,11 +406,13 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                     __syncthreads();
                     if (sh_fail) return;
                 }
-                for (int j = loaded_hi + 1; j <= hi; ++j)
+                for (int j = loaded_hi + 1; j <= hi; ++j) {
+                    T *cw = W.col(j);
                     for (int q = tid; q < 3 * b + 1; q += blockDim.x) {
                         const int i = j + q - 2 * b;
-                        if (i >= 0 && i < n) W.at(i, j) = __ldcg(A.at(i, j));
+                        if (i >= 0 && i < n) cw[i] = __ldcg(A.at(i, j));
                     }
+                }
                 loaded_hi = hi;
             }
             __syncthreads();
@@ -404,11 +423,13 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
             __syncthreads();
         }
         // flush what is left and release the whole band to the next group
-        for (int j = flushed_lo + 1; j <= loaded_hi; ++j)
+        for (int j = flushed_lo + 1; j <= loaded_hi; ++j) {
+            const T *cw = W.col(j);
             for (int q = tid; q < 3 * b + 1; q += blockDim.x) {
                 const int i = j + q - 2 * b;
-                if (i >= 0 && i < n) __stcg(A.at(i, j), W.at(i, j));
+                if (i >= 0 && i < n) __stcg(A.at(i, j), cw[i]);
             }
+        }
         __threadfence();
         __syncthreads();
         if (tid == 0) st_release(&done[grp], INT_MAX);

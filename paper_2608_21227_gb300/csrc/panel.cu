@@ -269,7 +269,6 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
     double *Ts = Gs + (size_t)nb * nb;
     __shared__ double cpart[2][kNbMax + 1];  // this block's partial sums, double-buffered by column parity
     __shared__ double rowb[2][kNbMax + 1];   // row j (owner block only)
-    __shared__ double red[kNbMax + 1], rowv[kNbMax + 1];
     __shared__ T wcoef[kNbMax + 1];
     __shared__ double sh_tau, sh_beta, sh_scale;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -313,32 +312,49 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
         if (p == owner)
             for (int c = j + tid; c < nb; c += blockDim.x) rowb[buf][c - j] = (double)S[(size_t)c * R + (j - r0)];
         cluster.sync();
-        // fixed-order sum over the cluster's blocks (deterministic)
-        for (int it = tid; it < nitem; it += blockDim.x) {
-            double sum = 0.0;
-            for (int q = 0; q < nP; ++q) sum += cluster.map_shared_rank(&cpart[buf][0], q)[it];
-            red[it] = sum;
-            rowv[it] = cluster.map_shared_rank(&rowb[buf][0], owner)[it];
-        }
-        __syncthreads();
-        if (tid == 0) {
-            double alpha = rowv[0], xn2 = red[0];
-            double tj = 0.0, beta = alpha, scale = 0.0;
-            if (xn2 > 0.0) {
-                double r = sqrt(alpha * alpha + xn2);
-                beta = alpha >= 0.0 ? -r : r;
-                tj = (beta - alpha) / beta;
-                scale = 1.0 / (alpha - beta);
+        // warp 0: fixed-order sum over the cluster's blocks (every remote load in
+        // flight at once), the reflector in the panel's precision, and the update
+        // coefficients w_c = tau (a_jc + x . a_c / (alpha - beta)) = tau v . a_c
+        if (warp == 0) {
+            const int i0 = lane, i1 = lane + 32;  // items: nitem <= kNbMax = 64
+            double s0 = 0.0, s1 = 0.0, w0 = 0.0, w1 = 0.0;
+            {
+                double v0[16], v1[16];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    v0[q] = 0.0;
+                    v1[q] = 0.0;
+                    if (q < nP) {
+                        const double *cp = cluster.map_shared_rank(&cpart[buf][0], q);
+                        if (i0 < nitem) v0[q] = cp[i0];
+                        if (i1 < nitem) v1[q] = cp[i1];
+                    }
+                }
+                const double *rb = cluster.map_shared_rank(&rowb[buf][0], owner);
+                if (i0 < nitem) w0 = rb[i0];
+                if (i1 < nitem) w1 = rb[i1];
+#pragma unroll
+                for (int q = 0; q < 16; ++q) s0 += v0[q], s1 += v1[q];
             }
-            sh_tau = tj;
-            sh_beta = beta;
-            sh_scale = scale;
-            if (p == 0) tau[j] = (T)tj;
+            const T alpha = (T)__shfl_sync(0xffffffffu, w0, 0), xn2 = (T)__shfl_sync(0xffffffffu, s0, 0);
+            T tj = T(0), beta = alpha, scale = T(0);
+            if (xn2 > T(0)) {
+                const T r = sqrt(alpha * alpha + xn2);
+                beta = alpha >= T(0) ? -r : r;
+                tj = (beta - alpha) / beta;
+                scale = T(1) / (alpha - beta);
+            }
+            if (lane == 0) {
+                sh_tau = (double)tj;
+                sh_beta = (double)beta;
+                sh_scale = (double)scale;
+                if (p == 0) tau[j] = tj;
+            }
+            if (i0 >= 1 && i0 < nitem) wcoef[i0] = tj * ((T)w0 + scale * (T)s0);
+            if (i1 < nitem) wcoef[i1] = tj * ((T)w1 + scale * (T)s1);
         }
         __syncthreads();
         const double tj = sh_tau, sc = sh_scale;
-        for (int it = 1 + tid; it < nitem; it += blockDim.x) wcoef[it] = (T)(tj * (rowv[it] + sc * red[it]));
-        __syncthreads();
         if (tj != 0.0) {
             const T scT = (T)sc;
             for (int rr = rr_lo + tid; rr < nr; rr += blockDim.x) {
