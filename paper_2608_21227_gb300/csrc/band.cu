@@ -362,87 +362,181 @@ NLA_DEV void group_need(int n, int b, int s0, int g, int tau, int &lo, int &hi, 
     }
 }
 
+// Mover warp: copy band columns j0..j1 (3b+1 storage rows each) from global
+// memory into the window, eight loads per lane in flight before their stores.
 template <typename T>
-__global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int wc, int *done, int *info) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int sh_fail;
-    const int ldw = (3 * b + 2) & ~1;  // even: lanes walking a row hit distinct banks
-    Win<T> W{reinterpret_cast<T *>(smem_raw), ldw, wc, 2 * b};
-    T *vbase = W.w + (size_t)wc * ldw;  // 64 entries per warp
-    const int tid = threadIdx.x, warp = tid >> 5;
-    T *v = vbase + warp * 64;
-    Band<T> A{AB, ldab, 2 * b};
-    const int nsweeps = n - 2;
-    const int ngroups = (nsweeps + G - 1) / G;
-    if (tid == 0) sh_fail = 0;
-    __syncthreads();
-    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-        const int s0 = grp * G, g = min(G, nsweeps - s0);
-        int loaded_hi = -1, flushed_lo = -1;  // window holds columns [flushed_lo+1 .. loaded_hi]
-        for (int tau = 0;; ++tau) {
-            int lo, hi;
-            bool active;
-            group_need(n, b, s0, g, tau, lo, hi, active);
-            if (!active) break;
-            if (flushed_lo < 0) flushed_lo = lo - 1, loaded_hi = lo - 1;  // first step: nothing cached yet
-            // write back columns the group no longer touches, then announce them
-            if (lo - 1 > flushed_lo) {
-                for (int j = flushed_lo + 1; j < lo; ++j) {
-                    const T *cw = W.col(j);
-                    for (int q = tid; q < 3 * b + 1; q += blockDim.x) {
-                        const int i = j + q - 2 * b;
-                        if (i >= 0 && i < n) __stcg(A.at(i, j), cw[i]);
-                    }
-                }
-                flushed_lo = lo - 1;
-                __threadfence();
-                __syncthreads();
-                if (tid == 0) st_release(&done[grp], lo);
-            }
-            // load newly needed columns once the previous group has finished with them
-            if (hi > loaded_hi) {
-                if (grp > 0) {
-                    if (tid == 0 && !spin_until_geq(&done[grp - 1], hi + 1, info, 64)) sh_fail = 1;
-                    __syncthreads();
-                    if (sh_fail) return;
-                }
-                for (int j = loaded_hi + 1; j <= hi; ++j) {
-                    T *cw = W.col(j);
-                    for (int q = tid; q < 3 * b + 1; q += blockDim.x) {
-                        const int i = j + q - 2 * b;
-                        if (i >= 0 && i < n) cw[i] = __ldcg(A.at(i, j));
-                    }
-                }
-                loaded_hi = hi;
-            }
-            __syncthreads();
-            if (warp < g) {
-                const int s = s0 + warp, k = tau - 3 * warp;
-                if (s < nsweeps && k >= 0 && s + k * b + 1 <= n - 1) warp_chase_step<T>(W, n, b, s, k, v);
-            }
-            __syncthreads();
-        }
-        // flush what is left and release the whole band to the next group
-        for (int j = flushed_lo + 1; j <= loaded_hi; ++j) {
-            const T *cw = W.col(j);
-            for (int q = tid; q < 3 * b + 1; q += blockDim.x) {
-                const int i = j + q - 2 * b;
-                if (i >= 0 && i < n) __stcg(A.at(i, j), cw[i]);
+NLA_DEV void mover_load(const Win<T> &W, const Band<T> &A, int n, int b, int j0, int j1, int lane) {
+    const int h = 3 * b + 1, tot = (j1 - j0 + 1) * h;
+    for (int base = 0; base < tot; base += 32 * 8) {
+        T r[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * 32 + lane;
+            r[u] = T(0);
+            if (idx < tot) {
+                const int j = j0 + idx / h, i = j + idx % h - 2 * b;
+                if (i >= 0 && i < n) r[u] = __ldcg(A.at(i, j));
             }
         }
-        __threadfence();
-        __syncthreads();
-        if (tid == 0) st_release(&done[grp], INT_MAX);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int idx = base + u * 32 + lane;
+            if (idx < tot) {
+                const int j = j0 + idx / h, i = j + idx % h - 2 * b;
+                if (i >= 0 && i < n) W.col(j)[i] = r[u];
+            }
+        }
     }
 }
 
-// Sweeps per block group that fit the shared-memory window, or 0 if none.
-static int chase_group_size(int b, int elem, size_t budget) {
-    const size_t ldw = (size_t)((3 * b + 2) & ~1);
-    for (int G = 16; G >= 1; --G) {
-        const size_t wc = (size_t)(3 * G - 1) * b + G + 1;
-        if (wc * ldw * elem + (size_t)G * 64 * elem <= budget) return G;
+// Bounded spin of a chase warp on the window's "loaded up to" column.
+NLA_DEV bool wait_loaded(volatile int *sh_hi, int hi, volatile int *sh_abort, int *info) {
+    if (*sh_hi >= hi) return true;
+    const unsigned long long t0 = global_ns();
+    while (*sh_hi < hi) {
+        if (*sh_abort) return false;
+        if (global_ns() - t0 > kSpinBudgetNs) {
+            if (info) atomicExch(info, kInfoTimeout);
+            *sh_abort = 1;
+            return false;
+        }
     }
+    return true;
+}
+
+// Block = G chase warps + one mover warp (warp G).  The chase warps run the
+// group's sweeps on the window in lockstep (named barrier 1 per wavefront step)
+// and never touch global memory; the mover keeps the window fed: it writes
+// back columns the group will not touch again and announces them in
+// done[group], and it loads up to `pf` steps ahead the columns the previous
+// group has released.  The window holds columns [flushed + 1, loaded] in
+// wc >= (3G - 1) b + G + 1 + pf b circular slots.
+template <typename T>
+__global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int wc, int pf, int *done, int *info) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int sh_tau, sh_hi, sh_abort;  // chase progress, loaded-up-to column, abort flag
+    const int ldw = (3 * b + 2) & ~1;          // even: lanes walking a row hit distinct banks
+    Win<T> W{reinterpret_cast<T *>(smem_raw), ldw, wc, 2 * b};
+    T *vbase = W.w + (size_t)wc * ldw;          // 64 entries per chase warp
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    Band<T> A{AB, ldab, 2 * b};
+    const int nsweeps = n - 2;
+    const int ngroups = (nsweeps + G - 1) / G;
+    volatile int *vtau = &sh_tau, *vhi = &sh_hi, *vabort = &sh_abort;
+    if (tid == 0) sh_abort = 0;
+    for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+        const int s0 = grp * G, g = min(G, nsweeps - s0);
+        int lo0, hi0;
+        bool act0;
+        group_need(n, b, s0, g, 0, lo0, hi0, act0);
+        if (tid == 0) {
+            sh_tau = 0;
+            sh_hi = lo0 - 1;
+        }
+        __syncthreads();
+        if (*vabort) break;
+        if (warp < G) {
+            // ---------------- chase warps
+            T *v = vbase + warp * 64;
+            for (int tau = 0;; ++tau) {
+                int lo, hi;
+                bool active;
+                group_need(n, b, s0, g, tau, lo, hi, active);
+                if (!active) break;
+                bool ok = true;
+                if (lane == 0) ok = wait_loaded(vhi, hi, vabort, info);
+                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                __threadfence_block();
+                if (ok && warp < g) {
+                    const int s = s0 + warp, k = tau - 3 * warp;
+                    if (k >= 0 && s + k * b + 1 <= n - 1) warp_chase_step<T>(W, n, b, s, k, v);
+                }
+                asm volatile("bar.sync 1, %0;" ::"r"(32 * G) : "memory");
+                if (*vabort) break;
+                if (warp == 0 && lane == 0) {
+                    __threadfence_block();
+                    *vtau = tau + 1;
+                }
+            }
+        } else {
+            // ---------------- mover warp
+            int flushed = lo0 - 1, loaded = lo0 - 1;
+            for (;;) {
+                if (*vabort) break;
+                const int t = *vtau;  // steps < t are complete
+                __threadfence_block();
+                int lo, hi;
+                bool active;
+                group_need(n, b, s0, g, t, lo, hi, active);
+                const int fin = active ? lo - 1 : loaded;  // columns <= fin are final
+                bool worked = false;
+                if (fin > flushed) {
+                    for (int j = flushed + 1; j <= fin; ++j) {
+                        const T *cw = W.col(j);
+                        for (int q = lane; q < 3 * b + 1; q += 32) {
+                            const int i = j + q - 2 * b;
+                            if (i >= 0 && i < n) __stcg(A.at(i, j), cw[i]);
+                        }
+                    }
+                    flushed = fin;
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) st_release(&done[grp], active ? flushed + 1 : INT_MAX);
+                    worked = true;
+                }
+                if (!active) break;
+                // load ahead: the columns steps t .. t + pf need, within the window's capacity
+                int lt, want;
+                bool at;
+                group_need(n, b, s0, g, t + pf, lt, want, at);
+                want = max(want, hi);
+                want = min(want, flushed + wc);
+                if (want > loaded) {
+                    int avail = want;
+                    if (grp > 0) {
+                        int have = 0;
+                        if (lane == 0) {
+                            have = ld_acquire(&done[grp - 1]);
+                            // the current step cannot start without its columns: wait for those
+                            if (have < hi + 1 && hi > loaded) {
+                                if (!spin_until_geq(&done[grp - 1], hi + 1, info, 64)) *vabort = 1;
+                                have = ld_acquire(&done[grp - 1]);
+                            }
+                        }
+                        have = __shfl_sync(0xffffffffu, have, 0);
+                        __syncwarp();  // lane 0's acquire orders the whole warp's loads below
+                        if (*vabort) break;
+                        avail = min(want, have - 1);
+                    }
+                    if (avail > loaded) {
+                        mover_load<T>(W, A, n, b, loaded + 1, avail, lane);
+                        loaded = avail;
+                        __syncwarp();
+                        __threadfence_block();
+                        if (lane == 0) *vhi = loaded;
+                        worked = true;
+                    }
+                }
+                if (!worked) __nanosleep(32);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Sweeps per block group and prefetch depth that fit the shared-memory window
+// (G = 0: none fits).
+static int chase_group_size(int b, int elem, size_t budget, int &pf) {
+    const size_t ldw = (size_t)((3 * b + 2) & ~1);
+    for (int G = 16; G >= 1; --G)
+        for (int p : {4, 2, 1}) {
+            const size_t wc = (size_t)(3 * G - 1) * b + G + 1 + (size_t)p * b;
+            if (wc * ldw * elem + (size_t)G * 64 * elem <= budget) {
+                pf = p;
+                return G;
+            }
+        }
+    pf = 0;
     return 0;
 }
 
@@ -461,7 +555,8 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
     int *progress = reinterpret_cast<int *>(scratch);
     const int nsweeps = n - 2;
     const size_t kGroupBudget = 200 * 1024;
-    int G = chase_group_size(b, (int)sizeof(T), kGroupBudget);
+    int pf = 0;
+    int G = chase_group_size(b, (int)sizeof(T), kGroupBudget, pf);
     {  // NLA_CHASE_GROUP caps the sweeps per block (0: one sweep per block, global-memory band)
         static const int cap = [] {
             const char *v = getenv("NLA_CHASE_GROUP");
@@ -479,12 +574,12 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
                                  (int)kGroupBudget);
             gattr = true;
         }
-        const int wc = (3 * G - 1) * b + G + 1;
+        const int wc = (3 * G - 1) * b + G + 1 + pf * b;
         const size_t smem = (size_t)wc * ((3 * b + 2) & ~1) * sizeof(T) + (size_t)G * 64 * sizeof(T);
         const int grid = std::min(ngroups, device_sm_count());
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(32 * G);
+        cfg.blockDim = dim3(32 * (G + 1));
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
@@ -492,7 +587,7 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        err = cudaLaunchKernelEx(&cfg, band2bd_group_kernel<T>, AB, ldab, n, b, G, wc, progress, info);
+        err = cudaLaunchKernelEx(&cfg, band2bd_group_kernel<T>, AB, ldab, n, b, G, wc, pf, progress, info);
         if (err != cudaSuccess) return err;
     } else if (nsweeps > 0 && b > 1) {
         cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)nsweeps, st);
