@@ -362,28 +362,43 @@ NLA_DEV void group_need(int n, int b, int s0, int g, int tau, int &lo, int &hi, 
     }
 }
 
-// Mover warp: copy band columns j0..j1 (3b+1 storage rows each) from global
-// memory into the window, eight loads per lane in flight before their stores.
-template <typename T>
-NLA_DEV void mover_load(const Win<T> &W, const Band<T> &A, int n, int b, int j0, int j1, int lane) {
-    const int h = 3 * b + 1, tot = (j1 - j0 + 1) * h;
-    for (int base = 0; base < tot; base += 32 * 8) {
-        T r[8];
+// Mover warp: copy band columns j0..j1 (3b+1 storage rows each) between global
+// memory and the window.  Lanes walk the storage rows of a column; up to eight
+// columns' loads are in flight before their stores (3b+1 <= 2*32 rows per lane
+// pair for b <= 21, more passes otherwise).
+template <typename T, bool LOAD>
+NLA_DEV void mover_copy(const Win<T> &W, const Band<T> &A, int n, int b, int j0, int j1, int lane) {
+    const int h = 3 * b + 1;
+    for (int q0 = 0; q0 < h; q0 += 64) {
+        for (int jb = j0; jb <= j1; jb += 8) {
+            T r[8][2];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int idx = base + u * 32 + lane;
-            r[u] = T(0);
-            if (idx < tot) {
-                const int j = j0 + idx / h, i = j + idx % h - 2 * b;
-                if (i >= 0 && i < n) r[u] = __ldcg(A.at(i, j));
+            for (int u = 0; u < 8; ++u) {
+                const int j = jb + u;
+                if (j > j1) break;
+                const T *cw = W.col(j);
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int q = q0 + lane + 32 * h2, i = j + q - 2 * b;
+                    const bool in = q < h && i >= 0 && i < n;
+                    if (LOAD)
+                        r[u][h2] = in ? __ldcg(A.at(i, j)) : T(0);
+                    else if (in)
+                        __stcg(A.at(i, j), cw[i]);
+                }
             }
-        }
+            if (LOAD) {
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int idx = base + u * 32 + lane;
-            if (idx < tot) {
-                const int j = j0 + idx / h, i = j + idx % h - 2 * b;
-                if (i >= 0 && i < n) W.col(j)[i] = r[u];
+                for (int u = 0; u < 8; ++u) {
+                    const int j = jb + u;
+                    if (j > j1) break;
+                    T *cw = W.col(j);
+#pragma unroll
+                    for (int h2 = 0; h2 < 2; ++h2) {
+                        const int q = q0 + lane + 32 * h2, i = j + q - 2 * b;
+                        if (q < h && i >= 0 && i < n) cw[i] = r[u][h2];
+                    }
+                }
             }
         }
     }
@@ -394,6 +409,7 @@ NLA_DEV bool wait_loaded(volatile int *sh_hi, int hi, volatile int *sh_abort, in
     if (*sh_hi >= hi) return true;
     const unsigned long long t0 = global_ns();
     while (*sh_hi < hi) {
+        __nanosleep(40);  // leave the issue slots to the mover warp
         if (*sh_abort) return false;
         if (global_ns() - t0 > kSpinBudgetNs) {
             if (info) atomicExch(info, kInfoTimeout);
@@ -471,13 +487,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                 const int fin = active ? lo - 1 : loaded;  // columns <= fin are final
                 bool worked = false;
                 if (fin > flushed) {
-                    for (int j = flushed + 1; j <= fin; ++j) {
-                        const T *cw = W.col(j);
-                        for (int q = lane; q < 3 * b + 1; q += 32) {
-                            const int i = j + q - 2 * b;
-                            if (i >= 0 && i < n) __stcg(A.at(i, j), cw[i]);
-                        }
-                    }
+                    mover_copy<T, false>(W, A, n, b, flushed + 1, fin, lane);
                     flushed = fin;
                     __threadfence();
                     __syncwarp();
@@ -509,7 +519,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                         avail = min(want, have - 1);
                     }
                     if (avail > loaded) {
-                        mover_load<T>(W, A, n, b, loaded + 1, avail, lane);
+                        mover_copy<T, true>(W, A, n, b, loaded + 1, avail, lane);
                         loaded = avail;
                         __syncwarp();
                         __threadfence_block();

@@ -23,6 +23,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -466,9 +467,15 @@ static int cluster_plan(int M, int nb, int &R, size_t &dyn) {
     }
     int k0 = 0;
     while (k0 < 4 && (1 << k0) * kPanelRowsTarget < M) ++k0;  // smallest size with <= 256 rows per block
+    static const int force = [] {  // NLA_PANEL_CLUSTER: cluster size to use where it fits (0: grid kernel)
+        const char *v = getenv("NLA_PANEL_CLUSTER");
+        return v ? atoi(v) : -1;
+    }();
+    if (force == 0) return 0;
     int best = 0;
     for (int k = 0; k < 5; ++k) {
         if (!sched[k]) continue;
+        if (force > 0 && (1 << k) != force) continue;
         const int C = 1 << k;
         const int r = (M + C - 1) / C;
         const size_t d = (((size_t)r * nb * sizeof(T) + 15) & ~(size_t)15) + (size_t)2 * nb * nb * sizeof(double);

@@ -186,6 +186,7 @@ qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
             const unsigned char *sb = base + (size_t)st * stage;
             const int r0 = rbeg + t * th;  // trailing-matrix row of the stage's first row
+            const bool diag_stage = r0 < NB;  // only the stage holding V's unit diagonal needs masking
             for (int q = rw; q < 8 * BR; q += RW) {
                 const int bx = q >> 3, qq = q & 7;
                 const unsigned char *xb = sb + bx * xbytes;
@@ -194,23 +195,35 @@ qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
                 for (int i = 0; i < 4; ++i)
                     x[i] = *reinterpret_cast<const float4 *>(xb + (lane + 32 * i) * 128 + ((qq ^ (lane & 7)) << 4));
                 const float *vb = reinterpret_cast<const float *>(sb + BR * xbytes + bx * vbytes) + (16 * rg) * 32 + 4 * qq;
-                const int rq = r0 + bx * kBoxRows + 4 * qq;
-                const bool diag = rq < NB;  // the chunk meets V's unit diagonal
+                if (!diag_stage) {
 #pragma unroll
-                for (int a = 0; a < 16; ++a) {
-                    float4 v = *reinterpret_cast<const float4 *>(vb + a * 32);
-                    if (diag) {
+                    for (int a = 0; a < 16; ++a) {
+                        const float4 v = *reinterpret_cast<const float4 *>(vb + a * 32);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            float s4 = acc[a][i];
+                            s4 = fmaf(v.x, x[i].x, s4);
+                            s4 = fmaf(v.y, x[i].y, s4);
+                            s4 = fmaf(v.z, x[i].z, s4);
+                            acc[a][i] = fmaf(v.w, x[i].w, s4);
+                        }
+                    }
+                } else {
+                    const int rq = r0 + bx * kBoxRows + 4 * qq;
+#pragma unroll
+                    for (int a = 0; a < 16; ++a) {
+                        float4 v = *reinterpret_cast<const float4 *>(vb + a * 32);
                         const int k = 16 * rg + a;
                         v.x = unit_lower(rq, k, v.x), v.y = unit_lower(rq + 1, k, v.y);
                         v.z = unit_lower(rq + 2, k, v.z), v.w = unit_lower(rq + 3, k, v.w);
-                    }
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) {
-                        float s4 = acc[a][i];
-                        s4 = fmaf(v.x, x[i].x, s4);
-                        s4 = fmaf(v.y, x[i].y, s4);
-                        s4 = fmaf(v.z, x[i].z, s4);
-                        acc[a][i] = fmaf(v.w, x[i].w, s4);
+                        for (int i = 0; i < 4; ++i) {
+                            float s4 = acc[a][i];
+                            s4 = fmaf(v.x, x[i].x, s4);
+                            s4 = fmaf(v.y, x[i].y, s4);
+                            s4 = fmaf(v.z, x[i].z, s4);
+                            acc[a][i] = fmaf(v.w, x[i].w, s4);
+                        }
                     }
                 }
             }
@@ -325,24 +338,40 @@ lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             unsigned char *sb = base + (size_t)st * stage;
             const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
             const int cb = cbeg + t * tcols;
-            for (int j = cw; j < tcols; j += NC) {
-                float x[RL];
-                ld_rows<RL>(xptr_rows<RL>(sb, tcols, j, lane), x);
-                const int c = cb + j;
-                const bool diag = c < NB;
+            if (cb >= NB) {  // no column of this stage meets V's unit diagonal
+#pragma unroll 2
+                for (int j = cw; j < tcols; j += NC) {
+                    float x[RL];
+                    ld_rows<RL>(xptr_rows<RL>(sb, tcols, j, lane), x);
 #pragma unroll
-                for (int k4 = 0; k4 < NB; k4 += 4) {
-                    float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
-                    if (diag) {
+                    for (int k4 = 0; k4 < NB; k4 += 4) {
+                        const float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
+#pragma unroll
+                        for (int a = 0; a < RL; ++a) {
+                            acc[a][k4] = fmaf(x[a], q.x, acc[a][k4]);
+                            acc[a][k4 + 1] = fmaf(x[a], q.y, acc[a][k4 + 1]);
+                            acc[a][k4 + 2] = fmaf(x[a], q.z, acc[a][k4 + 2]);
+                            acc[a][k4 + 3] = fmaf(x[a], q.w, acc[a][k4 + 3]);
+                        }
+                    }
+                }
+            } else {
+                for (int j = cw; j < tcols; j += NC) {
+                    float x[RL];
+                    ld_rows<RL>(xptr_rows<RL>(sb, tcols, j, lane), x);
+                    const int c = cb + j;
+#pragma unroll
+                    for (int k4 = 0; k4 < NB; k4 += 4) {
+                        float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
                         q.x = unit_lower(c, k4, q.x), q.y = unit_lower(c, k4 + 1, q.y);
                         q.z = unit_lower(c, k4 + 2, q.z), q.w = unit_lower(c, k4 + 3, q.w);
-                    }
 #pragma unroll
-                    for (int a = 0; a < RL; ++a) {
-                        acc[a][k4] = fmaf(x[a], q.x, acc[a][k4]);
-                        acc[a][k4 + 1] = fmaf(x[a], q.y, acc[a][k4 + 1]);
-                        acc[a][k4 + 2] = fmaf(x[a], q.z, acc[a][k4 + 2]);
-                        acc[a][k4 + 3] = fmaf(x[a], q.w, acc[a][k4 + 3]);
+                        for (int a = 0; a < RL; ++a) {
+                            acc[a][k4] = fmaf(x[a], q.x, acc[a][k4]);
+                            acc[a][k4 + 1] = fmaf(x[a], q.y, acc[a][k4 + 1]);
+                            acc[a][k4 + 2] = fmaf(x[a], q.z, acc[a][k4 + 2]);
+                            acc[a][k4 + 3] = fmaf(x[a], q.w, acc[a][k4 + 3]);
+                        }
                     }
                 }
             }
@@ -493,28 +522,46 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
             unsigned char *sb = base + (size_t)st * stage;
             const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
             const int cb = cbeg + t * tcols;
-            for (int j = cw; j < tcols; j += NC) {
-                float *xp = xptr_rows<RL>(sb, tcols, j, lane);
-                float x[RL];
-                ld_rows<RL>(xp, x);
-                const int c = cb + j;
-                const bool diag = SIDE == 1 && c < NB;
+            if (SIDE == 0 || cb >= NB) {  // no column of this stage meets V's unit diagonal
+#pragma unroll 2
+                for (int j = cw; j < tcols; j += NC) {
+                    float *xp = xptr_rows<RL>(sb, tcols, j, lane);
+                    float x[RL];
+                    ld_rows<RL>(xp, x);
 #pragma unroll
-                for (int k4 = 0; k4 < NB; k4 += 4) {
-                    float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
-                    if (diag) {
+                    for (int k4 = 0; k4 < NB; k4 += 4) {
+                        const float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
+#pragma unroll
+                        for (int a = 0; a < RL; ++a) {
+                            x[a] = fmaf(-p[a][k4], q.x, x[a]);
+                            x[a] = fmaf(-p[a][k4 + 1], q.y, x[a]);
+                            x[a] = fmaf(-p[a][k4 + 2], q.z, x[a]);
+                            x[a] = fmaf(-p[a][k4 + 3], q.w, x[a]);
+                        }
+                    }
+                    st_rows<RL>(xp, x);
+                }
+            } else {
+                for (int j = cw; j < tcols; j += NC) {
+                    float *xp = xptr_rows<RL>(sb, tcols, j, lane);
+                    float x[RL];
+                    ld_rows<RL>(xp, x);
+                    const int c = cb + j;
+#pragma unroll
+                    for (int k4 = 0; k4 < NB; k4 += 4) {
+                        float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
                         q.x = unit_lower(c, k4, q.x), q.y = unit_lower(c, k4 + 1, q.y);
                         q.z = unit_lower(c, k4 + 2, q.z), q.w = unit_lower(c, k4 + 3, q.w);
-                    }
 #pragma unroll
-                    for (int a = 0; a < RL; ++a) {
-                        x[a] = fmaf(-p[a][k4], q.x, x[a]);
-                        x[a] = fmaf(-p[a][k4 + 1], q.y, x[a]);
-                        x[a] = fmaf(-p[a][k4 + 2], q.z, x[a]);
-                        x[a] = fmaf(-p[a][k4 + 3], q.w, x[a]);
+                        for (int a = 0; a < RL; ++a) {
+                            x[a] = fmaf(-p[a][k4], q.x, x[a]);
+                            x[a] = fmaf(-p[a][k4 + 1], q.y, x[a]);
+                            x[a] = fmaf(-p[a][k4 + 2], q.z, x[a]);
+                            x[a] = fmaf(-p[a][k4 + 3], q.w, x[a]);
+                        }
                     }
+                    st_rows<RL>(xp, x);
                 }
-                st_rows<RL>(xp, x);
             }
             tc::fence_async_smem();  // this lane's shared-memory writes -> visible to the TMA store
             __syncwarp();
