@@ -538,7 +538,9 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
 // (G = 0: none fits).
 static int chase_group_size(int b, int elem, size_t budget, int &pf) {
     const size_t ldw = (size_t)((3 * b + 2) & ~1);
-    for (int G = 16; G >= 1; --G)
+    // 8 sweeps per block measured fastest at n = 2048 and 8192, band 16 (more warps
+    // crowd the mover warp's issue slots; fewer lengthen the inter-group handoffs)
+    for (int G = 8; G >= 1; --G)
         for (int p : {4, 2, 1}) {
             const size_t wc = (size_t)(3 * G - 1) * b + G + 1 + (size_t)p * b;
             if (wc * ldw * elem + (size_t)G * 64 * elem <= budget) {
