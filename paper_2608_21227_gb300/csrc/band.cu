@@ -266,7 +266,10 @@ struct Win {
 };
 
 // One block step (right + left reflector) of sweep s at position k by one warp.
-template <typename T>
+// B = the band width when it is a compile-time constant (the inner loops over
+// the reflector are then unrolled and their shared-memory loads issue together),
+// 0 for the generic form.
+template <typename T, int B>
 NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) {
     const int lane = threadIdx.x & 31;
     const int c0 = s + k * b + 1;
@@ -275,6 +278,7 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) 
     const int cend = min(s + (k + 2) * b, n - 1);
     const int L = c1 - c0 + 1;
     if (L < 2) return;
+    constexpr int UB = B > 0 ? B : 1;
     const int sl0 = c0 % W.wc;
     // ---- right reflector on columns c0..c1 from row tr, applied to rows tr+1..c1
     T part = T(0);
@@ -300,9 +304,17 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) 
         for (int c = lane; c < L; c += 32) W.col_from(sl0, c0, c)[tr] = c == 0 ? beta : T(0);
         for (int i = tr + 1 + lane; i <= c1; i += 32) {  // one lane per row
             T w = T(0);
-            for (int c = 0; c < L; ++c) w += W.col_from(sl0, c0, c)[i] * v[c];
-            w *= tau;
-            for (int c = 0; c < L; ++c) W.col_from(sl0, c0, c)[i] -= w * v[c];
+            if (B > 0 && L == B) {
+#pragma unroll
+                for (int c = 0; c < UB; ++c) w += W.col_from(sl0, c0, c)[i] * v[c];
+                w *= tau;
+#pragma unroll
+                for (int c = 0; c < UB; ++c) W.col_from(sl0, c0, c)[i] -= w * v[c];
+            } else {
+                for (int c = 0; c < L; ++c) w += W.col_from(sl0, c0, c)[i] * v[c];
+                w *= tau;
+                for (int c = 0; c < L; ++c) W.col_from(sl0, c0, c)[i] -= w * v[c];
+            }
         }
         __syncwarp();
     }
@@ -330,9 +342,17 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) 
         for (int j = c0 + 1 + lane; j <= cend; j += 32) {  // one lane per column
             T *cj = W.col_from(sl0, c0, j - c0);
             T w = T(0);
-            for (int r = 0; r < L; ++r) w += v[r] * cj[c0 + r];
-            w *= tau;
-            for (int r = 0; r < L; ++r) cj[c0 + r] -= w * v[r];
+            if (B > 0 && L == B) {
+#pragma unroll
+                for (int r = 0; r < UB; ++r) w += v[r] * cj[c0 + r];
+                w *= tau;
+#pragma unroll
+                for (int r = 0; r < UB; ++r) cj[c0 + r] -= w * v[r];
+            } else {
+                for (int r = 0; r < L; ++r) w += v[r] * cj[c0 + r];
+                w *= tau;
+                for (int r = 0; r < L; ++r) cj[c0 + r] -= w * v[r];
+            }
         }
         __syncwarp();
     }
@@ -420,25 +440,26 @@ NLA_DEV bool wait_loaded(volatile int *sh_hi, int hi, volatile int *sh_abort, in
     return true;
 }
 
-// Block = G chase warps + one mover warp (warp G).  The chase warps run the
-// group's sweeps on the window in lockstep (named barrier 1 per wavefront step)
-// and never touch global memory; the mover keeps the window fed: it writes
-// back columns the group will not touch again and announces them in
-// done[group], and it loads up to `pf` steps ahead the columns the previous
-// group has released.  The window holds columns [flushed + 1, loaded] in
-// wc >= (3G - 1) b + G + 1 + pf b circular slots.
-template <typename T>
+// Block = G chase warps + a flusher warp (warp G) + a loader warp (warp G+1).
+// The chase warps run the group's sweeps on the window in lockstep (named
+// barrier 1 per wavefront step) and never touch global memory.  The flusher
+// writes back columns the group will not touch again and announces them in
+// done[group]; the loader brings in, up to `pf` steps ahead, the columns the
+// previous group has released.  The window holds columns [flushed + 1, loaded]
+// in wc >= (3G - 1) b + G + 1 + pf b circular slots.
+template <typename T, int B>
 __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int wc, int pf, int *done, int *info) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ int sh_tau, sh_hi, sh_abort;  // chase progress, loaded-up-to column, abort flag
-    const int ldw = (3 * b + 2) & ~1;          // even: lanes walking a row hit distinct banks
+    // chase progress, loaded-up-to column, flushed-up-to column, loader finished, abort flag
+    __shared__ int sh_tau, sh_hi, sh_fl, sh_ldone, sh_abort;
+    const int ldw = (3 * b + 2) & ~1;  // even: lanes walking a row hit distinct banks
     Win<T> W{reinterpret_cast<T *>(smem_raw), ldw, wc, 2 * b};
-    T *vbase = W.w + (size_t)wc * ldw;          // 64 entries per chase warp
+    T *vbase = W.w + (size_t)wc * ldw;  // 64 entries per chase warp
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     Band<T> A{AB, ldab, 2 * b};
     const int nsweeps = n - 2;
     const int ngroups = (nsweeps + G - 1) / G;
-    volatile int *vtau = &sh_tau, *vhi = &sh_hi, *vabort = &sh_abort;
+    volatile int *vtau = &sh_tau, *vhi = &sh_hi, *vfl = &sh_fl, *vldone = &sh_ldone, *vabort = &sh_abort;
     if (tid == 0) sh_abort = 0;
     for (int grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
         const int s0 = grp * G, g = min(G, nsweeps - s0);
@@ -448,6 +469,8 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
         if (tid == 0) {
             sh_tau = 0;
             sh_hi = lo0 - 1;
+            sh_fl = lo0 - 1;
+            sh_ldone = 0;
         }
         __syncthreads();
         if (*vabort) break;
@@ -465,7 +488,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                 __threadfence_block();
                 if (ok && warp < g) {
                     const int s = s0 + warp, k = tau - 3 * warp;
-                    if (k >= 0 && s + k * b + 1 <= n - 1) warp_chase_step<T>(W, n, b, s, k, v);
+                    if (k >= 0 && s + k * b + 1 <= n - 1) warp_chase_step<T, B>(W, n, b, s, k, v);
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(32 * G) : "memory");
                 if (*vabort) break;
@@ -474,9 +497,9 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                     *vtau = tau + 1;
                 }
             }
-        } else {
-            // ---------------- mover warp
-            int flushed = lo0 - 1, loaded = lo0 - 1;
+        } else if (warp == G) {
+            // ---------------- flusher
+            int flushed = lo0 - 1;
             for (;;) {
                 if (*vabort) break;
                 const int t = *vtau;  // steps < t are complete
@@ -484,23 +507,60 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                 int lo, hi;
                 bool active;
                 group_need(n, b, s0, g, t, lo, hi, active);
-                const int fin = active ? lo - 1 : loaded;  // columns <= fin are final
-                bool worked = false;
+                if (!active) {  // the group is done: every loaded column is final
+                    if (lane == 0) {
+                        const unsigned long long t0 = global_ns();
+                        while (!*vldone && !*vabort) {
+                            __nanosleep(64);
+                            if (global_ns() - t0 > kSpinBudgetNs) {
+                                if (info) atomicExch(info, kInfoTimeout);
+                                *vabort = 1;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    __threadfence_block();
+                    if (*vabort) break;
+                    const int fin = *vhi;
+                    if (fin > flushed) mover_copy<T, false>(W, A, n, b, flushed + 1, fin, lane);
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) st_release(&done[grp], INT_MAX);
+                    break;
+                }
+                const int fin = lo - 1;  // columns <= fin are final
                 if (fin > flushed) {
                     mover_copy<T, false>(W, A, n, b, flushed + 1, fin, lane);
                     flushed = fin;
                     __threadfence();
                     __syncwarp();
-                    if (lane == 0) st_release(&done[grp], active ? flushed + 1 : INT_MAX);
-                    worked = true;
+                    if (lane == 0) {
+                        st_release(&done[grp], flushed + 1);
+                        *vfl = flushed;  // the loader may reuse these slots now
+                    }
+                } else {
+                    __nanosleep(32);
                 }
+            }
+        } else {
+            // ---------------- loader
+            int loaded = lo0 - 1;
+            for (;;) {
+                if (*vabort) break;
+                const int t = *vtau;
+                __threadfence_block();
+                int lo, hi;
+                bool active;
+                group_need(n, b, s0, g, t, lo, hi, active);
                 if (!active) break;
-                // load ahead: the columns steps t .. t + pf need, within the window's capacity
+                // the columns steps t .. t + pf need, within the window's capacity
                 int lt, want;
                 bool at;
                 group_need(n, b, s0, g, t + pf, lt, want, at);
                 want = max(want, hi);
-                want = min(want, flushed + wc);
+                want = min(want, *vfl + wc);
+                __threadfence_block();
+                bool worked = false;
                 if (want > loaded) {
                     int avail = want;
                     if (grp > 0) {
@@ -529,6 +589,9 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                 }
                 if (!worked) __nanosleep(32);
             }
+            __syncwarp();
+            __threadfence_block();
+            if (lane == 0) *vldone = 1;
         }
         __syncthreads();
     }
@@ -536,11 +599,9 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
 
 // Sweeps per block group and prefetch depth that fit the shared-memory window
 // (G = 0: none fits).
-static int chase_group_size(int b, int elem, size_t budget, int &pf) {
+static int chase_group_size(int b, int elem, size_t budget, int gmax, int &pf) {
     const size_t ldw = (size_t)((3 * b + 2) & ~1);
-    // 8 sweeps per block measured fastest at n = 2048 and 8192, band 16 (more warps
-    // crowd the mover warp's issue slots; fewer lengthen the inter-group handoffs)
-    for (int G = 8; G >= 1; --G)
+    for (int G = gmax; G >= 1; --G)
         for (int p : {4, 2, 1}) {
             const size_t wc = (size_t)(3 * G - 1) * b + G + 1 + (size_t)p * b;
             if (wc * ldw * elem + (size_t)G * 64 * elem <= budget) {
@@ -567,22 +628,28 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
     int *progress = reinterpret_cast<int *>(scratch);
     const int nsweeps = n - 2;
     const size_t kGroupBudget = 200 * 1024;
+    // 8 sweeps per block measured fastest at n = 2048 and 8192, band 16 (more warps
+    // crowd the mover warps' issue slots; fewer lengthen the inter-group handoffs).
+    // NLA_CHASE_GROUP overrides it (0: one sweep per block on the global band).
+    static const int gset = [] {
+        const char *v = getenv("NLA_CHASE_GROUP");
+        return v ? atoi(v) : 8;
+    }();
     int pf = 0;
-    int G = chase_group_size(b, (int)sizeof(T), kGroupBudget, pf);
-    {  // NLA_CHASE_GROUP caps the sweeps per block (0: one sweep per block, global-memory band)
-        static const int cap = [] {
-            const char *v = getenv("NLA_CHASE_GROUP");
-            return v ? atoi(v) : -1;
-        }();
-        if (cap >= 0) G = std::min(G, cap);
-    }
+    int G = gset > 0 ? chase_group_size(b, (int)sizeof(T), kGroupBudget, std::min(gset, 30), pf) : 0;
     if (nsweeps > 0 && b > 1 && G >= 1) {
         const int ngroups = (nsweeps + G - 1) / G;
         cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)ngroups, st);
         if (err != cudaSuccess) return err;
         static bool gattr = false;
         if (!gattr) {
-            cudaFuncSetAttribute(band2bd_group_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            cudaFuncSetAttribute(band2bd_group_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kGroupBudget);
+            cudaFuncSetAttribute(band2bd_group_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kGroupBudget);
+            cudaFuncSetAttribute(band2bd_group_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kGroupBudget);
+            cudaFuncSetAttribute(band2bd_group_kernel<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kGroupBudget);
             gattr = true;
         }
@@ -591,7 +658,7 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
         const int grid = std::min(ngroups, device_sm_count());
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);
-        cfg.blockDim = dim3(32 * (G + 1));
+        cfg.blockDim = dim3(32 * (G + 2));
         cfg.dynamicSmemBytes = smem;
         cfg.stream = st;
         cudaLaunchAttribute attr[1];
@@ -599,7 +666,10 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        err = cudaLaunchKernelEx(&cfg, band2bd_group_kernel<T>, AB, ldab, n, b, G, wc, pf, progress, info);
+        auto kern = b == 16 ? band2bd_group_kernel<T, 16>
+                    : b == 32 ? band2bd_group_kernel<T, 32>
+                    : b == 64 ? band2bd_group_kernel<T, 64> : band2bd_group_kernel<T, 0>;
+        err = cudaLaunchKernelEx(&cfg, kern, AB, ldab, n, b, G, wc, pf, progress, info);
         if (err != cudaSuccess) return err;
     } else if (nsweeps > 0 && b > 1) {
         cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)nsweeps, st);

@@ -27,6 +27,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -255,27 +256,74 @@ panel_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, T *__res
 
 // ------------------------------------------------------------------ cluster variant
 // Same algorithm with the panel spread over one thread-block cluster (up to 16
-// blocks on one GPC): the per-column partial sums live in each block's shared
-// memory, are read by every block through distributed shared memory, and the
-// hardware cluster barrier replaces the global counter barrier.
+// blocks on one GPC).  Per column each block pushes its partial sums (and the
+// owner block row j) into every block's shared memory over distributed shared
+// memory and arrives on every block's mbarrier; a block waits only on its own
+// barrier, so the exchange costs one remote write latency instead of a
+// cluster-wide barrier plus remote reads.
+constexpr int kClusterThreads = 512;
+
+NLA_DEV uint32_t cluster_addr(const void *local, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(tc::smem_u32(local)), "r"(rank));
+    return r;
+}
+NLA_DEV void mbar_arrive_remote(uint32_t cluster_mbar) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cluster_mbar) : "memory");
+}
+NLA_DEV bool mbar_try_wait_cluster(uint64_t *mbar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(tc::smem_u32(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Dot product of two columns over rows [lo, hi) of the block, four independent
+// partial sums per lane, then a warp reduction.
 template <typename T>
-__global__ void __launch_bounds__(kPanelThreads)
+NLA_DEV T warp_dot(const T *x, const T *y, int lo, int hi, int lane) {
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int r = lo + lane;
+    for (; r + 96 < hi; r += 128) {
+        a0 += x[r] * y[r];
+        a1 += x[r + 32] * y[r + 32];
+        a2 += x[r + 64] * y[r + 64];
+        a3 += x[r + 96] * y[r + 96];
+    }
+    for (; r < hi; r += 32) a0 += x[r] * y[r];
+    return warp_sum((a0 + a1) + (a2 + a3));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kClusterThreads)
 panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, T *__restrict__ tau,
-                     T *__restrict__ Tm) {
+                     T *__restrict__ Tm, int *info) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cg::cluster_group cluster = cg::this_cluster();
     const int p = (int)cluster.block_rank(), nP = (int)cluster.num_blocks();
     T *S = reinterpret_cast<T *>(smem_raw);  // R x nb
     double *Gs = reinterpret_cast<double *>(smem_raw + (((size_t)R * nb * sizeof(T) + 15) & ~(size_t)15));
     double *Ts = Gs + (size_t)nb * nb;
-    __shared__ double cpart[2][kNbMax + 1];  // this block's partial sums, double-buffered by column parity
-    __shared__ double rowb[2][kNbMax + 1];   // row j (owner block only)
+    __shared__ double inbox[2][16][kNbMax + 1];  // partials pushed by each block, by column parity
+    __shared__ double rowin[2][kNbMax + 1];      // row j pushed by its owner block
+    __shared__ double mypart[kNbMax + 1];
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ T wcoef[kNbMax + 1];
     __shared__ double sh_tau, sh_beta, sh_scale;
+    __shared__ int sh_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int r0 = p * R;
     const int nr = max(0, min(M, r0 + R) - r0);
     const int kmax = min(nb, M);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], nP);
+        tc::mbar_init(&mbar[1], nP);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh_abort = 0;
+    }
     if (p == 0)
         for (int j = kmax + tid; j < nb; j += blockDim.x) tau[j] = T(0);
     if (cs == 1) {
@@ -289,54 +337,52 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
             S[(size_t)c * R + rr] = P[(long)(r0 + rr) * rs + (long)c * cs];
         }
     }
-    __syncthreads();
+    cluster.sync();  // every block's barriers are initialised before the first remote arrive
     for (int j = 0; j < kmax; ++j) {
         const int buf = j & 1;
         const int nitem = nb - j;
         const int rr_lo = max(0, j + 1 - r0);
         const T *xj = S + (size_t)j * R;
         for (int it = warp; it < nitem; it += nwarps) {
-            double sacc;
-            if (it == 0) {
-                T s2 = T(0);
-                for (int rr = rr_lo + lane; rr < nr; rr += 32) s2 += xj[rr] * xj[rr];
-                sacc = (double)warp_sum(s2);
-            } else {
-                const T *ac = S + (size_t)(j + it) * R;
-                T s1 = T(0);
-                for (int rr = rr_lo + lane; rr < nr; rr += 32) s1 += xj[rr] * ac[rr];
-                sacc = (double)warp_sum(s1);
-            }
-            if (lane == 0) cpart[buf][it] = sacc;
+            const T *ac = S + (size_t)(j + it) * R;  // item 0: ||x||^2; item t > 0: x . a_{j+t}
+            const T d = warp_dot<T>(xj, ac, rr_lo, nr, lane);
+            if (lane == 0) mypart[it] = (double)d;
         }
+        __syncthreads();
+        // push this block's partials (and row j, by its owner) to every block of the cluster
         const int owner = j / R;
-        if (p == owner)
-            for (int c = j + tid; c < nb; c += blockDim.x) rowb[buf][c - j] = (double)S[(size_t)c * R + (j - r0)];
-        cluster.sync();
-        // warp 0: fixed-order sum over the cluster's blocks (every remote load in
-        // flight at once), the reflector in the panel's precision, and the update
-        // coefficients w_c = tau (a_jc + x . a_c / (alpha - beta)) = tau v . a_c
+        for (int idx = tid; idx < nP * nitem; idx += blockDim.x) {
+            const int q = idx / nitem, it = idx % nitem;
+            cluster.map_shared_rank(&inbox[buf][p][0], q)[it] = mypart[it];
+            if (p == owner) cluster.map_shared_rank(&rowin[buf][0], q)[it] = (double)S[(size_t)(j + it) * R + (j - r0)];
+        }
+        __syncthreads();  // all of this block's pushes precede its arrivals
+        if (tid < nP) mbar_arrive_remote(cluster_addr(&mbar[buf], tid));
+        // warp 0: wait for every block's partials, sum them in a fixed order, form the
+        // reflector in the panel's precision and the coefficients w_c = tau v . a_c
         if (warp == 0) {
-            const int i0 = lane, i1 = lane + 32;  // items: nitem <= kNbMax = 64
-            double s0 = 0.0, s1 = 0.0, w0 = 0.0, w1 = 0.0;
-            {
-                double v0[16], v1[16];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    v0[q] = 0.0;
-                    v1[q] = 0.0;
-                    if (q < nP) {
-                        const double *cp = cluster.map_shared_rank(&cpart[buf][0], q);
-                        if (i0 < nitem) v0[q] = cp[i0];
-                        if (i1 < nitem) v1[q] = cp[i1];
+            if (lane == 0 && !sh_abort) {
+                const uint32_t par = (uint32_t)((j >> 1) & 1);
+                if (!mbar_try_wait_cluster(&mbar[buf], par)) {
+                    const unsigned long long t0 = global_ns();
+                    while (!mbar_try_wait_cluster(&mbar[buf], par)) {
+                        if (global_ns() - t0 > kSpinBudgetNs) {
+                            if (info) atomicExch(info, kInfoTimeout);
+                            sh_abort = 1;
+                            break;
+                        }
                     }
                 }
-                const double *rb = cluster.map_shared_rank(&rowb[buf][0], owner);
-                if (i0 < nitem) w0 = rb[i0];
-                if (i1 < nitem) w1 = rb[i1];
-#pragma unroll
-                for (int q = 0; q < 16; ++q) s0 += v0[q], s1 += v1[q];
             }
+            __syncwarp();  // lane 0's acquire orders the warp's reads below
+            const int i0 = lane, i1 = lane + 32;  // nitem <= kNbMax = 64
+            double s0 = 0.0, s1 = 0.0, w0 = 0.0, w1 = 0.0;
+            for (int q = 0; q < nP; ++q) {
+                if (i0 < nitem) s0 += inbox[buf][q][i0];
+                if (i1 < nitem) s1 += inbox[buf][q][i1];
+            }
+            if (i0 < nitem) w0 = rowin[buf][i0];
+            if (i1 < nitem) w1 = rowin[buf][i1];
             const T alpha = (T)__shfl_sync(0xffffffffu, w0, 0), xn2 = (T)__shfl_sync(0xffffffffu, s0, 0);
             T tj = T(0), beta = alpha, scale = T(0);
             if (xn2 > T(0)) {
@@ -427,314 +473,6 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
     }
 }
 
-// ------------------------------------------------------------------ TSQR variant
-// Communication-avoiding panel: each block of the cluster factors its own rows
-// (local Householder QR, block barriers only), block 0 factors the stacked
-// triangular factors, every block forms its rows of the explicit Q1 = Q(:, 0:nb),
-// and the compact-WY pair (V, T) of the Householder QR of the whole panel is
-// recovered from Q1 by an LU factorisation without pivoting (Householder
-// reconstruction): with Sigma = diag(+-1) chosen on the fly so that every pivot
-// has magnitude >= 1,
-//     Q1 - [Sigma; 0] = V U,   T = -U Sigma V1^{-T},   R := Sigma R,
-// since I - V T V^T has first columns Q1 Sigma (V1 = top nb x nb block of V).
-// Four cluster barriers per panel instead of one per column.
-
-// Householder QR of the rows x cols column-major block A (column c at A + c*ld)
-// by one thread block: reflector tails overwrite the strictly lower part, R the
-// upper part, tau[cols].  Warp 0 forms each reflector; each warp then applies it
-// to the columns it owns.
-template <typename T>
-__device__ void block_house_qr(T *A, int ld, int rows, int cols, T *tau, T *sc) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int j = 0; j < cols; ++j) {
-        if (warp == 0) {
-            T *x = A + (size_t)j * ld;
-            if (j > 0) {  // finish the previous column: v = x / (alpha - beta), R entry = beta
-                T *xp = A + (size_t)(j - 1) * ld;
-                const T s0 = sc[1];
-                for (int r = j + lane; r < rows; r += 32) xp[r] *= s0;
-                if (lane == 0) xp[j - 1] = sc[2];
-            }
-            T s2 = T(0);
-            for (int r = j + 1 + lane; r < rows; r += 32) s2 += x[r] * x[r];
-            s2 = warp_sum(s2);
-            if (lane == 0) {
-                const T alpha = x[j];
-                T tj = T(0), beta = alpha, scale = T(0);
-                if (s2 > T(0)) {
-                    const T rr = sqrt(alpha * alpha + s2);
-                    beta = alpha >= T(0) ? -rr : rr;
-                    tj = (beta - alpha) / beta;
-                    scale = T(1) / (alpha - beta);
-                }
-                tau[j] = tj;
-                sc[0] = tj;
-                sc[1] = tj != T(0) ? scale : T(0);
-                sc[2] = tj != T(0) ? beta : alpha;
-            }
-        }
-        __syncthreads();
-        const T tj = sc[0], scale = sc[1];
-        if (tj != T(0)) {
-            const T *x = A + (size_t)j * ld;
-            for (int c = j + 1 + warp; c < cols; c += nw) {
-                T *a = A + (size_t)c * ld;
-                T d = T(0);
-                for (int r = j + 1 + lane; r < rows; r += 32) d += x[r] * a[r];
-                d = warp_sum(d);
-                const T w = tj * (a[j] + scale * d);
-                for (int r = j + 1 + lane; r < rows; r += 32) a[r] -= w * scale * x[r];
-                __syncwarp();
-                if (lane == 0) a[j] -= w;
-            }
-        }
-        __syncthreads();
-    }
-    if (warp == 0 && cols > 0) {
-        T *xp = A + (size_t)(cols - 1) * ld;
-        const T s0 = sc[1];
-        for (int r = cols + lane; r < rows; r += 32) xp[r] *= s0;
-        if (lane == 0) xp[cols - 1] = sc[2];
-    }
-    __syncthreads();
-}
-
-// Q <- H_0 H_1 ... H_{k-1} Q for the reflectors stored in V (unit lower, rows x k,
-// column c at V + c*ldv) and tau; Q is rows x cols (column c at Q + c*ldq).  Each
-// warp owns whole columns of Q, so no barrier is needed between reflectors.
-template <typename T>
-__device__ void block_apply_q(const T *V, int ldv, const T *tau, int k, T *Q, int ldq, int rows, int cols) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int c = warp; c < cols; c += nw) {
-        T *q = Q + (size_t)c * ldq;
-        for (int i = k - 1; i >= 0; --i) {
-            const T ti = tau[i];
-            if (ti == T(0)) continue;
-            const T *v = V + (size_t)i * ldv;
-            T d = T(0);
-            for (int r = i + 1 + lane; r < rows; r += 32) d += v[r] * q[r];
-            d = warp_sum(d) + q[i];
-            const T w = ti * d;
-            for (int r = i + 1 + lane; r < rows; r += 32) q[r] -= w * v[r];
-            __syncwarp();
-            if (lane == 0) q[i] -= w;
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kPanelThreads)
-panel_tsqr_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, T *__restrict__ tau,
-                  T *__restrict__ Tm) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cg::cluster_group cluster = cg::this_cluster();
-    const int p = (int)cluster.block_rank(), nP = (int)cluster.num_blocks();
-    const int ZR = nP * nb;  // rows of the stacked triangular factors
-    T *S = reinterpret_cast<T *>(smem_raw);  // R x nb: local rows, then local V / R
-    T *Qb = S + (size_t)R * nb;              // R x nb: local rows of Q1, then of V
-    T *Z = Qb + (size_t)R * nb;              // ZR x nb (block 0): stacked R's -> top V / R
-    T *Qt = Z + (size_t)ZR * nb;             // ZR x nb (block 0): explicit top Q
-    T *U = Qt + (size_t)ZR * nb;             // nb x nb (column-major), LU upper factor
-    T *taul = U + (size_t)nb * nb;           // nb local taus
-    T *taut = taul + kNbMax;                 // nb top taus
-    T *sg = taut + kNbMax;                   // nb signs
-    T *sc = sg + kNbMax;                     // 4 scratch scalars
-    const int tid = threadIdx.x;
-    const int r0 = p * R;
-    const int nr = max(0, min(M, r0 + R) - r0);  // >= nb (host guarantees)
-    // ---- load this block's rows
-    if (cs == 1) {
-        for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
-            const int c = idx % nb, rr = idx / nb;
-            S[(size_t)c * R + rr] = P[(long)(r0 + rr) * rs + c];
-        }
-    } else {
-        for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
-            const int rr = idx % nr, c = idx / nr;
-            S[(size_t)c * R + rr] = P[(long)(r0 + rr) * rs + (long)c * cs];
-        }
-    }
-    __syncthreads();
-    // ---- 1. local QR
-    block_house_qr<T>(S, R, nr, nb, taul, sc);
-    cluster.sync();  // every R_q ready
-    // ---- 2. block 0: QR of the stacked R's and the explicit top Q
-    if (p == 0) {
-        for (int idx = tid; idx < ZR * nb; idx += blockDim.x) {
-            const int c = idx / ZR, zr = idx % ZR, q = zr / nb, i = zr % nb;
-            T v = T(0);
-            if (i <= c) v = cluster.map_shared_rank(S, q)[(size_t)c * R + i];
-            Z[(size_t)c * ZR + zr] = v;
-            Qt[(size_t)c * ZR + zr] = zr == c ? T(1) : T(0);
-        }
-        __syncthreads();
-        block_house_qr<T>(Z, ZR, ZR, nb, taut, sc);
-        block_apply_q<T>(Z, ZR, taut, nb, Qt, ZR, ZR, nb);
-    }
-    cluster.sync();  // Qt ready
-    // ---- 3. local rows of Q1 = Q_p [Qt(p*nb : p*nb+nb, :); 0]
-    {
-        const T *qt = cluster.map_shared_rank(Qt, 0);
-        for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
-            const int c = idx / nr, rr = idx % nr;
-            Qb[(size_t)c * R + rr] = rr < nb ? qt[(size_t)c * ZR + p * nb + rr] : T(0);
-        }
-        __syncthreads();
-        block_apply_q<T>(S, R, taul, nb, Qb, R, nr, nb);
-    }
-    // ---- 4. block 0: LU without pivoting of Q1(0:nb, :) - Sigma (one warp, nb <= 64)
-    if (p == 0) {
-        if (tid < 32) {
-            const int lane = tid;
-            for (int i = 0; i < nb; ++i) {
-                // pivot column i: rows i..nb-1 already updated by steps < i
-                const T a = Qb[(size_t)i * R + i];
-                const T s = a >= T(0) ? T(-1) : T(1);  // -sign(a), sign(0) = +1
-                const T piv = a - s;
-                if (lane == 0) {
-                    sg[i] = s;
-                    Qb[(size_t)i * R + i] = piv;
-                }
-                __syncwarp();
-                const T inv = T(1) / piv;
-                for (int k = i + 1 + lane; k < nb; k += 32) Qb[(size_t)i * R + k] *= inv;  // L(k, i)
-                __syncwarp();
-                // trailing update of rows i+1.., columns i+1..
-                for (int c = i + 1; c < nb; ++c) {
-                    const T u = Qb[(size_t)c * R + i];
-                    for (int k = i + 1 + lane; k < nb; k += 32) Qb[(size_t)c * R + k] -= Qb[(size_t)i * R + k] * u;
-                }
-                __syncwarp();
-            }
-            // U (upper, incl. diagonal) to its own array
-            for (int idx = lane; idx < nb * nb; idx += 32) {
-                const int c = idx / nb, i = idx % nb;
-                U[(size_t)c * nb + i] = i <= c ? Qb[(size_t)c * R + i] : T(0);
-            }
-        }
-        __syncthreads();
-    }
-    cluster.sync();  // U, Sigma ready
-    // ---- 5. V rows = Q1 rows U^{-1} (block 0: rows >= nb; rows < nb hold L1 from the LU)
-    {
-        const T *Uu = U;
-        if (p != 0) {  // local copy of block 0's U (this block's Z is unused)
-            const T *Ur = cluster.map_shared_rank(U, 0);
-            for (int idx = tid; idx < nb * nb; idx += blockDim.x) Z[idx] = Ur[idx];
-            __syncthreads();
-            Uu = Z;
-        }
-        const int rbeg = (p == 0) ? nb : 0;
-        for (int rr = rbeg + tid; rr < nr; rr += blockDim.x) {
-            for (int i = 0; i < nb; ++i) {
-                T x = Qb[(size_t)i * R + rr];
-                for (int j = 0; j < i; ++j) x -= Qb[(size_t)j * R + rr] * Uu[(size_t)i * nb + j];
-                Qb[(size_t)i * R + rr] = x / Uu[(size_t)i * nb + i];
-            }
-        }
-        __syncthreads();
-    }
-    // ---- 6. write back: V below the diagonal, Sigma R on and above it (block 0)
-    if (cs == 1) {
-        for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
-            const int c = idx % nb, rr = idx / nb, r = r0 + rr;
-            T v;
-            if (r > c)
-                v = Qb[(size_t)c * R + rr];
-            else
-                v = sg[r] * Z[(size_t)c * ZR + r];
-            P[(long)r * rs + c] = v;
-        }
-    } else {
-        for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
-            const int rr = idx % nr, c = idx / nr, r = r0 + rr;
-            T v;
-            if (r > c)
-                v = Qb[(size_t)c * R + rr];
-            else
-                v = sg[r] * Z[(size_t)c * ZR + r];
-            P[(long)r * rs + (long)c * cs] = v;
-        }
-    }
-    // ---- 7. block 0: T = -U Sigma V1^{-T} (upper triangular), tau = diag(T).
-    // Row rr of T solves V1 x = -(U Sigma)(rr, :)^T (V1 unit lower = L1 in Qb).
-    if (p == 0) {
-        for (int rr = tid; rr < nb; rr += blockDim.x) {
-            for (int i = 0; i < nb; ++i) {
-                T x = T(0);
-                if (i >= rr) {
-                    x = -U[(size_t)i * nb + rr] * sg[i];
-                    for (int j = rr; j < i; ++j) x -= Qb[(size_t)j * R + i] * Tm[rr + (size_t)j * nb];
-                }
-                Tm[rr + (size_t)i * nb] = x;
-            }
-            tau[rr] = Tm[rr + (size_t)rr * nb];
-        }
-    }
-    cluster.sync();  // remote reads of every block's shared memory are done
-}
-
-// Cluster size and rows per block for the TSQR panel, or 0 when it does not apply:
-// 2..16 blocks of <= 512 rows, every block at least nb rows, everything in shared memory.
-template <typename T>
-static int tsqr_plan(int M, int nb, int &R, size_t &dyn) {
-    static bool init = false;
-    static size_t max_dyn = 0;
-    static bool sched[5] = {false, false, false, false, false};
-    if (!init) {
-        init = true;
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, panel_tsqr_kernel<T>) == cudaSuccess && (size_t)optin > fa.sharedSizeBytes)
-            max_dyn = (size_t)optin - fa.sharedSizeBytes;
-        if (cudaFuncSetAttribute(panel_tsqr_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dyn) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(panel_tsqr_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-                cudaSuccess)
-            max_dyn = 0;
-        for (int k = 1; k < 5 && max_dyn > 0; ++k) {
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(1u << k);
-            cfg.blockDim = dim3(kPanelThreads);
-            cfg.dynamicSmemBytes = max_dyn;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = 1u << k;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            int ncl = 0;
-            sched[k] = cudaOccupancyMaxActiveClusters(&ncl, panel_tsqr_kernel<T>, &cfg) == cudaSuccess && ncl >= 1;
-        }
-        cudaGetLastError();
-    }
-    static const int mode = [] {  // NLA_PANEL_TSQR=0 disables this variant
-        const char *v = getenv("NLA_PANEL_TSQR");
-        return v ? atoi(v) : 1;
-    }();
-    if (!mode || nb > kNbMax || M < 2 * nb) return 0;
-    for (int k = 1; k < 5; ++k) {
-        const int C = 1 << k;
-        if (!sched[k]) continue;
-        const int r = (M + C - 1) / C;
-        if (r > 512 && k < 4) continue;        // prefer <= 512 rows per block
-        if (M - (C - 1) * r < nb) break;       // the last block needs nb rows
-        const size_t zr = (size_t)C * nb;
-        const size_t elems = 2 * (size_t)r * nb + 2 * zr * nb + (size_t)nb * nb + 3 * kNbMax + 4;
-        const size_t d = elems * sizeof(T);
-        if (d > max_dyn) continue;
-        R = r;
-        dyn = d;
-        return C;
-    }
-    return 0;
-}
-
 // Cluster size and rows per block for an M x nb panel, or 0 if it does not fit one cluster.
 // Which cluster sizes the device can schedule (one block per SM at the largest
 // dynamic shared memory) is asked once; smaller allocations schedule as well.
@@ -759,7 +497,7 @@ static int cluster_plan(int M, int nb, int &R, size_t &dyn) {
         for (int k = 0; k < 5 && max_dyn > 0; ++k) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(1u << k);
-            cfg.blockDim = dim3(kPanelThreads);
+            cfg.blockDim = dim3(kClusterThreads);
             cfg.dynamicSmemBytes = max_dyn;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -801,36 +539,14 @@ cudaError_t panel_factor(T *P, long rs, long cs, int M, int nb, T *tau, T *Tm, c
                          cudaStream_t st) {
     if (M <= 0 || nb <= 0) return cudaSuccess;
     if (nb > kNbMax) return cudaErrorInvalidValue;
-    {  // preferred: TSQR + Householder reconstruction in one cluster (four cluster barriers)
-        int R = 0;
-        size_t dyn = 0;
-        const int C = tsqr_plan<T>(M, nb, R, dyn);
-        if (C > 0) {
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(C);
-            cfg.blockDim = dim3(kPanelThreads);
-            cfg.dynamicSmemBytes = dyn;
-            cfg.stream = st;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = C;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            cudaError_t e = cudaLaunchKernelEx(&cfg, panel_tsqr_kernel<T>, P, rs, cs, M, nb, R, tau, Tm);
-            if (e == cudaSuccess) return e;
-            cudaGetLastError();
-        }
-    }
-    {  // next: one thread-block cluster, one cluster barrier per column
+    {  // preferred: one thread-block cluster, no global barrier
         int R = 0;
         size_t dyn = 0;
         const int C = cluster_plan<T>(M, nb, R, dyn);
         if (C > 0) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(C);
-            cfg.blockDim = dim3(kPanelThreads);
+            cfg.blockDim = dim3(kClusterThreads);
             cfg.dynamicSmemBytes = dyn;
             cfg.stream = st;
             cudaLaunchAttribute attr[1];
@@ -840,7 +556,7 @@ cudaError_t panel_factor(T *P, long rs, long cs, int M, int nb, T *tau, T *Tm, c
             attr[0].val.clusterDim.z = 1;
             cfg.attrs = attr;
             cfg.numAttrs = 1;
-            cudaError_t e = cudaLaunchKernelEx(&cfg, panel_cluster_kernel<T>, P, rs, cs, M, nb, R, tau, Tm);
+            cudaError_t e = cudaLaunchKernelEx(&cfg, panel_cluster_kernel<T>, P, rs, cs, M, nb, R, tau, Tm, ctl.info);
             if (e == cudaSuccess) return e;
             cudaGetLastError();  // fall back to the grid-wide version
         }
