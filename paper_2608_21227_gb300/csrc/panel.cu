@@ -305,14 +305,19 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
     cg::cluster_group cluster = cg::this_cluster();
     const int p = (int)cluster.block_rank(), nP = (int)cluster.num_blocks();
     T *S = reinterpret_cast<T *>(smem_raw);  // R x nb
-    double *Gs = reinterpret_cast<double *>(smem_raw + (((size_t)R * nb * sizeof(T) + 15) & ~(size_t)15));
-    double *Ts = Gs + (size_t)nb * nb;
-    __shared__ double inbox[2][16][kNbMax + 1];  // partials pushed by each block, by column parity
-    __shared__ double rowin[2][kNbMax + 1];      // row j pushed by its owner block
-    __shared__ double mypart[kNbMax + 1];
+    // Per column j the blocks exchange nb partial sums over their rows below j:
+    //   item 0            ||x||^2                     (x = column j below row j)
+    //   item t in 1..nb-1-j   x . a_{j+t}             (trailing columns)
+    //   item nb-j+i, i < j    x . v_i                 (finished reflectors: G(i, j))
+    // and the owner of row j pushes row j at the same positions (a_j,j+t and v_i[j]).
+    __shared__ T inbox[2][16][kNbMax];  // by column parity and source block
+    __shared__ T rowin[2][kNbMax];
+    __shared__ T mypart[kNbMax];
+    __shared__ T wcoef[kNbMax];
+    __shared__ T gcol[kNbMax];
+    __shared__ T Tsh[kNbMax * kNbMax];  // T(i, k) at Tsh[i + k*nb] (block 0)
     __shared__ __align__(8) uint64_t mbar[2];
-    __shared__ T wcoef[kNbMax + 1];
-    __shared__ double sh_tau, sh_beta, sh_scale;
+    __shared__ T sh_tau, sh_beta, sh_scale;
     __shared__ int sh_abort;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
     const int r0 = p * R;
@@ -324,8 +329,10 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sh_abort = 0;
     }
-    if (p == 0)
+    if (p == 0) {
         for (int j = kmax + tid; j < nb; j += blockDim.x) tau[j] = T(0);
+        for (int i = tid; i < nb * nb; i += blockDim.x) Tsh[i] = T(0);
+    }
     if (cs == 1) {
         for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
             int c = idx % nb, rr = idx / nb;
@@ -340,26 +347,29 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
     cluster.sync();  // every block's barriers are initialised before the first remote arrive
     for (int j = 0; j < kmax; ++j) {
         const int buf = j & 1;
-        const int nitem = nb - j;
+        const int ntr = nb - j;  // items 0 .. ntr-1: norm and trailing columns; ntr .. nb-1: G(i, j)
         const int rr_lo = max(0, j + 1 - r0);
         const T *xj = S + (size_t)j * R;
-        for (int it = warp; it < nitem; it += nwarps) {
-            const T *ac = S + (size_t)(j + it) * R;  // item 0: ||x||^2; item t > 0: x . a_{j+t}
-            const T d = warp_dot<T>(xj, ac, rr_lo, nr, lane);
-            if (lane == 0) mypart[it] = (double)d;
+        for (int it = warp; it < nb; it += nwarps) {
+            const int col = it < ntr ? j + it : it - ntr;
+            const T d = warp_dot<T>(xj, S + (size_t)col * R, rr_lo, nr, lane);
+            if (lane == 0) mypart[it] = d;
         }
         __syncthreads();
         // push this block's partials (and row j, by its owner) to every block of the cluster
         const int owner = j / R;
-        for (int idx = tid; idx < nP * nitem; idx += blockDim.x) {
-            const int q = idx / nitem, it = idx % nitem;
+        for (int idx = tid; idx < nP * nb; idx += blockDim.x) {
+            const int q = idx / nb, it = idx % nb;
             cluster.map_shared_rank(&inbox[buf][p][0], q)[it] = mypart[it];
-            if (p == owner) cluster.map_shared_rank(&rowin[buf][0], q)[it] = (double)S[(size_t)(j + it) * R + (j - r0)];
+            if (p == owner) {
+                const int col = it < ntr ? j + it : it - ntr;
+                cluster.map_shared_rank(&rowin[buf][0], q)[it] = S[(size_t)col * R + (j - r0)];
+            }
         }
         __syncthreads();  // all of this block's pushes precede its arrivals
         if (tid < nP) mbar_arrive_remote(cluster_addr(&mbar[buf], tid));
         // warp 0: wait for every block's partials, sum them in a fixed order, form the
-        // reflector in the panel's precision and the coefficients w_c = tau v . a_c
+        // reflector, the coefficients w_c = tau v . a_c and (block 0) column j of T
         if (warp == 0) {
             if (lane == 0 && !sh_abort) {
                 const uint32_t par = (uint32_t)((j >> 1) & 1);
@@ -375,15 +385,15 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
                 }
             }
             __syncwarp();  // lane 0's acquire orders the warp's reads below
-            const int i0 = lane, i1 = lane + 32;  // nitem <= kNbMax = 64
-            double s0 = 0.0, s1 = 0.0, w0 = 0.0, w1 = 0.0;
+            const int i0 = lane, i1 = lane + 32;  // nb <= kNbMax = 64
+            T s0 = T(0), s1 = T(0), w0 = T(0), w1 = T(0);
             for (int q = 0; q < nP; ++q) {
-                if (i0 < nitem) s0 += inbox[buf][q][i0];
-                if (i1 < nitem) s1 += inbox[buf][q][i1];
+                if (i0 < nb) s0 += inbox[buf][q][i0];
+                if (i1 < nb) s1 += inbox[buf][q][i1];
             }
-            if (i0 < nitem) w0 = rowin[buf][i0];
-            if (i1 < nitem) w1 = rowin[buf][i1];
-            const T alpha = (T)__shfl_sync(0xffffffffu, w0, 0), xn2 = (T)__shfl_sync(0xffffffffu, s0, 0);
+            if (i0 < nb) w0 = rowin[buf][i0];
+            if (i1 < nb) w1 = rowin[buf][i1];
+            const T alpha = __shfl_sync(0xffffffffu, w0, 0), xn2 = __shfl_sync(0xffffffffu, s0, 0);
             T tj = T(0), beta = alpha, scale = T(0);
             if (xn2 > T(0)) {
                 const T r = sqrt(alpha * alpha + xn2);
@@ -392,26 +402,39 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
                 scale = T(1) / (alpha - beta);
             }
             if (lane == 0) {
-                sh_tau = (double)tj;
-                sh_beta = (double)beta;
-                sh_scale = (double)scale;
+                sh_tau = tj;
+                sh_beta = beta;
+                sh_scale = scale;
                 if (p == 0) tau[j] = tj;
             }
-            if (i0 >= 1 && i0 < nitem) wcoef[i0] = tj * ((T)w0 + scale * (T)s0);
-            if (i1 < nitem) wcoef[i1] = tj * ((T)w1 + scale * (T)s1);
+            if (i0 >= 1 && i0 < ntr) wcoef[i0] = tj * (w0 + scale * s0);
+            if (i1 < ntr) wcoef[i1] = tj * (w1 + scale * s1);
+            if (p == 0) {
+                // G(i, j) = v_i . v_j = v_i[j] + x . v_i / (alpha - beta), i < j
+                if (i0 >= ntr && i0 < nb) gcol[i0 - ntr] = w0 + scale * s0;
+                if (i1 >= ntr && i1 < nb) gcol[i1 - ntr] = w1 + scale * s1;
+                __syncwarp();
+                // T(0:j, j) = -tau_j T(0:j, 0:j) G(0:j, j), T(j, j) = tau_j
+                for (int i = lane; i < j; i += 32) {
+                    T t = T(0);
+                    for (int q = i; q < j; ++q) t += Tsh[i + q * nb] * gcol[q];
+                    Tsh[i + j * nb] = -tj * t;
+                }
+                if (lane == 0) Tsh[j + j * nb] = tj;
+                __syncwarp();
+            }
         }
         __syncthreads();
-        const double tj = sh_tau, sc = sh_scale;
-        if (tj != 0.0) {
-            const T scT = (T)sc;
+        const T tj = sh_tau, scT = sh_scale;
+        if (tj != T(0)) {
             for (int rr = rr_lo + tid; rr < nr; rr += blockDim.x) {
-                T v = S[(size_t)j * R + rr] * scT;
+                const T v = S[(size_t)j * R + rr] * scT;
                 for (int c = j + 1; c < nb; ++c) S[(size_t)c * R + rr] -= v * wcoef[c - j];
                 S[(size_t)j * R + rr] = v;
             }
             if (p == owner) {
                 for (int c = j + 1 + tid; c < nb; c += blockDim.x) S[(size_t)c * R + (j - r0)] -= wcoef[c - j];
-                if (tid == 0) S[(size_t)j * R + (j - r0)] = (T)sh_beta;
+                if (tid == 0) S[(size_t)j * R + (j - r0)] = sh_beta;
             }
         }
         __syncthreads();
@@ -427,50 +450,9 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
             P[(long)(r0 + rr) * rs + (long)c * cs] = S[(size_t)c * R + rr];
         }
     }
-    // partial Gram matrix of this block's rows into its own Gs
-    for (int it = warp; it < nb * nb; it += nwarps) {
-        int i = it / nb, k = it % nb;
-        T sacc = T(0);
-        if (i < k && k < kmax) {
-            for (int rr = (k > r0 ? ((k - r0) & ~31) : 0) + lane; rr < nr; rr += 32) {  // rows below k only
-                const int r = r0 + rr;
-                if (r < k) continue;
-                const T vk = (r == k) ? T(1) : S[(size_t)k * R + rr];
-                sacc += S[(size_t)i * R + rr] * vk;
-            }
-            sacc = warp_sum(sacc);
-        }
-        if (lane == 0) Gs[i * nb + k] = (double)sacc;
-    }
-    cluster.sync();
-    if (p == 0) {
-        for (int it = tid; it < nb * nb; it += blockDim.x) {
-            int i = it / nb, k = it % nb;
-            double sum = 0.0;
-            if (i < k && k < kmax)
-                for (int q = 0; q < nP; ++q) sum += cluster.map_shared_rank(Gs, q)[it];
-            Ts[it] = sum;  // the summed Gram matrix (read below as G)
-        }
-    }
-    cluster.sync();  // every remote read is done: blocks may leave after this point
-    if (p != 0) return;
-    // T from G = Ts (summed Gram), built in Gs (no longer read remotely)
-    for (int it = tid; it < nb * nb; it += blockDim.x) Gs[it] = 0.0;
-    __syncthreads();
-    for (int k = 0; k < nb; ++k) {
-        double tk = (k < kmax) ? (double)tau[k] : 0.0;
-        double t = 0.0;
-        if (tid < k)
-            for (int q = tid; q < k; ++q) t += Gs[tid * nb + q] * Ts[q * nb + k];
-        __syncthreads();
-        if (tid < k) Gs[tid * nb + k] = -tk * t;
-        if (tid == k) Gs[k * nb + k] = tk;
-        __syncthreads();
-    }
-    for (int it = tid; it < nb * nb; it += blockDim.x) {
-        int i = it % nb, k = it / nb;
-        Tm[i + (size_t)k * nb] = (T)Gs[i * nb + k];
-    }
+    if (p == 0)
+        for (int idx = tid; idx < nb * nb; idx += blockDim.x) Tm[idx] = Tsh[idx];
+    cluster.sync();  // no block leaves while another may still write to its shared memory
 }
 
 // Cluster size and rows per block for an M x nb panel, or 0 if it does not fit one cluster.
@@ -524,7 +506,7 @@ static int cluster_plan(int M, int nb, int &R, size_t &dyn) {
         if (force > 0 && (1 << k) != force) continue;
         const int C = 1 << k;
         const int r = (M + C - 1) / C;
-        const size_t d = (((size_t)r * nb * sizeof(T) + 15) & ~(size_t)15) + (size_t)2 * nb * nb * sizeof(double);
+        const size_t d = (size_t)r * nb * sizeof(T);
         if (d > max_dyn) continue;
         best = C;
         R = r;

@@ -528,17 +528,22 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
                     float *xp = xptr_rows<RL>(sb, tcols, j, lane);
                     float x[RL];
                     ld_rows<RL>(xp, x);
+                    float d[RL][4];  // four independent partial sums per row: short FMA chains
+#pragma unroll
+                    for (int a = 0; a < RL; ++a) d[a][0] = d[a][1] = d[a][2] = d[a][3] = 0.f;
 #pragma unroll
                     for (int k4 = 0; k4 < NB; k4 += 4) {
                         const float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
 #pragma unroll
                         for (int a = 0; a < RL; ++a) {
-                            x[a] = fmaf(-p[a][k4], q.x, x[a]);
-                            x[a] = fmaf(-p[a][k4 + 1], q.y, x[a]);
-                            x[a] = fmaf(-p[a][k4 + 2], q.z, x[a]);
-                            x[a] = fmaf(-p[a][k4 + 3], q.w, x[a]);
+                            d[a][0] = fmaf(p[a][k4], q.x, d[a][0]);
+                            d[a][1] = fmaf(p[a][k4 + 1], q.y, d[a][1]);
+                            d[a][2] = fmaf(p[a][k4 + 2], q.z, d[a][2]);
+                            d[a][3] = fmaf(p[a][k4 + 3], q.w, d[a][3]);
                         }
                     }
+#pragma unroll
+                    for (int a = 0; a < RL; ++a) x[a] -= (d[a][0] + d[a][1]) + (d[a][2] + d[a][3]);
                     st_rows<RL>(xp, x);
                 }
             } else {
