@@ -265,12 +265,34 @@ struct Win {
     }
 };
 
-// One block step (right + left reflector) of sweep s at position k by one warp.
-// B = the band width when it is a compile-time constant (the inner loops over
-// the reflector are then unrolled and their shared-memory loads issue together),
-// 0 for the generic form.
+// Householder scalars of (alpha, x) with ||x||^2 = xn2: beta, tau = (beta - alpha) / beta
+// and 1 / (alpha - beta).  FP32 uses the fast reciprocal square root and division
+// (a few ulp, far inside the FP32 path's tolerance); FP64 the correctly rounded ones.
+template <typename T>
+NLA_DEV void house_scalars(T alpha, T xn2, T &beta, T &tau, T &scale) {
+    tau = T(0), beta = alpha, scale = T(0);
+    if (xn2 > T(0)) {
+        if constexpr (sizeof(T) == 4) {
+            const float q = alpha * alpha + xn2;
+            const float r = q * rsqrtf(q);
+            beta = alpha >= 0.f ? -r : r;
+            tau = __fdividef(beta - alpha, beta);
+            scale = __fdividef(1.f, alpha - beta);
+        } else {
+            const T r = sqrt(alpha * alpha + xn2);
+            beta = alpha >= T(0) ? -r : r;
+            tau = (beta - alpha) / beta;
+            scale = T(1) / (alpha - beta);
+        }
+    }
+}
+
+// One block step (right + left reflector) of sweep s at position k by one warp;
+// sl0 = window slot of column c0 = s + k b + 1.  B = the band width when it is a
+// compile-time constant (<= 32: the reflector and the lane's row or column are then
+// held in registers, every load issues at once and nothing is reloaded), 0 otherwise.
 template <typename T, int B>
-NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) {
+NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, int sl0, T *v) {
     const int lane = threadIdx.x & 31;
     const int c0 = s + k * b + 1;
     const int tr = (k == 0) ? s : s + (k - 1) * b + 1;
@@ -278,39 +300,48 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) 
     const int cend = min(s + (k + 2) * b, n - 1);
     const int L = c1 - c0 + 1;
     if (L < 2) return;
-    constexpr int UB = B > 0 ? B : 1;
-    const int sl0 = c0 % W.wc;
+    constexpr int UB = (B > 0 && B <= 32) ? B : 1;
     // ---- right reflector on columns c0..c1 from row tr, applied to rows tr+1..c1
-    T part = T(0);
-    for (int c = 1 + lane; c < L; c += 32) {
-        T x = W.col_from(sl0, c0, c)[tr];
-        part += x * x;
-    }
-    T xn2 = warp_sum(part);
-    T alpha = W.col_from(sl0, c0, 0)[tr];
-    T tau = T(0), beta = alpha, scale = T(0);
-    if (xn2 > T(0)) {
-        T r = sqrt(alpha * alpha + xn2);
-        beta = alpha >= T(0) ? -r : r;
-        tau = (beta - alpha) / beta;
-        scale = T(1) / (alpha - beta);
-    }
+    // (lane c < 32 holds entry (tr, c0 + c); L <= 64 for the generic form)
+    T xa = lane < L ? W.col_from(sl0, c0, lane)[tr] : T(0);
+    T xb = lane + 32 < L ? W.col_from(sl0, c0, lane + 32)[tr] : T(0);
+    T xn2 = warp_sum((lane > 0 ? xa * xa : T(0)) + xb * xb);
+    T alpha = __shfl_sync(0xffffffffu, xa, 0);
+    T tau, beta, scale;
+    house_scalars<T>(alpha, xn2, beta, tau, scale);
     if (tau != T(0)) {
-        for (int c = lane; c < L; c += 32) {
-            T *cp = W.col_from(sl0, c0, c);
-            v[c] = c == 0 ? T(1) : cp[tr] * scale;
+        if (lane < L) {
+            v[lane] = lane == 0 ? T(1) : xa * scale;
+            W.col_from(sl0, c0, lane)[tr] = lane == 0 ? beta : T(0);
+        }
+        if (lane + 32 < L) {
+            v[lane + 32] = xb * scale;
+            W.col_from(sl0, c0, lane + 32)[tr] = T(0);
         }
         __syncwarp();
-        for (int c = lane; c < L; c += 32) W.col_from(sl0, c0, c)[tr] = c == 0 ? beta : T(0);
-        for (int i = tr + 1 + lane; i <= c1; i += 32) {  // one lane per row
-            T w = T(0);
-            if (B > 0 && L == B) {
+        if (B > 0 && B <= 32 && L == B) {
+            T vr[UB];
 #pragma unroll
-                for (int c = 0; c < UB; ++c) w += W.col_from(sl0, c0, c)[i] * v[c];
-                w *= tau;
+            for (int c = 0; c < UB; ++c) vr[c] = v[c];
+            for (int i = tr + 1 + lane; i <= c1; i += 32) {  // one lane per row
+                T xr[UB];
 #pragma unroll
-                for (int c = 0; c < UB; ++c) W.col_from(sl0, c0, c)[i] -= w * v[c];
-            } else {
+                for (int c = 0; c < UB; ++c) xr[c] = W.col_from(sl0, c0, c)[i];
+                T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+#pragma unroll
+                for (int c = 0; c < UB; c += 4) {
+                    d0 += xr[c] * vr[c];
+                    if (c + 1 < UB) d1 += xr[c + 1] * vr[c + 1];
+                    if (c + 2 < UB) d2 += xr[c + 2] * vr[c + 2];
+                    if (c + 3 < UB) d3 += xr[c + 3] * vr[c + 3];
+                }
+                const T w = tau * ((d0 + d1) + (d2 + d3));
+#pragma unroll
+                for (int c = 0; c < UB; ++c) W.col_from(sl0, c0, c)[i] = xr[c] - w * vr[c];
+            }
+        } else {
+            for (int i = tr + 1 + lane; i <= c1; i += 32) {  // one lane per row
+                T w = T(0);
                 for (int c = 0; c < L; ++c) w += W.col_from(sl0, c0, c)[i] * v[c];
                 w *= tau;
                 for (int c = 0; c < L; ++c) W.col_from(sl0, c0, c)[i] -= w * v[c];
@@ -319,36 +350,47 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, T *v) 
         __syncwarp();
     }
     // ---- left reflector on rows c0..c1 from column c0, applied to columns c0+1..cend
-    const T *cl = W.col_from(sl0, c0, 0);
-    part = T(0);
-    for (int r = 1 + lane; r < L; r += 32) {
-        T x = cl[c0 + r];
-        part += x * x;
-    }
-    xn2 = warp_sum(part);
-    alpha = cl[c0];
-    tau = T(0), beta = alpha, scale = T(0);
-    if (xn2 > T(0)) {
-        T r = sqrt(alpha * alpha + xn2);
-        beta = alpha >= T(0) ? -r : r;
-        tau = (beta - alpha) / beta;
-        scale = T(1) / (alpha - beta);
-    }
+    T *clw = W.col_from(sl0, c0, 0) + c0;  // clw[r] = entry (c0 + r, c0)
+    xa = lane < L ? clw[lane] : T(0);
+    xb = lane + 32 < L ? clw[lane + 32] : T(0);
+    xn2 = warp_sum((lane > 0 ? xa * xa : T(0)) + xb * xb);
+    alpha = __shfl_sync(0xffffffffu, xa, 0);
+    house_scalars<T>(alpha, xn2, beta, tau, scale);
     if (tau != T(0)) {
-        T *clw = W.col_from(sl0, c0, 0);
-        for (int r = lane; r < L; r += 32) v[r] = r == 0 ? T(1) : clw[c0 + r] * scale;
+        if (lane < L) {
+            v[lane] = lane == 0 ? T(1) : xa * scale;
+            clw[lane] = lane == 0 ? beta : T(0);
+        }
+        if (lane + 32 < L) {
+            v[lane + 32] = xb * scale;
+            clw[lane + 32] = T(0);
+        }
         __syncwarp();
-        for (int r = lane; r < L; r += 32) clw[c0 + r] = r == 0 ? beta : T(0);
-        for (int j = c0 + 1 + lane; j <= cend; j += 32) {  // one lane per column
-            T *cj = W.col_from(sl0, c0, j - c0);
-            T w = T(0);
-            if (B > 0 && L == B) {
+        if (B > 0 && B <= 32 && L == B) {
+            T vr[UB];
 #pragma unroll
-                for (int r = 0; r < UB; ++r) w += v[r] * cj[c0 + r];
-                w *= tau;
+            for (int r = 0; r < UB; ++r) vr[r] = v[r];
+            for (int j = c0 + 1 + lane; j <= cend; j += 32) {  // one lane per column
+                T *cj = W.col_from(sl0, c0, j - c0) + c0;
+                T xr[UB];
 #pragma unroll
-                for (int r = 0; r < UB; ++r) cj[c0 + r] -= w * v[r];
-            } else {
+                for (int r = 0; r < UB; ++r) xr[r] = cj[r];
+                T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+#pragma unroll
+                for (int r = 0; r < UB; r += 4) {
+                    d0 += xr[r] * vr[r];
+                    if (r + 1 < UB) d1 += xr[r + 1] * vr[r + 1];
+                    if (r + 2 < UB) d2 += xr[r + 2] * vr[r + 2];
+                    if (r + 3 < UB) d3 += xr[r + 3] * vr[r + 3];
+                }
+                const T w = tau * ((d0 + d1) + (d2 + d3));
+#pragma unroll
+                for (int r = 0; r < UB; ++r) cj[r] = xr[r] - w * vr[r];
+            }
+        } else {
+            for (int j = c0 + 1 + lane; j <= cend; j += 32) {  // one lane per column
+                T *cj = W.col_from(sl0, c0, j - c0);
+                T w = T(0);
                 for (int r = 0; r < L; ++r) w += v[r] * cj[c0 + r];
                 w *= tau;
                 for (int r = 0; r < L; ++r) cj[c0 + r] -= w * v[r];
@@ -477,6 +519,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
         if (warp < G) {
             // ---------------- chase warps
             T *v = vbase + warp * 64;
+            int wslot = 0;  // window slot of this warp's current c0 (advanced by b per step)
             for (int tau = 0;; ++tau) {
                 int lo, hi;
                 bool active;
@@ -488,7 +531,15 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                 __threadfence_block();
                 if (ok && warp < g) {
                     const int s = s0 + warp, k = tau - 3 * warp;
-                    if (k >= 0 && s + k * b + 1 <= n - 1) warp_chase_step<T, B>(W, n, b, s, k, v);
+                    if (k >= 0 && s + k * b + 1 <= n - 1) {
+                        if (k == 0) {
+                            wslot = (s + 1) % wc;
+                        } else {
+                            wslot += b;
+                            if (wslot >= wc) wslot -= wc;
+                        }
+                        warp_chase_step<T, B>(W, n, b, s, k, wslot, v);
+                    }
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(32 * G) : "memory");
                 if (*vabort) break;
@@ -500,6 +551,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
         } else if (warp == G) {
             // ---------------- flusher
             int flushed = lo0 - 1;
+            unsigned idle = 32;  // backoff while there is nothing to write back
             for (;;) {
                 if (*vabort) break;
                 const int t = *vtau;  // steps < t are complete
@@ -538,13 +590,16 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                         st_release(&done[grp], flushed + 1);
                         *vfl = flushed;  // the loader may reuse these slots now
                     }
+                    idle = 32;
                 } else {
-                    __nanosleep(32);
+                    __nanosleep(idle);
+                    idle = min(idle * 2, 512u);
                 }
             }
         } else {
             // ---------------- loader
             int loaded = lo0 - 1;
+            unsigned idle = 32;  // backoff while nothing new can be loaded
             for (;;) {
                 if (*vabort) break;
                 const int t = *vtau;
@@ -587,7 +642,12 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                         worked = true;
                     }
                 }
-                if (!worked) __nanosleep(32);
+                if (worked) {
+                    idle = 32;
+                } else {
+                    __nanosleep(idle);
+                    idle = min(idle * 2, 512u);
+                }
             }
             __syncwarp();
             __threadfence_block();
