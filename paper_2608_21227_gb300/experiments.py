@@ -1,0 +1,157 @@
+"""Measurement drivers beside the benchmark: mixed-precision accuracy / speed and small-case latency.
+
+    python -m paper_2608_21227_gb300.experiments mixed --out tuned/mixed_gb300.json
+    python -m paper_2608_21227_gb300.experiments latency --out tuned/latency_gb300.json
+
+mixed:   A = U diag(sigma) V^T stored in FP64 with Haar-random U, V and sigma_i =
+         kappa^(-(i-1)/(p-1)), kappa in {1, 1e4, 1e8}, shapes 16384^2 and 32768 x 8192.
+         For the FP64-native, TF32 and BF16 trailing updates: the error max_i |s_i - sigma_i|
+         / sigma_1 against the prescribed sigma (the input is formed in FP64, so its own
+         singular values are within ~1e-14 sigma_1 of sigma), the error against the FP64
+         path, the median relative error over sigma_i >= 1e-3 sigma_1, and the time (CUDA
+         events) with the speedup over FP64-native.
+latency: the 256 x 256 FP64 N(0,1) case (tile 32, band 32, default configuration): one
+         call captured into a CUDA graph, median of 20 replays.
+All work runs on the GPU through libnla.so; inputs are generated on the GPU with seeded
+torch generators (input generation only, not part of the timed library call).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import numpy as np
+
+from . import nla
+
+
+def haar(m, n, gen, device):
+    """m x n with orthonormal columns, Haar distributed (QR of a Gaussian with the sign fix)."""
+    import torch
+
+    G = torch.randn(m, n, generator=gen, device=device, dtype=torch.float64)
+    Q, R = torch.linalg.qr(G)
+    return Q * torch.sign(torch.diagonal(R)).unsqueeze(0)
+
+
+def prescribed(m, n, kappa, seed, device):
+    import torch
+
+    gen = torch.Generator(device=device)
+    gen.manual_seed(seed)
+    p = min(m, n)
+    sigma = torch.tensor(kappa ** (-np.arange(p) / max(p - 1, 1)), dtype=torch.float64, device=device)
+    U = haar(m, p, gen, device)
+    V = haar(n, p, gen, device)
+    A = (U * sigma.unsqueeze(0)) @ V.T  # row-major m x n == column-major A^T (same singular values)
+    del U, V
+    return A.contiguous(), sigma
+
+
+def timed_call(A, update, reps):
+    import torch
+
+    ts, S = [], None
+    for _ in range(reps):
+        B = A.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        S, info = nla.gesvd_vals(B, update=update)
+        e1.record()
+        torch.cuda.synchronize()
+        assert int(info.item()) == 0
+        ts.append(e0.elapsed_time(e1))
+        del B
+    return float(np.median(ts)), S.double().cpu().numpy()
+
+
+def mixed(args):
+    import torch
+
+    dev = torch.device("cuda", 0)
+    out = []
+    for (m, n) in [tuple(map(int, s.split("x"))) for s in args.shapes]:
+        for kappa in args.kappas:
+            seed = 400 + 10 * (m // 1024) + int(round(np.log10(kappa)))
+            A, sigma = prescribed(m, n, kappa, seed, dev)
+            sig = sigma.cpu().numpy()
+            reps = args.reps if kappa == args.kappas[0] else 1
+            t64, s64 = timed_call(A, nla.UPD_NATIVE, reps)
+            rec = {"m": m, "n": n, "kappa": kappa, "seed": seed, "fp64_ms": t64,
+                   "fp64_err_vs_sigma": float(np.max(np.abs(s64 - sig)) / sig[0])}
+            mask = sig >= 1e-3 * sig[0]
+            for name, upd in (("tf32", nla.UPD_TF32), ("bf16", nla.UPD_BF16)):
+                t, s = timed_call(A, upd, reps)
+                rec[name] = {"ms": t, "speedup_vs_fp64": t64 / t,
+                             "err_vs_sigma": float(np.max(np.abs(s - sig)) / sig[0]),
+                             "err_vs_fp64": float(np.max(np.abs(s - s64)) / s64[0]),
+                             "median_rel_err_top": float(np.median(np.abs(s[mask] - sig[mask]) / sig[mask]))}
+            print(json.dumps(rec), flush=True)
+            out.append(rec)
+            del A
+            torch.cuda.empty_cache()
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(out, f, indent=1)
+
+
+def latency(args):
+    import torch
+
+    from . import inputs
+
+    dev = torch.device("cuda", 0)
+    A0 = torch.from_numpy(np.ascontiguousarray(inputs.gaussian(256, 256, 1).T)).to(dev)
+    m, n, _ = nla.col_major_view(A0)
+    cfg = nla.Cfg.make(band=32, tile=64, threads=128, cols_per_block=2, unroll=1)
+    need = nla.gesvd_vals_workspace(m, n, nla.F64, cfg=cfg, preserve_a=True)
+    work = nla.workspace(need, dev)
+    S = torch.empty(n, dtype=torch.float64, device=dev)
+    info = torch.zeros(1, dtype=torch.int32, device=dev)
+    st = torch.cuda.Stream(dev)
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            nla.gesvd_vals(A0, cfg=cfg, preserve_a=True, work=work, S=S, info=info, stream=st)
+        st.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=st):
+            nla.gesvd_vals(A0, cfg=cfg, preserve_a=True, work=work, S=S, info=info, stream=st)
+        ts = []
+        for _ in range(20):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            g.replay()
+            e1.record(st)
+            st.synchronize()
+            ts.append(e0.elapsed_time(e1))
+    assert int(info.item()) == 0
+    flops = 4.0 * 256 ** 3 - 4.0 * 256 ** 3 / 3
+    rec = {"case": "256x256 FP64 N(0,1) seed 1, band 32, default configuration, CUDA graph replay",
+           "median_ms": float(np.median(ts)), "min_ms": float(np.min(ts)),
+           "gflops": flops / (float(np.median(ts)) / 1e3) / 1e9}
+    print(json.dumps(rec), flush=True)
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(rec, f, indent=1)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    sub = ap.add_subparsers(dest="cmd", required=True)
+    m = sub.add_parser("mixed")
+    m.add_argument("--shapes", nargs="+", default=["16384x16384", "32768x8192"])
+    m.add_argument("--kappas", type=float, nargs="+", default=[1.0, 1e4, 1e8])
+    m.add_argument("--reps", type=int, default=2)
+    m.add_argument("--out")
+    la = sub.add_parser("latency")
+    la.add_argument("--out")
+    args = ap.parse_args()
+    t0 = time.time()
+    {"mixed": mixed, "latency": latency}[args.cmd](args)
+    print(json.dumps({"seconds": round(time.time() - t0, 1)}))
+
+
+if __name__ == "__main__":
+    main()
