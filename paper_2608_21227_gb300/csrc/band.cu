@@ -405,32 +405,69 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, int sl
 // not started yet will start at column s+1), hi the last column a running
 // sweep touches now.  active = some sweep of the group is unfinished.
 NLA_DEV void group_need(int n, int b, int s0, int g, int tau, int &lo, int &hi, bool &active) {
+    // c0 of sweep i at step tau - 3i decreases with i, so the last started sweep
+    // (i_ls) holds the lowest column in use and the first unfinished one (i_f) the
+    // highest; sweeps with s >= n - 2 do not run.
     lo = n;
     hi = -1;
     active = false;
-    for (int i = 0; i < g; ++i) {
-        const int s = s0 + i, k = tau - 3 * i;
-        if (s >= n - 2) continue;
-        if (k < 0) {  // not started yet
-            active = true;
-            lo = min(lo, s + 1);
-            continue;
-        }
-        const int c0 = s + k * b + 1;
-        if (c0 > n - 1) continue;  // finished
+    const int gv = min(g, n - 2 - s0);
+    if (gv <= 0) return;
+    const int ils = min(gv - 1, tau / 3);
+    const int num = s0 + tau * b + 2 - n, den = 3 * b - 1;
+    const int ifst = num <= 0 ? 0 : (num + den - 1) / den;
+    if (ifst <= ils) {
         active = true;
-        lo = min(lo, c0);
-        hi = max(hi, min(s + (k + 2) * b, n - 1));
+        lo = s0 + ils + (tau - 3 * ils) * b + 1;
+        hi = min(s0 + ifst + (tau - 3 * ifst + 2) * b, n - 1);
+    }
+    if (ils + 1 < gv) {
+        active = true;
+        lo = min(lo, s0 + ils + 2);
     }
 }
 
 // Mover warp: copy band columns j0..j1 (3b+1 storage rows each) between global
-// memory and the window.  Lanes walk the storage rows of a column; up to eight
-// columns' loads are in flight before their stores (3b+1 <= 2*32 rows per lane
-// pair for b <= 21, more passes otherwise).
-template <typename T, bool LOAD>
+// memory and the window.  With the compact layout (ldab = 3b+1) the columns are
+// one contiguous run in global memory: lanes walk it element by element (coalesced),
+// eight loads per lane in flight before their stores; otherwise column by column.
+template <typename T, bool LOAD, int B>
 NLA_DEV void mover_copy(const Win<T> &W, const Band<T> &A, int n, int b, int j0, int j1, int lane) {
     const int h = 3 * b + 1;
+    if (B > 0 && A.ldab == (long)(3 * B + 1)) {
+        constexpr int H = 3 * B + 1;
+        T *g = A.AB + (long)j0 * H;
+        const int tot = (j1 - j0 + 1) * H;
+        const int sl0 = j0 % W.wc;
+        for (int base = 0; base < tot; base += 32 * 8) {
+            T r[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int e = base + u * 32 + lane;
+                if (e < tot) {
+                    int sl = sl0 + e / H;
+                    sl -= sl >= W.wc ? W.wc : 0;
+                    T *wp = W.w + (size_t)sl * W.ldw + (e % H);
+                    if (LOAD)
+                        r[u] = __ldcg(g + e);
+                    else
+                        __stcg(g + e, *wp);
+                }
+            }
+            if (LOAD) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int e = base + u * 32 + lane;
+                    if (e < tot) {
+                        int sl = sl0 + e / H;
+                        sl -= sl >= W.wc ? W.wc : 0;
+                        W.w[(size_t)sl * W.ldw + (e % H)] = r[u];
+                    }
+                }
+            }
+        }
+        return;
+    }
     for (int q0 = 0; q0 < h; q0 += 64) {
         for (int jb = j0; jb <= j1; jb += 8) {
             T r[8][2];
@@ -525,13 +562,16 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                 bool active;
                 group_need(n, b, s0, g, tau, lo, hi, active);
                 if (!active) break;
+                const int s = s0 + warp, k = tau - 3 * warp;
+                const bool mine = warp < g && k >= 0 && s + k * b + 1 <= n - 1;  // this warp steps now
                 bool ok = true;
-                if (lane == 0) ok = wait_loaded(vhi, hi, vabort, info);
-                ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-                __threadfence_block();
-                if (ok && warp < g) {
-                    const int s = s0 + warp, k = tau - 3 * warp;
-                    if (k >= 0 && s + k * b + 1 <= n - 1) {
+                if (mine) {  // wait for the last column of this warp's own footprint
+                    if (lane == 0) ok = wait_loaded(vhi, min(s + (k + 2) * b, n - 1), vabort, info);
+                    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    __threadfence_block();
+                }
+                if (ok && mine) {
+                    {
                         if (k == 0) {
                             wslot = (s + 1) % wc;
                         } else {
@@ -574,7 +614,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                     __threadfence_block();
                     if (*vabort) break;
                     const int fin = *vhi;
-                    if (fin > flushed) mover_copy<T, false>(W, A, n, b, flushed + 1, fin, lane);
+                    if (fin > flushed) mover_copy<T, false, B>(W, A, n, b, flushed + 1, fin, lane);
                     __threadfence();
                     __syncwarp();
                     if (lane == 0) st_release(&done[grp], INT_MAX);
@@ -582,7 +622,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                 }
                 const int fin = lo - 1;  // columns <= fin are final
                 if (fin > flushed) {
-                    mover_copy<T, false>(W, A, n, b, flushed + 1, fin, lane);
+                    mover_copy<T, false, B>(W, A, n, b, flushed + 1, fin, lane);
                     flushed = fin;
                     __threadfence();
                     __syncwarp();
@@ -634,7 +674,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                         avail = min(want, have - 1);
                     }
                     if (avail > loaded) {
-                        mover_copy<T, true>(W, A, n, b, loaded + 1, avail, lane);
+                        mover_copy<T, true, B>(W, A, n, b, loaded + 1, avail, lane);
                         loaded = avail;
                         __syncwarp();
                         __threadfence_block();
