@@ -735,24 +735,50 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
         const char *v = getenv("NLA_CHASE_GROUP");
         return v ? atoi(v) : 8;
     }();
-    int pf = 0;
-    int G = gset > 0 ? chase_group_size(b, (int)sizeof(T), kGroupBudget, std::min(gset, 30), pf) : 0;
+    auto kern = b == 16 ? band2bd_group_kernel<T, 16>
+                : b == 32 ? band2bd_group_kernel<T, 32>
+                : b == 64 ? band2bd_group_kernel<T, 64> : band2bd_group_kernel<T, 0>;
+    static bool gattr = false;
+    if (!gattr) {
+        for (auto k : {band2bd_group_kernel<T, 0>, band2bd_group_kernel<T, 16>, band2bd_group_kernel<T, 32>,
+                       band2bd_group_kernel<T, 64>})
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGroupBudget);
+        cudaGetLastError();
+        gattr = true;
+    }
+    // the largest G (<= the requested one) whose block -- G chase warps + 2 movers, its
+    // window -- is resident on every SM (registers, shared memory), cached per band width
+    static int gcache[4] = {-1, -1, -1, -1}, pcache[4] = {0, 0, 0, 0};
+    const int ci = b == 16 ? 1 : b == 32 ? 2 : b == 64 ? 3 : 0;
+    int G = 0, pf = 0;
+    if (gset > 0 && ci > 0 && gcache[ci] >= 0) {
+        G = gcache[ci];
+        pf = pcache[ci];
+    } else if (gset > 0) {
+        for (int gmax = std::min(gset, 30); gmax >= 1; --gmax) {
+            int p2 = 0;
+            const int g2 = chase_group_size(b, (int)sizeof(T), kGroupBudget, gmax, p2);
+            if (g2 < 1) break;
+            const int wc2 = (3 * g2 - 1) * b + g2 + 1 + p2 * b;
+            const size_t sm2 = (size_t)wc2 * ((3 * b + 2) & ~1) * sizeof(T) + (size_t)g2 * 64 * sizeof(T);
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * (g2 + 2), sm2) == cudaSuccess && nb >= 1) {
+                G = g2;
+                pf = p2;
+                break;
+            }
+            cudaGetLastError();
+            gmax = std::min(gmax, g2);
+        }
+        if (ci > 0) {
+            gcache[ci] = G;
+            pcache[ci] = pf;
+        }
+    }
     if (nsweeps > 0 && b > 1 && G >= 1) {
         const int ngroups = (nsweeps + G - 1) / G;
         cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)ngroups, st);
         if (err != cudaSuccess) return err;
-        static bool gattr = false;
-        if (!gattr) {
-            cudaFuncSetAttribute(band2bd_group_kernel<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kGroupBudget);
-            cudaFuncSetAttribute(band2bd_group_kernel<T, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kGroupBudget);
-            cudaFuncSetAttribute(band2bd_group_kernel<T, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kGroupBudget);
-            cudaFuncSetAttribute(band2bd_group_kernel<T, 64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kGroupBudget);
-            gattr = true;
-        }
         const int wc = (3 * G - 1) * b + G + 1 + pf * b;
         const size_t smem = (size_t)wc * ((3 * b + 2) & ~1) * sizeof(T) + (size_t)G * 64 * sizeof(T);
         const int grid = std::min(ngroups, device_sm_count());
@@ -766,9 +792,6 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
         attr[0].val.cooperative = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        auto kern = b == 16 ? band2bd_group_kernel<T, 16>
-                    : b == 32 ? band2bd_group_kernel<T, 32>
-                    : b == 64 ? band2bd_group_kernel<T, 64> : band2bd_group_kernel<T, 0>;
         err = cudaLaunchKernelEx(&cfg, kern, AB, ldab, n, b, G, wc, pf, progress, info);
         if (err != cudaSuccess) return err;
     } else if (nsweeps > 0 && b > 1) {
