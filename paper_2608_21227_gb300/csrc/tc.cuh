@@ -33,6 +33,16 @@ NLA_DEV uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
            ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
 }
 
+// UMMA shared-memory descriptor of a K-major operand in the 128-byte-swizzled
+// layout a TMA box with 128-byte rows produces: rows of 128 bytes, 8-row groups
+// 1024 bytes apart (SBO), 16-byte chunks XOR-ed with (row & 7); the group base
+// must be 1024-byte aligned.  Successive K steps advance the start address by
+// their byte offset within the 128-byte row.
+NLA_DEV uint64_t sdesc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | (1ull << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
 // Instruction descriptor: D = FP32, A and B of format `fmt` (kind::tf32: 2;
 // kind::f16 with BF16 operands: 1), both K-major, shape M x N.
 __host__ __device__ constexpr uint32_t idesc(uint32_t fmt, uint32_t M, uint32_t N) {

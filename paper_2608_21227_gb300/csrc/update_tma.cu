@@ -30,6 +30,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -263,6 +264,190 @@ qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         float sum = 0.f;
         if (c < wc)
             for (int q = 0; q < nsplit; ++q) sum += __ldcg(part + ((size_t)q * NB + k) * N + c0 + c);
+        W[idx] = sum;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NB * wc; idx += blockDim.x) {
+        const int k = idx % NB, c = idx / NB;
+        float sum = 0.f;
+        for (int j = 0; j <= k; ++j) sum = fmaf(Tm[j + (size_t)k * NB], W[j * 128 + c], sum);
+        fin[(size_t)(c0 + c) * NB + k] = sum;
+    }
+    if (tid == 0) tickets[blockIdx.x] = 0u;
+}
+
+// ------------------------------------------------------------------ qr_proj on the tensor cores
+// W^T (128 strip columns x NB) = X_strip^T V accumulated in TMEM by tcgen05.mma
+// (kind::tf32, M = 128, N = NB, K = 8 per instruction) over 32-row stages of X.
+// FP32 accuracy from TF32 operands by the three-term split x = hi + lo,
+// hi = x with the low 13 mantissa bits cleared (what the tensor core reads of an
+// FP32 word), lo = x - hi (exact): x . v ~ hi_x hi_v + hi_x lo_v + lo_x hi_v, the
+// dropped lo_x lo_v term and the truncation of lo are below 2^-21 relative.
+// Roles: warp 0 issues the TMA loads of X and V (128-byte-swizzled boxes, which
+// are the canonical K-major operand layout); warps 2..5 write the lo copies and
+// mask V's unit diagonal; warp 1 owns TMEM and one lane issues the MMAs, each
+// stage's commit freeing it for the producer; warps 2..5 read the accumulator
+// back (each warp its TMEM lane quadrant).
+constexpr int kTcWarps = 6;
+
+NLA_DEV float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+template <int NB>
+__global__ void __launch_bounds__(32 * kTcWarps, 1)
+qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int M, int N,
+                  const float *__restrict__ Tm, int S, int Ms, float *part, float *fin, unsigned int *tickets,
+                  int *info) {
+    constexpr uint32_t kCols = NB < 32 ? 32 : NB;  // TMEM columns (power of two >= 32)
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t full[kMaxStages], conv[kMaxStages], empty[kMaxStages], accdone;
+    __shared__ uint32_t tmem_base;
+    __shared__ int sh_last, sh_abort;
+    unsigned char *base = align1k(smem_raw);
+    const int xbytes = 32 * 128 * 4, vbytes = NB * 128;  // one 32-row box of X (128 columns) and of V
+    const int stage = 2 * xbytes + 2 * vbytes;          // hi and lo copies
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int c0 = blockIdx.x * 128, wc = min(128, N - c0);
+    const int sp = blockIdx.y, nsplit = gridDim.y;
+    const int rbeg = sp * Ms, rend = min(M, rbeg + Ms);
+    const int nt = (rend - rbeg + kBoxRows - 1) / kBoxRows;
+    if (tid == 0) {
+        for (int i = 0; i < S; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&conv[i], 4);
+            tc::mbar_init(&empty[i], 1);
+        }
+        tc::mbar_init(&accdone, 1);
+        sh_abort = 0;
+        tma::fence_init();
+        tma::prefetch_map(&tmX);
+        tma::prefetch_map(&tmV);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&tmem_base, kCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tmem_base;
+    auto xhi = [&](int st) { return base + (size_t)st * stage; };
+    auto xlo = [&](int st) { return base + (size_t)st * stage + xbytes; };
+    auto vhi = [&](int st) { return base + (size_t)st * stage + 2 * xbytes; };
+    auto vlo = [&](int st) { return base + (size_t)st * stage + 2 * xbytes + vbytes; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int t = 0; t < nt; ++t) {
+                const int st = t % S;
+                if (t >= S && !tc::mbar_wait(&empty[st], (uint32_t)(((t / S) - 1) & 1), info)) {
+                    sh_abort = 1;
+                    break;
+                }
+                tma::expect_tx(&full[st], (uint32_t)(xbytes + vbytes));
+                const int r0 = rbeg + t * kBoxRows;
+                tma::load_2d(xhi(st), &tmX, r0, c0, &full[st]);
+                tma::load_2d(vhi(st), &tmV, r0, 0, &full[st]);
+                issued = t + 1;
+            }
+            drain_loads(full, issued, S, info);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id = tc::idesc(2, 128, NB);
+            for (int t = 0; t < nt; ++t) {
+                const int st = t % S;
+                if (*(volatile int *)&sh_abort || !tc::mbar_wait(&conv[st], (uint32_t)((t / S) & 1), info)) {
+                    sh_abort = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t ah = tc::smem_u32(xhi(st)), al = tc::smem_u32(xlo(st));
+                const uint32_t bh = tc::smem_u32(vhi(st)), bl = tc::smem_u32(vlo(st));
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {  // 8 TF32 = 32 bytes of K per instruction
+                    const uint32_t off = kk * 32;
+                    tc::mma_tf32(tbase, tc::sdesc_sw128(ah + off), tc::sdesc_sw128(bh + off), id,
+                                 (t > 0 || kk > 0) ? 1u : 0u);
+                    tc::mma_tf32(tbase, tc::sdesc_sw128(ah + off), tc::sdesc_sw128(bl + off), id, 1u);
+                    tc::mma_tf32(tbase, tc::sdesc_sw128(al + off), tc::sdesc_sw128(bh + off), id, 1u);
+                }
+                tc::mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
+            }
+            tc::mma_commit(&accdone);  // every issued MMA has completed
+        }
+        __syncwarp();
+    } else {
+        // ---- warps 2..5: lo copies (and V's unit diagonal), then the epilogue
+        const int ct = tid - 64;  // 0..127
+        for (int t = 0; t < nt; ++t) {
+            const int st = t % S;
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) {
+                sh_abort = 1;
+                break;
+            }
+            const int r0 = rbeg + t * kBoxRows;  // trailing-matrix row of the stage's first row
+            float *vh = reinterpret_cast<float *>(vhi(st));
+            if (r0 < NB) {
+                // V(r, k) with r <= k: 1 on the diagonal, 0 above (entry (r, k) of the box:
+                // row k, 16-byte chunk (r/4) ^ (k & 7), word r % 4)
+                for (int e = ct; e < NB * kBoxRows; e += 128) {
+                    const int k = e / kBoxRows, rr = e % kBoxRows, r = r0 + rr;
+                    if (r <= k) vh[k * 32 + ((((rr >> 2) ^ (k & 7))) << 2) + (rr & 3)] = r == k ? 1.f : 0.f;
+                }
+                asm volatile("bar.sync 2, 128;" ::: "memory");
+            }
+            const float4 *xs = reinterpret_cast<const float4 *>(xhi(st));
+            float4 *xl = reinterpret_cast<float4 *>(xlo(st));
+#pragma unroll 4
+            for (int e = ct; e < xbytes / 16; e += 128) {
+                const float4 v = xs[e];
+                xl[e] = make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+            }
+            const float4 *vs = reinterpret_cast<const float4 *>(vh);
+            float4 *vl = reinterpret_cast<float4 *>(vlo(st));
+            for (int e = ct; e < vbytes / 16; e += 128) {
+                const float4 v = vs[e];
+                vl[e] = make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+            }
+            tc::fence_async_smem();  // the lo copies -> visible to the tensor core
+            __syncwarp();
+            if (lane == 0) tma::arrive(&conv[st]);
+        }
+        // epilogue: W^T rows of this warp's TMEM lane quadrant
+        const bool ok = tc::mbar_wait_warp(&accdone, 0, info);
+        tc::fence_after_sync();
+        const int q = warp & 3;  // TMEM lanes 32q .. 32q + 31
+        const int col = 32 * q + lane;
+        if (ok && !*(volatile int *)&sh_abort) {
+#pragma unroll
+            for (int c = 0; c < NB; c += 16) {
+                float w[16];
+                tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c, w);
+                tc::tmem_wait_ld();
+                if (col < wc) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) part[((size_t)sp * NB + c + k) * N + c0 + col] = w[k];
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tbase, kCols);
+    __threadfence();
+    __syncthreads();
+    if (sh_abort) return;
+    if (tid == 0) sh_last = atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(nsplit - 1);
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    float *W = reinterpret_cast<float *>(base);
+    for (int idx = tid; idx < NB * 128; idx += blockDim.x) {
+        const int k = idx >> 7, c = idx & 127;
+        float sum = 0.f;
+        if (c < wc)
+            for (int qq = 0; qq < nsplit; ++qq) sum += __ldcg(part + ((size_t)qq * NB + k) * N + c0 + c);
         W[idx] = sum;
     }
     __syncthreads();
@@ -631,8 +816,27 @@ cudaError_t left_nb(float *X, long ldx, int M, int N, const float *V, long ldv, 
         !tma_encode_2d(&mX2, X, 4, M, N, ldx * 4, kBoxRows, sh.tc, true) ||
         !tma_encode_2d(&mQ, fin, 4, NB, N, NB * 4, NB, sh.tc, false))
         return cudaErrorInvalidValue;
-    // pass 1 (+ step 2): W' = T^T V^T X
-    {
+    // pass 1 (+ step 2): W' = T^T V^T X -- on the tensor cores (3xTF32) unless disabled
+    static const bool use_tc = [] {
+        const char *v = getenv("NLA_PROJ_TC");
+        return !v || atoi(v) != 0;
+    }();
+    CUtensorMap mVs;
+    if (use_tc && tma_encode_2d(&mVs, V, 4, M, NB, ldv * 4, kBoxRows, NB, true)) {
+        static bool attr = false;
+        set_smem(qr_proj_tc_kernel<NB>, attr);
+        const int stage = 2 * (32 * 128 * 4) + 2 * NB * 128;
+        const int S = std::max(2, std::min({sh.stages, kMaxStages, (200 * 1024) / stage}));
+        const int nstrip = (N + 127) / 128;
+        int nsplit = splits_for(nstrip, (M + kBoxRows - 1) / kBoxRows, sh.waves);
+        const int Ms = ((M + nsplit - 1) / nsplit + kBoxRows - 1) / kBoxRows * kBoxRows;
+        nsplit = (M + Ms - 1) / Ms;
+        const size_t smem = (size_t)S * stage + 1024;
+        qr_proj_tc_kernel<NB><<<dim3(nstrip, nsplit), 32 * kTcWarps, smem, st>>>(mX, mVs, M, N, Tm, S, Ms, part, fin,
+                                                                              sc.tickets, sc.info);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    } else {
         static bool attr = false;
         set_smem(qr_proj_kernel<NB>, attr);
         const int th = sh.br * kBoxRows;
