@@ -826,7 +826,12 @@ cudaError_t left_nb(float *X, long ldx, int M, int N, const float *V, long ldv, 
         static bool attr = false;
         set_smem(qr_proj_tc_kernel<NB>, attr);
         const int stage = 2 * (32 * 128 * 4) + 2 * NB * 128;
-        const int S = std::max(2, std::min({sh.stages, kMaxStages, (200 * 1024) / stage}));
+        static const int sforce = [] {  // NLA_TC_STAGES: pipeline depth of the tensor-core projection
+            const char *v = getenv("NLA_TC_STAGES");
+            return v ? atoi(v) : 0;
+        }();
+        // 3 stages measured best at 8192 (deeper rings cost blocks per SM)
+        const int S = std::max(2, std::min({sforce > 0 ? sforce : 3, kMaxStages, (200 * 1024) / stage}));
         const int nstrip = (N + 127) / 128;
         int nsplit = splits_for(nstrip, (M + kBoxRows - 1) / kBoxRows, sh.waves);
         const int Ms = ((M + nsplit - 1) / nsplit + kBoxRows - 1) / kBoxRows * kBoxRows;
