@@ -66,6 +66,14 @@ size_t tma_cfg_smem(int nb, const UpdCfg &c);
 bool trail_tma_eligible(const float *X, long ldx, const float *V, long ldv, int nb, const UpdScratch &sc);
 cudaError_t trail_tma(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb, const float *Tm,
                       const UpdCfg &c, const UpdScratch &sc, cudaStream_t st);
+// The same in two parts: the projection (step 1 + T, into the scratch) and the
+// update of rows [off, off + len) (side 0) / columns [off, off + len) (side 1) of
+// the M x N block; off a multiple of 4.  Parts of one projection may run in any
+// order and on different streams.
+cudaError_t trail_tma_project(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb,
+                              const float *Tm, const UpdCfg &c, const UpdScratch &sc, cudaStream_t st);
+cudaError_t trail_tma_apply(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb, int off,
+                            int len, const UpdCfg &c, const UpdScratch &sc, cudaStream_t st);
 
 // QR side: X (M x N at X, ldx) <- (I - V T V^T)^T X, V = unit lower M x nb at Vp (ldv).
 template <typename T>

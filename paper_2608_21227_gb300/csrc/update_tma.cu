@@ -617,7 +617,7 @@ lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 template <int NB, int SIDE>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int M, int N,
-                    const float *__restrict__ Pv, long ldp, int tcols, int NC, int S, int Ns, int *info) {
+                    const float *__restrict__ Pv, long ldp, int tcols, int NC, int S, int Ns, int moff, int *info) {
     constexpr int RL = 64 / NB, H = 32 * RL;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], done[kMaxStages];
@@ -694,7 +694,7 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
                 float v = 0.f;
                 if (i < M) {
                     if constexpr (SIDE == 0)
-                        v = unit_lower(i, k, i > k ? __ldg(Pv + i + (long)k * ldp) : 0.f);
+                        v = unit_lower(moff + i, k, moff + i > k ? __ldg(Pv + i + (long)k * ldp) : 0.f);
                     else
                         v = __ldg(Pv + (size_t)k * M + i);
                 }
@@ -707,7 +707,7 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
             unsigned char *sb = base + (size_t)st * stage;
             const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
             const int cb = cbeg + t * tcols;
-            if (SIDE == 0 || cb >= NB) {  // no column of this stage meets V's unit diagonal
+            if (SIDE == 0 || moff + cb >= NB) {  // no column of this stage meets V's unit diagonal
 #pragma unroll 2
                 for (int j = cw; j < tcols; j += NC) {
                     float *xp = xptr_rows<RL>(sb, tcols, j, lane);
@@ -736,7 +736,7 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
                     float *xp = xptr_rows<RL>(sb, tcols, j, lane);
                     float x[RL];
                     ld_rows<RL>(xp, x);
-                    const int c = cb + j;
+                    const int c = moff + cb + j;  // global column: V's unit diagonal
 #pragma unroll
                     for (int k4 = 0; k4 < NB; k4 += 4) {
                         float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
@@ -806,15 +806,13 @@ TmaShape shape_of(int nb, const UpdCfg &c) {
 }
 
 template <int NB>
-cudaError_t left_nb(float *X, long ldx, int M, int N, const float *V, long ldv, const float *Tm, const TmaShape &sh,
-                    const UpdScratch &sc, cudaStream_t st) {
+cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long ldv, const float *Tm,
+                         const TmaShape &sh, const UpdScratch &sc, cudaStream_t st) {
     float *part = reinterpret_cast<float *>(sc.work);
     float *fin = part + (size_t)kMaxSplitTma * 64 * std::max(M, N);
-    CUtensorMap mX, mV, mX2, mQ;
+    CUtensorMap mX, mV;
     if (!tma_encode_2d(&mX, X, 4, M, N, ldx * 4, kBoxRows, 128, true) ||
-        !tma_encode_2d(&mV, V, 4, M, NB, ldv * 4, kBoxRows, NB, false) ||
-        !tma_encode_2d(&mX2, X, 4, M, N, ldx * 4, kBoxRows, sh.tc, true) ||
-        !tma_encode_2d(&mQ, fin, 4, NB, N, NB * 4, NB, sh.tc, false))
+        !tma_encode_2d(&mV, V, 4, M, NB, ldv * 4, kBoxRows, NB, false))
         return cudaErrorInvalidValue;
     // pass 1 (+ step 2): W' = T^T V^T X -- on the tensor cores (3xTF32) unless disabled
     static const bool use_tc = [] {
@@ -856,26 +854,39 @@ cudaError_t left_nb(float *X, long ldx, int M, int N, const float *V, long ldv, 
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    // pass 2: X -= V W'
-    {
-        static bool attr = false;
-        set_smem(strip_update_kernel<NB, 0>, attr);
-        constexpr int H = 32 * (64 / NB);
-        const int stage = stage_bytes_cols(NB, sh.tc);
-        const int nstrip = (M + H - 1) / H;
-        int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (N + sh.tc - 1) / sh.tc));
-        const int Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
-        ncs = (N + Ns - 1) / Ns;
-        const size_t smem = (size_t)sh.stages * stage + 1024;
-        strip_update_kernel<NB, 0><<<dim3(nstrip, ncs), 32 * (sh.nc + 1), smem, st>>>(mX2, mQ, M, N, V, ldv, sh.tc,
-                                                                                    sh.nc, sh.stages, Ns, sc.info);
-    }
+    return cudaGetLastError();
+}
+
+// pass 2 on rows [off, off + len) of the M x N trailing block: X -= V W'
+template <int NB>
+cudaError_t left_apply_nb(float *X, long ldx, int M, int N, const float *V, long ldv, int off, int len,
+                          const TmaShape &sh, const UpdScratch &sc, cudaStream_t st) {
+    if (len <= 0) return cudaSuccess;
+    float *part = reinterpret_cast<float *>(sc.work);
+    const float *fin = part + (size_t)kMaxSplitTma * 64 * std::max(M, N);
+    float *Xo = X + off;
+    const float *Vo = V + off;
+    CUtensorMap mX2, mQ;
+    if (!tma_encode_2d(&mX2, Xo, 4, len, N, ldx * 4, kBoxRows, sh.tc, true) ||
+        !tma_encode_2d(&mQ, fin, 4, NB, N, NB * 4, NB, sh.tc, false))
+        return cudaErrorInvalidValue;
+    static bool attr = false;
+    set_smem(strip_update_kernel<NB, 0>, attr);
+    constexpr int H = 32 * (64 / NB);
+    const int stage = stage_bytes_cols(NB, sh.tc);
+    const int nstrip = (len + H - 1) / H;
+    int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (N + sh.tc - 1) / sh.tc));
+    const int Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
+    ncs = (N + Ns - 1) / Ns;
+    const size_t smem = (size_t)sh.stages * stage + 1024;
+    strip_update_kernel<NB, 0><<<dim3(nstrip, ncs), 32 * (sh.nc + 1), smem, st>>>(mX2, mQ, len, N, Vo, ldv, sh.tc,
+                                                                                sh.nc, sh.stages, Ns, off, sc.info);
     return cudaGetLastError();
 }
 
 template <int NB>
-cudaError_t right_nb(float *X, long ldx, int M, int N, const float *Vt, long ldvt, const float *Tm,
-                     const TmaShape &sh, const UpdScratch &sc, cudaStream_t st) {
+cudaError_t right_proj_nb(float *X, long ldx, int M, int N, const float *Vt, long ldvt, const float *Tm,
+                          const TmaShape &sh, const UpdScratch &sc, cudaStream_t st) {
     float *part = reinterpret_cast<float *>(sc.work);
     float *fin = part + (size_t)kMaxSplitTma * 64 * std::max(M, N);
     CUtensorMap mX, mQ;
@@ -887,27 +898,40 @@ cudaError_t right_nb(float *X, long ldx, int M, int N, const float *Vt, long ldv
     const int nstrip = (M + H - 1) / H;
     const size_t smem = (size_t)sh.stages * stage + 1024;
     // pass 1 (+ step 2): Y' = X V T
-    {
-        static bool attr = false;
-        set_smem(lq_proj_kernel<NB>, attr);
-        int nsplit = splits_for(nstrip, (N + sh.tc - 1) / sh.tc, sh.waves);
-        const int Ns = ((N + nsplit - 1) / nsplit + sh.tc - 1) / sh.tc * sh.tc;
-        nsplit = (N + Ns - 1) / Ns;
-        lq_proj_kernel<NB><<<dim3(nstrip, nsplit), 32 * (sh.nc + 1), smem, st>>>(
-            mX, mQ, M, N, Tm, sh.tc, sh.nc, sh.stages, Ns, part, fin, sc.tickets, sc.info);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    // pass 2: X -= Y' V^T
-    {
-        static bool attr = false;
-        set_smem(strip_update_kernel<NB, 1>, attr);
-        int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (N + sh.tc - 1) / sh.tc));
-        const int Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
-        ncs = (N + Ns - 1) / Ns;
-        strip_update_kernel<NB, 1><<<dim3(nstrip, ncs), 32 * (sh.nc + 1), smem, st>>>(mX, mQ, M, N, fin, 0, sh.tc,
-                                                                                    sh.nc, sh.stages, Ns, sc.info);
-    }
+    static bool attr = false;
+    set_smem(lq_proj_kernel<NB>, attr);
+    int nsplit = splits_for(nstrip, (N + sh.tc - 1) / sh.tc, sh.waves);
+    const int Ns = ((N + nsplit - 1) / nsplit + sh.tc - 1) / sh.tc * sh.tc;
+    nsplit = (N + Ns - 1) / Ns;
+    lq_proj_kernel<NB><<<dim3(nstrip, nsplit), 32 * (sh.nc + 1), smem, st>>>(mX, mQ, M, N, Tm, sh.tc, sh.nc, sh.stages,
+                                                                             Ns, part, fin, sc.tickets, sc.info);
+    return cudaGetLastError();
+}
+
+// pass 2 on columns [off, off + len) of the M x N trailing block: X -= Y' V^T
+template <int NB>
+cudaError_t right_apply_nb(float *X, long ldx, int M, int N, const float *Vt, long ldvt, int off, int len,
+                           const TmaShape &sh, const UpdScratch &sc, cudaStream_t st) {
+    if (len <= 0) return cudaSuccess;
+    float *part = reinterpret_cast<float *>(sc.work);
+    const float *fin = part + (size_t)kMaxSplitTma * 64 * std::max(M, N);
+    float *Xo = X + (long)off * ldx;
+    const float *Vo = Vt + (long)off * ldvt;
+    CUtensorMap mX, mQ;
+    if (!tma_encode_2d(&mX, Xo, 4, M, len, ldx * 4, kBoxRows, sh.tc, true) ||
+        !tma_encode_2d(&mQ, Vo, 4, NB, len, ldvt * 4, NB, sh.tc, false))
+        return cudaErrorInvalidValue;
+    constexpr int H = 32 * (64 / NB);
+    const int stage = stage_bytes_cols(NB, sh.tc);
+    const int nstrip = (M + H - 1) / H;
+    const size_t smem = (size_t)sh.stages * stage + 1024;
+    static bool attr = false;
+    set_smem(strip_update_kernel<NB, 1>, attr);
+    int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (len + sh.tc - 1) / sh.tc));
+    const int Ns = ((len + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
+    ncs = (len + Ns - 1) / Ns;
+    strip_update_kernel<NB, 1><<<dim3(nstrip, ncs), 32 * (sh.nc + 1), smem, st>>>(mX, mQ, M, len, fin, 0, sh.tc, sh.nc,
+                                                                                sh.stages, Ns, off, sc.info);
     return cudaGetLastError();
 }
 
@@ -934,23 +958,49 @@ bool trail_tma_eligible(const float *X, long ldx, const float *V, long ldv, int 
     return ldx % 4 == 0 && ldv % 4 == 0;
 }
 
-cudaError_t trail_tma(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb, const float *Tm,
-                      const UpdCfg &c, const UpdScratch &sc, cudaStream_t st) {
+cudaError_t trail_tma_project(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb,
+                              const float *Tm, const UpdCfg &c, const UpdScratch &sc, cudaStream_t st) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     if (!trail_tma_eligible(X, ldx, V, ldv, nb, sc) || !tma_cfg_valid(nb, c)) return cudaErrorInvalidConfiguration;
     const TmaShape sh = shape_of(nb, c);
     if (side == 0) {
         switch (nb) {
-            case 16: return left_nb<16>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
-            case 32: return left_nb<32>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
-            default: return left_nb<64>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+            case 16: return left_proj_nb<16>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+            case 32: return left_proj_nb<32>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+            default: return left_proj_nb<64>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
         }
     }
     switch (nb) {
-        case 16: return right_nb<16>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
-        case 32: return right_nb<32>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
-        default: return right_nb<64>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+        case 16: return right_proj_nb<16>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+        case 32: return right_proj_nb<32>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
+        default: return right_proj_nb<64>(X, ldx, M, N, V, ldv, Tm, sh, sc, st);
     }
+}
+
+cudaError_t trail_tma_apply(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb, int off,
+                            int len, const UpdCfg &c, const UpdScratch &sc, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || len <= 0) return cudaSuccess;
+    if (!trail_tma_eligible(X, ldx, V, ldv, nb, sc) || !tma_cfg_valid(nb, c) || off % 4) return cudaErrorInvalidConfiguration;
+    const TmaShape sh = shape_of(nb, c);
+    if (side == 0) {
+        switch (nb) {
+            case 16: return left_apply_nb<16>(X, ldx, M, N, V, ldv, off, len, sh, sc, st);
+            case 32: return left_apply_nb<32>(X, ldx, M, N, V, ldv, off, len, sh, sc, st);
+            default: return left_apply_nb<64>(X, ldx, M, N, V, ldv, off, len, sh, sc, st);
+        }
+    }
+    switch (nb) {
+        case 16: return right_apply_nb<16>(X, ldx, M, N, V, ldv, off, len, sh, sc, st);
+        case 32: return right_apply_nb<32>(X, ldx, M, N, V, ldv, off, len, sh, sc, st);
+        default: return right_apply_nb<64>(X, ldx, M, N, V, ldv, off, len, sh, sc, st);
+    }
+}
+
+cudaError_t trail_tma(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb, const float *Tm,
+                      const UpdCfg &c, const UpdScratch &sc, cudaStream_t st) {
+    cudaError_t e = trail_tma_project(side, X, ldx, M, N, V, ldv, nb, Tm, c, sc, st);
+    if (e != cudaSuccess) return e;
+    return trail_tma_apply(side, X, ldx, M, N, V, ldv, nb, 0, side == 0 ? M : N, c, sc, st);
 }
 
 }  // namespace nla
