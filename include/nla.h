@@ -213,6 +213,16 @@ void nla_trace_reset(void);
 nla_status nla_tc_selftest(int prec, int K, int N, const float *dA, const float *dB, float *dD,
                            int *dInfo, nla_stream_t stream);
 
+/* Failure-detection self-test (no counterpart in the paper): one block waits,
+ * with a budget of budget_us microseconds, on something that never happens --
+ * mode 0: a global flag that nothing sets (the inter-block spin every
+ * cooperative kernel of the library uses); mode 1: an mbarrier phase that never
+ * completes (the stage barriers of the TMA / tensor-core kernels).  The wait
+ * gives up, the kernel writes -NLA_ERR_TIMEOUT to *dInfo and returns, and the
+ * context stays usable.  budget_us in [1, 2000000]; returns NLA_ERR_ARG
+ * otherwise.  Asynchronous on `stream`. */
+nla_status nla_wait_selftest(int mode, int budget_us, int *dInfo, nla_stream_t stream);
+
 /* Message for the last non-OK status returned on this thread. */
 const char *nla_last_error(void);
 

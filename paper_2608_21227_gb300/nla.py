@@ -68,6 +68,7 @@ _SIGNATURES = {
     "nla_band2bd": [_i, _i, _i, _vp, _i, _vp, _vp, _vp, _sz, _vp, _popts, _vp],
     "nla_bdsvd_vals_workspace": [_i, _psz],
     "nla_bdsvd_vals": [_i, _vp, _vp, _vp, _i, _vp, _sz, _vp, _vp],
+    "nla_wait_selftest": [_i, _i, _vp, _vp],
 }
 
 
@@ -268,6 +269,16 @@ def band2bd(ABt, band, stream=None):
     _check(lib().nla_band2bd(n, int(band), dt, _vp(ABt.data_ptr()), ldab, _vp(d.data_ptr()), _vp(e.data_ptr()),
                              _vp(work.data_ptr()), work.numel(), _vp(info.data_ptr()), None, _stream_ptr(stream)))
     return d[:n], e[: max(n - 1, 0)], info
+
+
+def wait_selftest(mode, budget_us, stream=None):
+    """Run the failure-detection self-test (a bounded wait on something that never
+    happens); returns the device info word (-NLA_ERR_TIMEOUT when the wait gave up)."""
+    import torch
+
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(lib().nla_wait_selftest(int(mode), int(budget_us), _vp(info.data_ptr()), _stream_ptr(stream)))
+    return info
 
 
 def bdsvd_vals(d, e, dtype=None, stream=None):
