@@ -243,13 +243,17 @@ band2bd_kernel(T *AB, long ldab, int n, int b, int *progress, int *info) {
 // A block runs a group of G consecutive sweeps s0 .. s0+G-1, one warp per
 // sweep, on a window of band columns held in shared memory (columns stored
 // circularly, the same 3b+1 storage rows per column).  At wavefront step tau,
-// warp i performs block step k = tau - 3i of its sweep: the footprints of the
-// G warps are disjoint and each warp trails the previous one by the three
-// steps the dependency needs, so one __syncthreads per tau orders them.
-// Columns that no sweep of the group will touch again are written back to
-// global memory and announced in done[group] ("every column < value is
-// final"); the next group waits (bounded spin) until the columns it loads are
-// final.  The window spans at most (3G-1) b + G + 1 columns.
+// warp i performs block step k = tau - 2i of its sweep in two halves -- every
+// warp's right reflector, a barrier, every warp's left reflector, a barrier.
+// With sweeps two block steps apart, half-steps that share an entry then run
+// in the order of the sequential chase and concurrent ones are disjoint (the
+// one entry that steps (s, k+2) and (s+1, k) share is written by the former's
+// right reflector before the latter's left one); a whole-step schedule would
+// need three steps between sweeps.  Columns that no sweep of the group will
+// touch again are written back to global memory and announced in done[group]
+// ("every column < value is final"); the next group waits (bounded spin) until
+// the columns it loads are final.  The window spans at most (2G-1) b + G + 1
+// columns.
 template <typename T>
 struct Win {
     T *w;
@@ -292,7 +296,7 @@ NLA_DEV void house_scalars(T alpha, T xn2, T &beta, T &tau, T &scale) {
 // compile-time constant (<= 32: the reflector and the lane's row or column are then
 // held in registers, every load issues at once and nothing is reloaded), 0 otherwise.
 template <typename T, int B>
-NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, int sl0, T *v) {
+NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, int sl0, T *v, int part) {
     const int lane = threadIdx.x & 31;
     const int c0 = s + k * b + 1;
     const int tr = (k == 0) ? s : s + (k - 1) * b + 1;
@@ -301,13 +305,14 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, int sl
     const int L = c1 - c0 + 1;
     if (L < 2) return;
     constexpr int UB = (B > 0 && B <= 32) ? B : 1;
+    T xa, xb, xn2, alpha, tau, beta, scale;
+    if (part == 1) goto left;
     // ---- right reflector on columns c0..c1 from row tr, applied to rows tr+1..c1
     // (lane c < 32 holds entry (tr, c0 + c); L <= 64 for the generic form)
-    T xa = lane < L ? W.col_from(sl0, c0, lane)[tr] : T(0);
-    T xb = lane + 32 < L ? W.col_from(sl0, c0, lane + 32)[tr] : T(0);
-    T xn2 = warp_sum((lane > 0 ? xa * xa : T(0)) + xb * xb);
-    T alpha = __shfl_sync(0xffffffffu, xa, 0);
-    T tau, beta, scale;
+    xa = lane < L ? W.col_from(sl0, c0, lane)[tr] : T(0);
+    xb = lane + 32 < L ? W.col_from(sl0, c0, lane + 32)[tr] : T(0);
+    xn2 = warp_sum((lane > 0 ? xa * xa : T(0)) + xb * xb);
+    alpha = __shfl_sync(0xffffffffu, xa, 0);
     house_scalars<T>(alpha, xn2, beta, tau, scale);
     if (tau != T(0)) {
         if (lane < L) {
@@ -349,6 +354,8 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, int sl
         }
         __syncwarp();
     }
+    if (part == 0) return;
+left:
     // ---- left reflector on rows c0..c1 from column c0, applied to columns c0+1..cend
     T *clw = W.col_from(sl0, c0, 0) + c0;  // clw[r] = entry (c0 + r, c0)
     xa = lane < L ? clw[lane] : T(0);
@@ -404,8 +411,10 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, int sl
 // is the first column any unfinished sweep will still touch (a sweep that has
 // not started yet will start at column s+1), hi the last column a running
 // sweep touches now.  active = some sweep of the group is unfinished.
+constexpr int kLag = 2;  // block steps between consecutive sweeps of a group
+
 NLA_DEV void group_need(int n, int b, int s0, int g, int tau, int &lo, int &hi, bool &active) {
-    // c0 of sweep i at step tau - 3i decreases with i, so the last started sweep
+    // c0 of sweep i at step tau - kLag i decreases with i, so the last started sweep
     // (i_ls) holds the lowest column in use and the first unfinished one (i_f) the
     // highest; sweeps with s >= n - 2 do not run.
     lo = n;
@@ -413,13 +422,13 @@ NLA_DEV void group_need(int n, int b, int s0, int g, int tau, int &lo, int &hi, 
     active = false;
     const int gv = min(g, n - 2 - s0);
     if (gv <= 0) return;
-    const int ils = min(gv - 1, tau / 3);
-    const int num = s0 + tau * b + 2 - n, den = 3 * b - 1;
+    const int ils = min(gv - 1, tau / kLag);
+    const int num = s0 + tau * b + 2 - n, den = kLag * b - 1;
     const int ifst = num <= 0 ? 0 : (num + den - 1) / den;
     if (ifst <= ils) {
         active = true;
-        lo = s0 + ils + (tau - 3 * ils) * b + 1;
-        hi = min(s0 + ifst + (tau - 3 * ifst + 2) * b, n - 1);
+        lo = s0 + ils + (tau - kLag * ils) * b + 1;
+        hi = min(s0 + ifst + (tau - kLag * ifst + 2) * b, n - 1);
     }
     if (ils + 1 < gv) {
         active = true;
@@ -521,11 +530,11 @@ NLA_DEV bool wait_loaded(volatile int *sh_hi, int hi, volatile int *sh_abort, in
 
 // Block = G chase warps + a flusher warp (warp G) + a loader warp (warp G+1).
 // The chase warps run the group's sweeps on the window in lockstep (named
-// barrier 1 per wavefront step) and never touch global memory.  The flusher
+// barrier 1 after each half-step) and never touch global memory.  The flusher
 // writes back columns the group will not touch again and announces them in
 // done[group]; the loader brings in, up to `pf` steps ahead, the columns the
 // previous group has released.  The window holds columns [flushed + 1, loaded]
-// in wc >= (3G - 1) b + G + 1 + pf b circular slots.
+// in wc >= (2G - 1) b + G + 1 + pf b circular slots.
 template <typename T, int B>
 __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int wc, int pf, int *done, int *info) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -562,7 +571,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                 bool active;
                 group_need(n, b, s0, g, tau, lo, hi, active);
                 if (!active) break;
-                const int s = s0 + warp, k = tau - 3 * warp;
+                const int s = s0 + warp, k = tau - kLag * warp;
                 const bool mine = warp < g && k >= 0 && s + k * b + 1 <= n - 1;  // this warp steps now
                 bool ok = true;
                 if (mine) {  // wait for the last column of this warp's own footprint
@@ -578,9 +587,13 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                             wslot += b;
                             if (wslot >= wc) wslot -= wc;
                         }
-                        warp_chase_step<T, B>(W, n, b, s, k, wslot, v);
+                        warp_chase_step<T, B>(W, n, b, s, k, wslot, v, 0);  // right reflector
                     }
                 }
+                // the right reflectors of this step all precede every left reflector:
+                // with sweeps two steps apart that is the order the sequential chase needs
+                asm volatile("bar.sync 1, %0;" ::"r"(32 * G) : "memory");
+                if (ok && mine) warp_chase_step<T, B>(W, n, b, s, k, wslot, v, 1);  // left reflector
                 asm volatile("bar.sync 1, %0;" ::"r"(32 * G) : "memory");
                 if (*vabort) break;
                 if (warp == 0 && lane == 0) {
@@ -703,7 +716,7 @@ static int chase_group_size(int b, int elem, size_t budget, int gmax, int &pf) {
     const size_t ldw = (size_t)((3 * b + 2) & ~1);
     for (int G = gmax; G >= 1; --G)
         for (int p : {4, 2, 1}) {
-            const size_t wc = (size_t)(3 * G - 1) * b + G + 1 + (size_t)p * b;
+            const size_t wc = (size_t)(kLag * G - 1) * b + G + 1 + (size_t)p * b;
             if (wc * ldw * elem + (size_t)G * 64 * elem <= budget) {
                 pf = p;
                 return G;
@@ -759,7 +772,7 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
             int p2 = 0;
             const int g2 = chase_group_size(b, (int)sizeof(T), kGroupBudget, gmax, p2);
             if (g2 < 1) break;
-            const int wc2 = (3 * g2 - 1) * b + g2 + 1 + p2 * b;
+            const int wc2 = (kLag * g2 - 1) * b + g2 + 1 + p2 * b;
             const size_t sm2 = (size_t)wc2 * ((3 * b + 2) & ~1) * sizeof(T) + (size_t)g2 * 64 * sizeof(T);
             int nb = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, 32 * (g2 + 2), sm2) == cudaSuccess && nb >= 1) {
@@ -779,7 +792,7 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
         const int ngroups = (nsweeps + G - 1) / G;
         cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)ngroups, st);
         if (err != cudaSuccess) return err;
-        const int wc = (3 * G - 1) * b + G + 1 + pf * b;
+        const int wc = (kLag * G - 1) * b + G + 1 + pf * b;
         const size_t smem = (size_t)wc * ((3 * b + 2) & ~1) * sizeof(T) + (size_t)G * 64 * sizeof(T);
         const int grid = std::min(ngroups, device_sm_count());
         cudaLaunchConfig_t cfg = {};
