@@ -741,12 +741,12 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
     int *progress = reinterpret_cast<int *>(scratch);
     const int nsweeps = n - 2;
     const size_t kGroupBudget = 200 * 1024;
-    // 8 sweeps per block measured fastest at n = 2048 and 8192, band 16 (more warps
-    // crowd the mover warps' issue slots; fewer lengthen the inter-group handoffs).
-    // NLA_CHASE_GROUP overrides it (0: one sweep per block on the global band).
+    // Up to 16 sweeps per block (the occupancy check below lowers it to what one SM
+    // holds); measured fastest at n = 2048 and 8192, band 16.  NLA_CHASE_GROUP
+    // overrides it (0: one sweep per block on the global band).
     static const int gset = [] {
         const char *v = getenv("NLA_CHASE_GROUP");
-        return v ? atoi(v) : 8;
+        return v ? atoi(v) : 16;
     }();
     auto kern = b == 16 ? band2bd_group_kernel<T, 16>
                 : b == 32 ? band2bd_group_kernel<T, 32>

@@ -314,8 +314,9 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
     __shared__ T rowin[2][kNbMax];
     __shared__ T mypart[kNbMax];
     __shared__ T wcoef[kNbMax];
-    __shared__ T gcol[kNbMax];
-    __shared__ T Tsh[kNbMax * kNbMax];  // T(i, k) at Tsh[i + k*nb] (block 0)
+    // block 0: T(i, k), i <= k, at Tsh[i + k*nb] and G(i, k) = v_i . v_k, i < k, transposed
+    // into the strictly lower part, at Tsh[k + i*nb]
+    __shared__ T Tsh[kNbMax * kNbMax];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ T sh_tau, sh_beta, sh_scale;
     __shared__ int sh_abort;
@@ -396,10 +397,18 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
             const T alpha = __shfl_sync(0xffffffffu, w0, 0), xn2 = __shfl_sync(0xffffffffu, s0, 0);
             T tj = T(0), beta = alpha, scale = T(0);
             if (xn2 > T(0)) {
-                const T r = sqrt(alpha * alpha + xn2);
-                beta = alpha >= T(0) ? -r : r;
-                tj = (beta - alpha) / beta;
-                scale = T(1) / (alpha - beta);
+                if constexpr (sizeof(T) == 4) {  // a few ulp, far inside the FP32 path's tolerance
+                    const float q = alpha * alpha + xn2;
+                    const float r = q * rsqrtf(q);
+                    beta = alpha >= 0.f ? -r : r;
+                    tj = __fdividef(beta - alpha, beta);
+                    scale = __fdividef(1.f, alpha - beta);
+                } else {
+                    const T r = sqrt(alpha * alpha + xn2);
+                    beta = alpha >= T(0) ? -r : r;
+                    tj = (beta - alpha) / beta;
+                    scale = T(1) / (alpha - beta);
+                }
             }
             if (lane == 0) {
                 sh_tau = tj;
@@ -409,29 +418,27 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
             }
             if (i0 >= 1 && i0 < ntr) wcoef[i0] = tj * (w0 + scale * s0);
             if (i1 < ntr) wcoef[i1] = tj * (w1 + scale * s1);
-            if (p == 0) {
-                // G(i, j) = v_i . v_j = v_i[j] + x . v_i / (alpha - beta), i < j
-                if (i0 >= ntr && i0 < nb) gcol[i0 - ntr] = w0 + scale * s0;
-                if (i1 >= ntr && i1 < nb) gcol[i1 - ntr] = w1 + scale * s1;
-                __syncwarp();
-                // T(0:j, j) = -tau_j T(0:j, 0:j) G(0:j, j), T(j, j) = tau_j
-                for (int i = lane; i < j; i += 32) {
-                    T t = T(0);
-                    for (int q = i; q < j; ++q) t += Tsh[i + q * nb] * gcol[q];
-                    Tsh[i + j * nb] = -tj * t;
-                }
-                if (lane == 0) Tsh[j + j * nb] = tj;
-                __syncwarp();
+            if (p == 0) {  // G(i, j) = v_i . v_j = v_i[j] + x . v_i / (alpha - beta), i < j; T after the loop
+                if (i0 >= ntr && i0 < nb) Tsh[j + (i0 - ntr) * nb] = w0 + scale * s0;
+                if (i1 >= ntr && i1 < nb) Tsh[j + (i1 - ntr) * nb] = w1 + scale * s1;
             }
         }
         __syncthreads();
         const T tj = sh_tau, scT = sh_scale;
         if (tj != T(0)) {
-            for (int rr = rr_lo + tid; rr < nr; rr += blockDim.x) {
-                const T v = S[(size_t)j * R + rr] * scT;
-                for (int c = j + 1; c < nb; ++c) S[(size_t)c * R + rr] -= v * wcoef[c - j];
-                S[(size_t)j * R + rr] = v;
+            // columns in blocks of 16: the coefficients in registers, then independent updates
+            for (int cb = j + 1; cb < nb; cb += 16) {
+                T wr[16];
+#pragma unroll
+                for (int u = 0; u < 16; ++u) wr[u] = cb + u < nb ? wcoef[cb + u - j] : T(0);
+                for (int rr = rr_lo + tid; rr < nr; rr += blockDim.x) {
+                    const T v = S[(size_t)j * R + rr] * scT;
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+                        if (cb + u < nb) S[(size_t)(cb + u) * R + rr] -= v * wr[u];
+                }
             }
+            for (int rr = rr_lo + tid; rr < nr; rr += blockDim.x) S[(size_t)j * R + rr] *= scT;
             if (p == owner) {
                 for (int c = j + 1 + tid; c < nb; c += blockDim.x) S[(size_t)c * R + (j - r0)] -= wcoef[c - j];
                 if (tid == 0) S[(size_t)j * R + (j - r0)] = sh_beta;
@@ -450,8 +457,23 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
             P[(long)(r0 + rr) * rs + (long)c * cs] = S[(size_t)c * R + rr];
         }
     }
-    if (p == 0)
-        for (int idx = tid; idx < nb * nb; idx += blockDim.x) Tm[idx] = Tsh[idx];
+    if (p == 0) {
+        // T(0:k, k) = -tau_k T(0:k, 0:k) G(0:k, k), T(k, k) = tau_k -- one warp, column by column
+        if (warp == 0) {
+            for (int kk = 0; kk < kmax; ++kk) {
+                const T tk = tau[kk];
+                for (int i = lane; i < kk; i += 32) {
+                    T t = T(0);
+                    for (int q = i; q < kk; ++q) t += Tsh[i + q * nb] * Tsh[kk + q * nb];  // T(i, q) G(q, kk)
+                    Tsh[i + kk * nb] = -tk * t;
+                }
+                if (lane == 0) Tsh[kk + kk * nb] = tk;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < nb * nb; idx += blockDim.x) Tm[idx] = (idx % nb) <= (idx / nb) ? Tsh[idx] : T(0);
+    }
     cluster.sync();  // no block leaves while another may still write to its shared memory
 }
 
