@@ -436,13 +436,48 @@ NLA_DEV void group_need(int n, int b, int s0, int g, int tau, int &lo, int &hi, 
     }
 }
 
+// One element global -> shared without a register round trip (LDGSTS): every copy a
+// lane issues is in flight at once; cp_async_wait_all() completes the lane's copies.
+template <typename T>
+NLA_DEV void cp_async_elem(T *dst_smem, const T *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst_smem)),
+                 "l"(src), "n"((int)sizeof(T))
+                 : "memory");
+}
+NLA_DEV void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Mover warp: copy band columns j0..j1 (3b+1 storage rows each) between global
 // memory and the window.  With the compact layout (ldab = 3b+1) the columns are
-// one contiguous run in global memory: lanes walk it element by element (coalesced),
-// eight loads per lane in flight before their stores; otherwise column by column.
+// one contiguous run in global memory: lanes walk it element by element (coalesced);
+// otherwise column by column.  Loads are asynchronous copies that all issue before
+// the one wait (a single memory latency per call); write-backs keep eight loads from
+// the window in flight before their stores.
 template <typename T, bool LOAD, int B>
 NLA_DEV void mover_copy(const Win<T> &W, const Band<T> &A, int n, int b, int j0, int j1, int lane) {
     const int h = 3 * b + 1;
+    if (LOAD) {
+        if (B > 0 && A.ldab == (long)(3 * B + 1)) {
+            constexpr int H = 3 * B + 1;
+            const T *g = A.AB + (long)j0 * H;
+            const int tot = (j1 - j0 + 1) * H;
+            const int sl0 = j0 % W.wc;
+            for (int e = lane; e < tot; e += 32) {
+                int sl = sl0 + e / H;
+                sl -= sl >= W.wc ? W.wc : 0;
+                cp_async_elem(W.w + (size_t)sl * W.ldw + (e % H), g + e);
+            }
+        } else {
+            for (int j = j0; j <= j1; ++j) {
+                T *cw = W.col(j);
+                for (int q = lane; q < h; q += 32) {
+                    const int i = j + q - 2 * b;
+                    if (i >= 0 && i < n) cp_async_elem(cw + i, A.at(i, j));
+                }
+            }
+        }
+        cp_async_wait_all();
+        return;
+    }
     if (B > 0 && A.ldab == (long)(3 * B + 1)) {
         constexpr int H = 3 * B + 1;
         T *g = A.AB + (long)j0 * H;
@@ -456,58 +491,22 @@ NLA_DEV void mover_copy(const Win<T> &W, const Band<T> &A, int n, int b, int j0,
                 if (e < tot) {
                     int sl = sl0 + e / H;
                     sl -= sl >= W.wc ? W.wc : 0;
-                    T *wp = W.w + (size_t)sl * W.ldw + (e % H);
-                    if (LOAD)
-                        r[u] = __ldcg(g + e);
-                    else
-                        __stcg(g + e, *wp);
+                    r[u] = W.w[(size_t)sl * W.ldw + (e % H)];
                 }
             }
-            if (LOAD) {
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int e = base + u * 32 + lane;
-                    if (e < tot) {
-                        int sl = sl0 + e / H;
-                        sl -= sl >= W.wc ? W.wc : 0;
-                        W.w[(size_t)sl * W.ldw + (e % H)] = r[u];
-                    }
-                }
+            for (int u = 0; u < 8; ++u) {
+                const int e = base + u * 32 + lane;
+                if (e < tot) __stcg(g + e, r[u]);
             }
         }
         return;
     }
-    for (int q0 = 0; q0 < h; q0 += 64) {
-        for (int jb = j0; jb <= j1; jb += 8) {
-            T r[8][2];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = jb + u;
-                if (j > j1) break;
-                const T *cw = W.col(j);
-#pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    const int q = q0 + lane + 32 * h2, i = j + q - 2 * b;
-                    const bool in = q < h && i >= 0 && i < n;
-                    if (LOAD)
-                        r[u][h2] = in ? __ldcg(A.at(i, j)) : T(0);
-                    else if (in)
-                        __stcg(A.at(i, j), cw[i]);
-                }
-            }
-            if (LOAD) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int j = jb + u;
-                    if (j > j1) break;
-                    T *cw = W.col(j);
-#pragma unroll
-                    for (int h2 = 0; h2 < 2; ++h2) {
-                        const int q = q0 + lane + 32 * h2, i = j + q - 2 * b;
-                        if (q < h && i >= 0 && i < n) cw[i] = r[u][h2];
-                    }
-                }
-            }
+    for (int j = j0; j <= j1; ++j) {
+        const T *cw = W.col(j);
+        for (int q = lane; q < h; q += 32) {
+            const int i = j + q - 2 * b;
+            if (i >= 0 && i < n) __stcg(A.at(i, j), cw[i]);
         }
     }
 }
@@ -652,6 +651,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
         } else {
             // ---------------- loader
             int loaded = lo0 - 1;
+            int have = grp > 0 ? 0 : INT_MAX;  // columns < have are final in the previous group
             unsigned idle = 32;  // backoff while nothing new can be loaded
             for (;;) {
                 if (*vabort) break;
@@ -670,22 +670,18 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                 __threadfence_block();
                 bool worked = false;
                 if (want > loaded) {
-                    int avail = want;
-                    if (grp > 0) {
-                        int have = 0;
-                        if (lane == 0) {
-                            have = ld_acquire(&done[grp - 1]);
+                    if (have - 1 < want) {  // (never for group 0)
+                        if (hi > loaded && have < hi + 1) {
                             // the current step cannot start without its columns: wait for those
-                            if (have < hi + 1 && hi > loaded) {
-                                if (!spin_until_geq(&done[grp - 1], hi + 1, info, 64)) *vabort = 1;
-                                have = ld_acquire(&done[grp - 1]);
-                            }
+                            if (lane == 0 && !spin_until_geq(&done[grp - 1], hi + 1, info, 64)) *vabort = 1;
+                            __syncwarp();
+                            if (*vabort) break;
                         }
-                        have = __shfl_sync(0xffffffffu, have, 0);
-                        __syncwarp();  // lane 0's acquire orders the whole warp's loads below
-                        if (*vabort) break;
-                        avail = min(want, have - 1);
+                        // every lane acquires, so that its own copies below see what the previous
+                        // group wrote; the smallest value seen is final for all of them
+                        have = __reduce_min_sync(0xffffffffu, ld_acquire(&done[grp - 1]));
                     }
+                    const int avail = min(want, have - 1);
                     if (avail > loaded) {
                         mover_copy<T, true, B>(W, A, n, b, loaded + 1, avail, lane);
                         loaded = avail;

@@ -19,7 +19,9 @@
 //
 // Householder convention (LAPACK-style): beta = -sign(alpha) ||[alpha; x]||,
 // sign(0) = +1, tau = (beta - alpha) / beta; a zero x gives tau = 0, H = I.
-// Norms and the cross-block sums are FP64 in every precision mode.
+// This grid variant takes norms and cross-block sums in FP64 in every precision
+// mode; the cluster variant below takes them in the panel's own precision (FP64 for
+// the FP64 and mixed-precision paths, FP32 for the plain FP32 path).
 #include <cooperative_groups.h>
 
 #include <algorithm>

@@ -12,6 +12,10 @@ mixed:   A = U diag(sigma) V^T stored in FP64 with Haar-random U, V and sigma_i 
          events) with the speedup over FP64-native.
 latency: the 256 x 256 FP64 N(0,1) case (tile 32, band 32, default configuration): one
          call captured into a CUDA graph, median of 20 replays.
+case:    one workload run `--reps` times, for profilers that capture single launches:
+         a dense SVD (--n, --dtype, --update; U[-1,1] entries, seed 7), a batch of the
+         batched workload's shapes (--batched COUNT), or cost-model forward/backward and
+         Adam steps (--mlp ROWS).
 All work runs on the GPU through libnla.so; inputs are generated on the GPU with seeded
 torch generators (input generation only, not part of the timed library call).
 """
@@ -137,6 +141,50 @@ def latency(args):
             json.dump(rec, f, indent=1)
 
 
+def case(args):
+    import torch
+
+    from . import inputs, kt
+
+    dev = torch.device("cuda", 0)
+    if args.batched:
+        ms, ns = inputs.batch_shapes(args.batched, seed=3)
+        mats = [torch.from_numpy(np.ascontiguousarray(inputs.gaussian(int(ms[i]), int(ns[i]), [3, i],
+                                                                      dtype=np.float32).T)).to(dev)
+                for i in range(args.batched)]
+        bt = nla.Batch(mats)
+        for _ in range(args.reps):
+            _, info = nla.gesvd_vals_batched(bt)
+        torch.cuda.synchronize()
+        assert int(info.abs().max().item()) == 0
+        print(json.dumps({"case": "batched", "count": args.batched}))
+        return
+    if args.mlp:
+        g = torch.Generator(device=dev)
+        g.manual_seed(5)
+        npar = kt.mlp_param_count()
+        params = torch.randn(npar, generator=g, device=dev) * 0.05
+        X = torch.randn(args.mlp, kt.FEATURES, generator=g, device=dev)
+        y = torch.randn(args.mlp, generator=g, device=dev)
+        mom, var = torch.zeros_like(params), torch.zeros_like(params)
+        for t in range(1, args.reps + 1):
+            _, grads = kt.mlp_forward_backward(params, X, y)
+            kt.mlp_adam_step(params, grads, mom, var, t, 1e-3)
+        torch.cuda.synchronize()
+        print(json.dumps({"case": "mlp", "rows": args.mlp}))
+        return
+    tdt = torch.float32 if args.dtype == "f32" else torch.float64
+    A0 = inputs.uniform_device(args.n, args.n, 7, dtype=tdt, device=dev)
+    upd = {"native": nla.UPD_NATIVE, "tf32": nla.UPD_TF32, "bf16": nla.UPD_BF16}[args.update]
+    for _ in range(args.reps):
+        A = A0.clone()
+        S, info = nla.gesvd_vals(A, update=upd)
+        torch.cuda.synchronize()
+        assert int(info.item()) == 0
+    print(json.dumps({"case": "gesvd", "n": args.n, "dtype": args.dtype, "update": args.update,
+                      "sigma_max": float(S[0].item())}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -147,9 +195,16 @@ def main():
     m.add_argument("--out")
     la = sub.add_parser("latency")
     la.add_argument("--out")
+    c = sub.add_parser("case")
+    c.add_argument("--n", type=int, default=2048)
+    c.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    c.add_argument("--update", choices=["native", "tf32", "bf16"], default="native")
+    c.add_argument("--batched", type=int, default=0)
+    c.add_argument("--mlp", type=int, default=0)
+    c.add_argument("--reps", type=int, default=2)
     args = ap.parse_args()
     t0 = time.time()
-    {"mixed": mixed, "latency": latency}[args.cmd](args)
+    {"mixed": mixed, "latency": latency, "case": case}[args.cmd](args)
     print(json.dumps({"seconds": round(time.time() - t0, 1)}))
 
 
