@@ -328,10 +328,8 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, int sl
             T vr[UB];
 #pragma unroll
             for (int c = 0; c < UB; ++c) vr[c] = v[c];
-            for (int i = tr + 1 + lane; i <= c1; i += 32) {  // one lane per row
-                T xr[UB];
-#pragma unroll
-                for (int c = 0; c < UB; ++c) xr[c] = W.col_from(sl0, c0, c)[i];
+            // apply to the lane's row held in xr (columns c0 .. c0 + B - 1)
+            auto apply_row = [&](T(&xr)[UB]) {
                 T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
 #pragma unroll
                 for (int c = 0; c < UB; c += 4) {
@@ -342,7 +340,31 @@ NLA_DEV void warp_chase_step(const Win<T> &W, int n, int b, int s, int k, int sl
                 }
                 const T w = tau * ((d0 + d1) + (d2 + d3));
 #pragma unroll
-                for (int c = 0; c < UB; ++c) W.col_from(sl0, c0, c)[i] = xr[c] - w * vr[c];
+                for (int c = 0; c < UB; ++c) xr[c] -= w * vr[c];
+            };
+            if (sl0 + B <= W.wc) {
+                // the B columns sit in consecutive slots: entry (i, c0 + c) is
+                // base[i + c (ldw - 1)], constant offsets from one address per lane
+                constexpr int LDW1 = ((3 * UB + 2) & ~1) - 1;
+                T *base = W.w + (size_t)sl0 * W.ldw + W.b2 - c0;
+                for (int i = tr + 1 + lane; i <= c1; i += 32) {  // one lane per row
+                    T *rp = base + i;
+                    T xr[UB];
+#pragma unroll
+                    for (int c = 0; c < UB; ++c) xr[c] = rp[c * LDW1];
+                    apply_row(xr);
+#pragma unroll
+                    for (int c = 0; c < UB; ++c) rp[c * LDW1] = xr[c];
+                }
+            } else {
+                for (int i = tr + 1 + lane; i <= c1; i += 32) {
+                    T xr[UB];
+#pragma unroll
+                    for (int c = 0; c < UB; ++c) xr[c] = W.col_from(sl0, c0, c)[i];
+                    apply_row(xr);
+#pragma unroll
+                    for (int c = 0; c < UB; ++c) W.col_from(sl0, c0, c)[i] = xr[c];
+                }
             }
         } else {
             for (int i = tr + 1 + lane; i <= c1; i += 32) {  // one lane per row

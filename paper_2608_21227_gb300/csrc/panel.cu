@@ -283,6 +283,14 @@ NLA_DEV bool mbar_try_wait_cluster(uint64_t *mbar, uint32_t parity) {
     return ok != 0;
 }
 
+// One element global -> shared as an asynchronous copy (completed by cp.async.wait_all).
+template <typename T>
+NLA_DEV void cp_async_4or8(T *dst_smem, const T *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(tc::smem_u32(dst_smem)), "l"(src),
+                 "n"((int)sizeof(T))
+                 : "memory");
+}
+
 // Dot product of two columns over rows [lo, hi) of the block, four independent
 // partial sums per lane, then a warp reduction.
 template <typename T>
@@ -316,6 +324,7 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
     __shared__ T rowin[2][kNbMax];
     __shared__ T mypart[kNbMax];
     __shared__ T wcoef[kNbMax];
+    __shared__ T taus[kNbMax];  // block 0: tau_j, for T after the column loop
     // block 0: T(i, k), i <= k, at Tsh[i + k*nb] and G(i, k) = v_i . v_k, i < k, transposed
     // into the strictly lower part, at Tsh[k + i*nb]
     __shared__ T Tsh[kNbMax * kNbMax];
@@ -336,17 +345,19 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
         for (int j = kmax + tid; j < nb; j += blockDim.x) tau[j] = T(0);
         for (int i = tid; i < nb * nb; i += blockDim.x) Tsh[i] = T(0);
     }
+    // the block's rows into shared memory: every copy in flight at once (one memory latency)
     if (cs == 1) {
         for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
             int c = idx % nb, rr = idx / nb;
-            S[(size_t)c * R + rr] = P[(long)(r0 + rr) * rs + c];
+            cp_async_4or8(&S[(size_t)c * R + rr], &P[(long)(r0 + rr) * rs + c]);
         }
     } else {
         for (int idx = tid; idx < nr * nb; idx += blockDim.x) {
             int rr = idx % nr, c = idx / nr;
-            S[(size_t)c * R + rr] = P[(long)(r0 + rr) * rs + (long)c * cs];
+            cp_async_4or8(&S[(size_t)c * R + rr], &P[(long)(r0 + rr) * rs + (long)c * cs]);
         }
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     cluster.sync();  // every block's barriers are initialised before the first remote arrive
     for (int j = 0; j < kmax; ++j) {
         const int buf = j & 1;
@@ -416,7 +427,10 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
                 sh_tau = tj;
                 sh_beta = beta;
                 sh_scale = scale;
-                if (p == 0) tau[j] = tj;
+                if (p == 0) {
+                    tau[j] = tj;
+                    taus[j] = tj;
+                }
             }
             if (i0 >= 1 && i0 < ntr) wcoef[i0] = tj * (w0 + scale * s0);
             if (i1 < ntr) wcoef[i1] = tj * (w1 + scale * s1);
@@ -429,15 +443,22 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
         const T tj = sh_tau, scT = sh_scale;
         if (tj != T(0)) {
             // columns in blocks of 16: the coefficients in registers, then independent updates
+            // (all 16 entries of a row are loaded before any is stored back: the loads then
+            // issue together instead of waiting on possibly aliasing stores)
             for (int cb = j + 1; cb < nb; cb += 16) {
+                const int nc = min(16, nb - cb);
                 T wr[16];
 #pragma unroll
-                for (int u = 0; u < 16; ++u) wr[u] = cb + u < nb ? wcoef[cb + u - j] : T(0);
+                for (int u = 0; u < 16; ++u) wr[u] = u < nc ? wcoef[cb + u - j] : T(0);
                 for (int rr = rr_lo + tid; rr < nr; rr += blockDim.x) {
+                    T *row = S + (size_t)cb * R + rr;
                     const T v = S[(size_t)j * R + rr] * scT;
+                    T xr[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) xr[u] = u < nc ? row[(size_t)u * R] : T(0);
 #pragma unroll
                     for (int u = 0; u < 16; ++u)
-                        if (cb + u < nb) S[(size_t)(cb + u) * R + rr] -= v * wr[u];
+                        if (u < nc) row[(size_t)u * R] = xr[u] - v * wr[u];
                 }
             }
             for (int rr = rr_lo + tid; rr < nr; rr += blockDim.x) S[(size_t)j * R + rr] *= scT;
@@ -463,7 +484,7 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
         // T(0:k, k) = -tau_k T(0:k, 0:k) G(0:k, k), T(k, k) = tau_k -- one warp, column by column
         if (warp == 0) {
             for (int kk = 0; kk < kmax; ++kk) {
-                const T tk = tau[kk];
+                const T tk = taus[kk];
                 for (int i = lane; i < kk; i += 32) {
                     T t = T(0);
                     for (int q = i; q < kk; ++q) t += Tsh[i + q * nb] * Tsh[kk + q * nb];  // T(i, q) G(q, kk)
