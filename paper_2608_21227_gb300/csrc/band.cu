@@ -759,12 +759,13 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
     int *progress = reinterpret_cast<int *>(scratch);
     const int nsweeps = n - 2;
     const size_t kGroupBudget = 200 * 1024;
-    // Up to 16 sweeps per block (the occupancy check below lowers it to what one SM
-    // holds); measured fastest at n = 2048 and 8192, band 16.  NLA_CHASE_GROUP
-    // overrides it (0: one sweep per block on the global band).
+    // Sweeps per block: FP32 up to 16 (the occupancy check below lowers it to what one
+    // SM holds), FP64 4 -- an FP64 block step is bound by the SM's small FP64 pipe, so
+    // more sweeps per SM slow every step down (measured at n = 256, 2048 and 8192).
+    // NLA_CHASE_GROUP overrides it (0: one sweep per block on the global band).
     static const int gset = [] {
         const char *v = getenv("NLA_CHASE_GROUP");
-        return v ? atoi(v) : 16;
+        return v ? atoi(v) : (sizeof(T) == 8 ? 4 : 16);
     }();
     auto kern = b == 16 ? band2bd_group_kernel<T, 16>
                 : b == 32 ? band2bd_group_kernel<T, 32>

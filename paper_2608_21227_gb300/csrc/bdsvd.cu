@@ -25,8 +25,9 @@
 //           absolute error level.  For FP64 output the coarse bracket stops at
 //           2^-16 and is widened by 2^-18 on both sides, which keeps the value
 //           inside it;
-//   fine:   (FP64 output) bisection with FP64 counts to 2^-51 of the bound, one
-//           thread per value.  The FP64 count forms 1/q from an FP32 estimate
+//   fine:   (FP64 output) multisection with FP64 counts to 2^-51 of the bound,
+//           kl lanes per value (kl = 1, plain bisection, for large n; more lanes
+//           when few values would leave most SMs idle).  The FP64 count forms 1/q from an FP32 estimate
 //           and two Newton-Raphson corrections r <- r + r (1 - q r) (quadratic
 //           convergence: ~2^-22 -> 2^-44 -> below FP64 rounding), i.e. four
 //           FMAs instead of a division.
@@ -147,27 +148,39 @@ coarse_kernel(int n, const double *__restrict__ hdr, const float *__restrict__ t
     }
 }
 
-// FP64 bisection from the widened coarse bracket, one thread per value.
+// FP64 search from the widened coarse bracket: a group of kl lanes (a power of two,
+// kl <= 32) per value counts at kl interior points per round (kl = 1: bisection).
+// Few values leave most SMs idle, so the host gives each value more lanes then.
 template <typename T>
 __global__ void __launch_bounds__(kBisectThreads)
 fine_kernel(int n, const double *__restrict__ hdr, const double *__restrict__ t2, const float2 *__restrict__ br,
-            T *__restrict__ S, double fine_tol) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n) return;
+            T *__restrict__ S, double fine_tol, int kl) {
+    const int idx = (blockIdx.x * blockDim.x + threadIdx.x) / kl;
+    const int l = threadIdx.x % kl;
+    const int gbase = (threadIdx.x & 31) & ~(kl - 1);
+    const unsigned gmask = (kl == 32 ? 0xffffffffu : ((1u << kl) - 1)) << gbase;
+    if (idx >= n) return;  // uniform over the group
     const double s = hdr[0];
     const int n2 = 2 * n - 1;
     const int j = n - 1 - idx;  // idx-th largest == j-th smallest; counts below x are negcount - n
     const float2 b = br[idx];
     double dlo = fmax(0.0, (double)b.x - 0x1p-18), dhi = fmin(1.0, (double)b.y + 0x1p-18);
+    const double frac = (double)(l + 1) / (double)(kl + 1);
     for (int it = 0; it < 80; ++it) {
-        const double mid = 0.5 * (dlo + dhi);
-        if (dhi - dlo <= fine_tol || mid <= dlo || mid >= dhi) break;
-        if (count_fine(n2, t2, mid) - n <= j)
-            dlo = mid;
-        else
-            dhi = mid;
+        const double x = fma(dhi - dlo, frac, dlo);
+        // stop at the tolerance or when the points no longer separate (FP64 spacing)
+        const bool done = dhi - dlo <= fine_tol || !(x > dlo && x < dhi);
+        if (__any_sync(gmask, done)) break;
+        const bool below = count_fine(n2, t2, x) - n <= j;
+        const unsigned full = gmask >> gbase;
+        const unsigned m = (__ballot_sync(gmask, below) >> gbase) & full;
+        const int f = m == full ? kl : __ffs(~m) - 1;  // first point whose count passes j; kl if none
+        const double xf = __shfl_sync(gmask, x, gbase + min(f, kl - 1));
+        const double xp = __shfl_sync(gmask, x, gbase + max(f - 1, 0));
+        if (f < kl) dhi = xf;
+        if (f > 0) dlo = xp;
     }
-    S[idx] = (T)(0.5 * (dlo + dhi) / s);
+    if (l == 0) S[idx] = (T)(0.5 * (dlo + dhi) / s);
 }
 
 template <typename T>
@@ -187,7 +200,14 @@ cudaError_t bdsvd_bisect(int n, const double *d, const double *e, T *S, void *sc
         return cudaGetLastError();
     }
     coarse_kernel<T><<<cblocks, kMsThreads, 0, st>>>(n, hdr, t2f, 0x1p-16f, br, nullptr);
-    fine_kernel<T><<<(n + kBisectThreads - 1) / kBisectThreads, kBisectThreads, 0, st>>>(n, hdr, t2, br, S, 0x1p-51);
+    // lanes per value: the largest power of two <= 32 that keeps n * kl / 32 warps
+    // within one per SM sub-partition (the FP64 count is bound by that pipe)
+    const long slots = 4L * device_sm_count() * 32;
+    int kl = 1;
+    while (kl < 32 && (long)n * kl * 2 <= slots) kl *= 2;
+    const long fthreads = (long)n * kl;
+    fine_kernel<T><<<(int)((fthreads + kBisectThreads - 1) / kBisectThreads), kBisectThreads, 0, st>>>(
+        n, hdr, t2, br, S, 0x1p-51, kl);
     return cudaGetLastError();
 }
 

@@ -147,6 +147,10 @@ def case(args):
     from . import inputs, kt
 
     dev = torch.device("cuda", 0)
+    if args.tuned:
+        import os
+
+        kt.load_config(os.path.join(os.path.dirname(os.path.abspath(__file__)), "tuned", "gb300.kt"))
     if args.batched:
         ms, ns = inputs.batch_shapes(args.batched, seed=3)
         mats = [torch.from_numpy(np.ascontiguousarray(inputs.gaussian(int(ms[i]), int(ns[i]), [3, i],
@@ -202,6 +206,7 @@ def main():
     c.add_argument("--batched", type=int, default=0)
     c.add_argument("--mlp", type=int, default=0)
     c.add_argument("--reps", type=int, default=2)
+    c.add_argument("--tuned", action="store_true", help="install the tuned table first")
     args = ap.parse_args()
     t0 = time.time()
     {"mixed": mixed, "latency": latency, "case": case}[args.cmd](args)
