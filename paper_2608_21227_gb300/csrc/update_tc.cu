@@ -79,6 +79,35 @@ NLA_DEV int scale_exp(double mx) {
     return e;
 }
 
+// GB300's FP64 pipe issues a small fraction of the FP32/integer rate, so the
+// per-element scaling and conversions below work on the IEEE bit patterns with
+// integer instructions.  An FP64 x = (-1)^s 1.m 2^(E-1023) (biased exponent E of
+// 11 bits, 52-bit m) is normal or zero throughout (subnormal inputs read as 0).
+// Biased exponent of |x| (0 for zero); the scale exponent of a set of values is
+// max(E) - 1022 (the frexp exponent of the largest), 0 if all are zero.
+NLA_DEV int f64_biased_exp(double x) { return (int)(((uint32_t)__double2hiint(x) >> 20) & 0x7FFu); }
+NLA_DEV int scale_exp_from_biased(int emax) { return emax > 0 ? emax - 1022 : 0; }
+// x * 2^-e as FP32 (exact scaling; the mantissa is truncated to FP32's 23 bits, far
+// below the TF32/BF16 rounding that follows); results below FP32's normal range are 0.
+NLA_DEV float f64_scaled_to_f32(double x, int e) {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const int E = (int)((hi >> 20) & 0x7FFu);
+    const int fe = E - 1023 + 127 - e;
+    const uint32_t sign = hi & 0x80000000u;
+    if (E == 0 || fe <= 0) return __uint_as_float(sign);
+    if (fe >= 255) return __uint_as_float(sign | 0x7F800000u);  // beyond FP32 (or not finite)
+    const uint32_t mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
+    return __uint_as_float(sign | ((uint32_t)fe << 23) | mant);
+}
+// v * 2^e as FP64 (exact); FP32 zeros and subnormals give 0.
+NLA_DEV double f32_scaled_to_f64(float v, int e) {
+    const uint32_t b = __float_as_uint(v);
+    const int E8 = (int)((b >> 23) & 0xFFu);
+    if (E8 == 0) return 0.0;
+    const uint32_t hi = (b & 0x80000000u) | ((uint32_t)(E8 - 127 + 1023 + e) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 struct TcShared {
     uint64_t mbar[3];
     uint32_t tmem_base;
@@ -182,7 +211,7 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
     unsigned char *A1 = sm;                                  // 2 x [128 x kKt]  X tile (strip line x K)
     unsigned char *B1 = A1 + 2 * kStrip * rb1;               // 2 x [64 x kKt]   V tile (reflector x K)
     int *ex1 = reinterpret_cast<int *>(B1 + 2 * 64 * rb1);   // 2 x 128
-    double *lmax = reinterpret_cast<double *>(ex1 + 2 * kStrip);  // 2 x 128
+    int *lmax = ex1 + 2 * kStrip;                            // 2 x 128 biased exponents
     TcShared *sh = reinterpret_cast<TcShared *>(lmax + 2 * kStrip);
     float *Wsh = reinterpret_cast<float *>(sm);              // reused after the MMAs: nbp x 128
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -219,17 +248,26 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
         if (t < ntiles) {
             const int k0 = kbeg + t * kKt;
             double xv[16];
-            double mx = 0.0;
+            if (SIDE == 0) {
+                // lanes over the tile's 32 rows, warp w over strip columns 16w .. 16w+15:
+                // coalesced column segments; the column's scale from a warp-wide max
+                const int kk = k0 + lane;
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-                const int kk = k0 + h * 16 + i;
-                double v = 0.0;
-                if (m < lw && kk < kend)
-                    v = SIDE == 0 ? X[kk + (long)(L0 + m) * ldx] : X[(L0 + m) + (long)kk * ldx];
-                xv[i] = v;
-                mx = fmax(mx, fabs(v));
+                for (int c = 0; c < 16; ++c) {
+                    const int mc = warp * 16 + c;
+                    xv[c] = (mc < lw && kk < kend) ? X[kk + (long)(L0 + mc) * ldx] : 0.0;
+                }
+            } else {
+                int emx = 0;
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const int kk = k0 + h * 16 + i;
+                    const double v = (m < lw && kk < kend) ? X[(L0 + m) + (long)kk * ldx] : 0.0;
+                    xv[i] = v;
+                    emx = max(emx, f64_biased_exp(v));
+                }
+                lmax[h * kStrip + m] = emx;
             }
-            lmax[h * kStrip + m] = mx;
             for (int idx = tid; idx < nbp * kKt; idx += blockDim.x) {
                 int n, k;
                 if (SIDE == 0) {
@@ -245,14 +283,24 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
                     else
                         v = g > n ? V[n + (long)g * ldv] : (g == n ? 1.0 : 0.0);
                 }
-                P::put(B1 + buf * 64 * rb1, tc::kmajor_off(n, k, es, rb1), (float)v);
+                P::put(B1 + buf * 64 * rb1, tc::kmajor_off(n, k, es, rb1), f64_scaled_to_f32(v, 0));
             }
-            __syncthreads();
-            const int e = scale_exp(fmax(lmax[m], lmax[kStrip + m]));
-            if (h == 0) ex1[buf * kStrip + m] = e;
+            if (SIDE == 0) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-                P::put(A1 + buf * kStrip * rb1, tc::kmajor_off(m, h * 16 + i, es, rb1), (float)ldexp(xv[i], -e));
+                for (int c = 0; c < 16; ++c) {
+                    const int mc = warp * 16 + c;
+                    const int e = scale_exp_from_biased(__reduce_max_sync(0xffffffffu, f64_biased_exp(xv[c])));
+                    if (lane == 0) ex1[buf * kStrip + mc] = e;
+                    P::put(A1 + buf * kStrip * rb1, tc::kmajor_off(mc, lane, es, rb1), f64_scaled_to_f32(xv[c], e));
+                }
+            } else {
+                __syncthreads();
+                const int e = scale_exp_from_biased(max(lmax[m], lmax[kStrip + m]));
+                if (h == 0) ex1[buf * kStrip + m] = e;
+#pragma unroll
+                for (int i = 0; i < 16; ++i)
+                    P::put(A1 + buf * kStrip * rb1, tc::kmajor_off(m, h * 16 + i, es, rb1), f64_scaled_to_f32(xv[i], e));
+            }
             tc::fence_async_smem();
             tc::fence_before_sync();
             __syncthreads();
@@ -381,7 +429,7 @@ tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__rest
             else
                 v = g > k ? V[k + (long)g * ldv] : (g == k ? 1.0 : 0.0);
         }
-        P::put(SIDE == 0 ? Aop : Bop, tc::kmajor_off(r, k, es, rb3), (float)v);
+        P::put(SIDE == 0 ? Aop : Bop, tc::kmajor_off(r, k, es, rb3), f64_scaled_to_f32(v, 0));
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -410,12 +458,12 @@ tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__rest
                 if (SIDE == 0) {
                     if (row < tw && col < lw) {
                         double *px = X + (T0 + row) + (long)(L0 + col) * ldx;
-                        *px -= ldexp((double)v[i], exs[col]);
+                        *px -= f32_scaled_to_f64(v[i], exs[col]);
                     }
                 } else {
                     if (row < lw && col < tw) {
                         double *px = X + (L0 + row) + (long)(T0 + col) * ldx;
-                        *px -= ldexp((double)v[i], exs[row]);
+                        *px -= f32_scaled_to_f64(v[i], exs[row]);
                     }
                 }
             }
