@@ -241,20 +241,20 @@ def extras(n, dev, stream, tuned_ms):
     ok = bool((bt.info == 0).all().item())
     # the plain FP64 path looped over a sample of the same matrices (upcast), same GPU
     k = 100
-    wl = nla.workspace(nla.gesvd_vals_workspace(1024, 256, nla.F64, preserve_a=True), dev)
+    wl = nla.workspace(nla.gesvd_vals_workspace(1024, 256, nla.F64, cfg=DEFAULT_CFG, preserve_a=True), dev)
     sample = [m.double() for m in mats[:k]]
     Sl = torch.empty(256, dtype=torch.float64, device=dev)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for a in sample:
-        nla.gesvd_vals(a, preserve_a=True, work=wl, S=Sl[: min(a.shape)], info=info, stream=stream)
+    for a in sample:  # the plain, untuned FP64 path
+        nla.gesvd_vals(a, cfg=DEFAULT_CFG, preserve_a=True, work=wl, S=Sl[: min(a.shape)], info=info, stream=stream)
     torch.cuda.synchronize()
     loop_per = (time.perf_counter() - t0) / k
     out["batched"] = {"workload": "10000 FP32 matrices, n~U{8..256}, m/n~U[1,4], N(0,1)", "ms_per_batch": round(b_ms, 3),
                       "matrices_per_s": round(10000 / (b_ms / 1e3), 1), "all_info_zero": ok,
                       "fp64_loop_matrices_per_s": round(1.0 / loop_per, 1),
                       "speedup_vs_fp64_loop": round((10000 / (b_ms / 1e3)) * loop_per, 1),
-                      "fp64_loop_sample": f"first {k} matrices, upcast, one nla_gesvd_vals call each"}
+                      "fp64_loop_sample": f"first {k} matrices, upcast, one nla_gesvd_vals call each, default configuration"}
     return out
 
 

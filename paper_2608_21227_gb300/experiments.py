@@ -1,11 +1,12 @@
 """Measurement drivers beside the benchmark: mixed-precision accuracy / speed and small-case latency.
 
-    python -m paper_2608_21227_gb300.experiments mixed --out tuned/mixed_gb300.json
+    python -m paper_2608_21227_gb300.experiments mixed --table tuned/gb300.kt --out tuned/mixed_gb300.json
     python -m paper_2608_21227_gb300.experiments latency --out tuned/latency_gb300.json
 
 mixed:   A = U diag(sigma) V^T stored in FP64 with Haar-random U, V and sigma_i =
          kappa^(-(i-1)/(p-1)), kappa in {1, 1e4, 1e8}, shapes 16384^2 and 32768 x 8192.
-         For the FP64-native, TF32 and BF16 trailing updates: the error max_i |s_i - sigma_i|
+         The FP64-native path runs untuned (default configuration); the TF32 and BF16
+         forms run with the tuned table (--table).  For each: the error max_i |s_i - sigma_i|
          / sigma_1 against the prescribed sigma (the input is formed in FP64, so its own
          singular values are within ~1e-14 sigma_1 of sigma), the error against the FP64
          path, the median relative error over sigma_i >= 1e-3 sigma_1, and the time (CUDA
@@ -53,9 +54,12 @@ def prescribed(m, n, kappa, seed, device):
     return A.contiguous(), sigma
 
 
-def timed_call(A, update, reps):
+def timed_call(A, update, reps, table=None):
     import torch
 
+    from . import kt
+
+    kt.load_config(table)  # None: untuned defaults
     ts, S = [], None
     for _ in range(reps):
         B = A.clone()
@@ -83,11 +87,12 @@ def mixed(args):
             sig = sigma.cpu().numpy()
             reps = args.reps if kappa == args.kappas[0] else 1
             t64, s64 = timed_call(A, nla.UPD_NATIVE, reps)
-            rec = {"m": m, "n": n, "kappa": kappa, "seed": seed, "fp64_ms": t64,
+            rec = {"m": m, "n": n, "kappa": kappa, "seed": seed, "fp64_ms": t64, "fp64_config": "default",
+                   "mixed_config": "tuned table" if args.table else "default",
                    "fp64_err_vs_sigma": float(np.max(np.abs(s64 - sig)) / sig[0])}
             mask = sig >= 1e-3 * sig[0]
             for name, upd in (("tf32", nla.UPD_TF32), ("bf16", nla.UPD_BF16)):
-                t, s = timed_call(A, upd, reps)
+                t, s = timed_call(A, upd, reps, args.table)
                 rec[name] = {"ms": t, "speedup_vs_fp64": t64 / t,
                              "err_vs_sigma": float(np.max(np.abs(s - sig)) / sig[0]),
                              "err_vs_fp64": float(np.max(np.abs(s - s64)) / s64[0]),
@@ -196,6 +201,7 @@ def main():
     m.add_argument("--shapes", nargs="+", default=["16384x16384", "32768x8192"])
     m.add_argument("--kappas", type=float, nargs="+", default=[1.0, 1e4, 1e8])
     m.add_argument("--reps", type=int, default=2)
+    m.add_argument("--table", help="tuned table for the TF32 / BF16 forms")
     m.add_argument("--out")
     la = sub.add_parser("latency")
     la.add_argument("--out")

@@ -176,7 +176,7 @@ def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
     s = sub.add_parser("sweep")
-    s.add_argument("--sizes", type=int, nargs="+", default=[1024, 2048, 4096, 8192])
+    s.add_argument("--sizes", type=int, nargs="*", default=[1024, 2048, 4096, 8192])
     s.add_argument("--dtypes", nargs="+", default=["f32", "f64"])
     s.add_argument("--bands", type=int, nargs="+", default=[16, 32, 64])
     s.add_argument("--reps", type=int, default=5)
