@@ -151,11 +151,26 @@ def trail_bytes_per_step(M, N, b, side, elem=4):
     return tot
 
 
+def fused_update_bytes_per_step(M, N, b, elem=4):
+    """Algorithmic bytes of the fused FP32 update schedule in one step: per panel pair the QR
+    projection reads the trailing block, the QR update of the row block reads and writes b rows,
+    the fused pass (QR update of the rows below + LQ projection) reads and writes the rest once,
+    and the LQ update reads and writes it once more (V, W', Y' are small)."""
+    tot = 0.0
+    for kb in range(0, N, b):
+        nb = min(b, N - kb)
+        c0 = kb + nb
+        if c0 >= N:
+            break
+        tot += elem * (M - kb) * (N - c0) + 2.0 * elem * nb * (N - c0) + 4.0 * elem * (M - c0) * (N - c0)
+    return tot
+
+
 # kernels each traced region launches on the FP32 path (panel: one cluster or grid kernel;
-# trailing update: projection + update; chase: sweeps + bidiagonal extraction; bisection:
-# preparation + multisection)
-KERNELS_PER_REGION = {"panel_qr": 1, "panel_lq": 1, "trail_left": 2, "trail_right": 2, "stage_copy": 1,
-                      "band_extract": 1, "band2bd": 2, "bisect": 2, "batched": 2}
+# trailing update: projection + update in one region, or -- fused schedule -- one kernel
+# per region; chase: sweeps + bidiagonal extraction; bisection: preparation + multisection)
+KERNELS_PER_REGION = {"panel_qr": 1, "panel_lq": 1, "trail_left": 2, "trail_right": 2, "trail_fused": 1,
+                      "stage_copy": 1, "band_extract": 1, "band2bd": 2, "bisect": 2, "batched": 2}
 
 
 def run_reference(args, rank):
@@ -241,15 +256,20 @@ def extras(n, dev, stream, tuned_ms):
     ok = bool((bt.info == 0).all().item())
     # the plain FP64 path looped over a sample of the same matrices (upcast), same GPU
     k = 100
-    wl = nla.workspace(nla.gesvd_vals_workspace(1024, 256, nla.F64, cfg=DEFAULT_CFG, preserve_a=True), dev)
+    wl = nla.workspace(nla.gesvd_vals_workspace(1024, 256, nla.F64, cfg=DEFAULT_CFG, preserve_a=True) * 2, dev)
     sample = [m.double() for m in mats[:k]]
     Sl = torch.empty(256, dtype=torch.float64, device=dev)
+    from paper_2608_21227_gb300 import kt
+
+    kt.load_config(None)  # the plain, untuned FP64 path: default configuration for every shape
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for a in sample:  # the plain, untuned FP64 path
-        nla.gesvd_vals(a, cfg=DEFAULT_CFG, preserve_a=True, work=wl, S=Sl[: min(a.shape)], info=info, stream=stream)
+    for a in sample:
+        nla.gesvd_vals(a, preserve_a=True, work=wl, S=Sl[: min(a.shape)], info=info, stream=stream)
     torch.cuda.synchronize()
     loop_per = (time.perf_counter() - t0) / k
+    if os.path.exists(TABLE):
+        kt.load_config(TABLE)
     out["batched"] = {"workload": "10000 FP32 matrices, n~U{8..256}, m/n~U[1,4], N(0,1)", "ms_per_batch": round(b_ms, 3),
                       "matrices_per_s": round(10000 / (b_ms / 1e3), 1), "all_info_zero": ok,
                       "fp64_loop_matrices_per_s": round(1.0 / loop_per, 1),
@@ -371,8 +391,16 @@ def main():
     e2e_value = world * flops(n, n) / (float(t_e2e.item()) / 1e3) / 1e9
 
     # ---------------- roofline of the dominant kernel (live CUDA-event timing of its launches)
-    launches = sum(v[0] * KERNELS_PER_REGION.get(k, 1) for k, v in trace.items())
-    dom = max(trace.items(), key=lambda kv: kv[1][1])[0] if trace else None
+    fused = "trail_fused" in trace
+    per_region = dict(KERNELS_PER_REGION, **({"trail_left": 1, "trail_right": 1} if fused else {}))
+    launches = sum(v[0] * per_region.get(k, 1) for k, v in trace.items())
+    # the trailing update is one memory stream split over its regions: judged as a whole
+    upd_regions = [k for k in ("trail_left", "trail_fused", "trail_right") if k in trace]
+    upd_ms = sum(trace[k][1] for k in upd_regions)
+    shares = {k: v[1] for k, v in trace.items() if k not in upd_regions}
+    if upd_regions:
+        shares["trail"] = upd_ms
+    dom = max(shares.items(), key=lambda kv: kv[1])[0] if shares else None
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -380,26 +408,21 @@ def main():
     except Exception:
         pass
     roof = None
-    if dom in ("trail_left", "trail_right"):
-        side = 0 if dom == "trail_left" else 1
-        b = nla.plan_cfg(n, n, nla.F32, side=side)[0]
-        sm_max = peaks.get("sm_max_mhz", 2070.0)
-        ffma = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FFMA lanes x 2 flop x max SM clock
+    if dom == "trail":
+        b = nla.plan_cfg(n, n, nla.F32, side=0)[0]
         hbm = peaks.get("hbm_gbs", 6769.4)
-        secs = trace[dom][1] / 1e3
-        if (b / 3.0) * hbm / 1e3 < ffma:  # 3-pass update: b/3 flop per byte -> HBM bound
-            byts = trail_bytes_per_step(n, n, b, side) * args.steps
-            achieved = byts / secs / 1e9
-            roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                    "frac": round(achieved / hbm, 4), "traffic": None,
-                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)",
-                    "note": "3-pass bytes (read X twice, write once); trailing blocks below 129 MB run from L2"}
+        secs = upd_ms / 1e3
+        if fused:
+            byts = fused_update_bytes_per_step(n, n, b) * args.steps
+            note = ("fused schedule: QR projection read + row-block update + fused pass (QR update below the "
+                    "row block + LQ projection) + LQ update; trailing blocks below 129 MB run from L2")
         else:
-            fl = trail_flops_per_step(n, n, b, side) * args.steps
-            achieved = fl / secs / 1e12
-            roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 3), "peak": round(ffma, 2),
-                    "unit": "TFLOP/s", "frac": round(achieved / ffma, 4), "traffic": None,
-                    "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 flop x max SM clock"}
+            byts = (trail_bytes_per_step(n, n, b, 0) + trail_bytes_per_step(n, n, b, 1)) * args.steps
+            note = "3-pass bytes per side (read X twice, write once); trailing blocks below 129 MB run from L2"
+        achieved = byts / secs / 1e9
+        roof = {"kernel": "trailing update (" + " + ".join(upd_regions) + ")", "bound": "hbm",
+                "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)", "note": note}
     elif dom == "band2bd":
         # each block step reads and writes its window: 3 b^2 entries, about n^2 / (2 b) steps
         b = nla.plan_cfg(n, n, nla.F32, side=0)[0]

@@ -144,6 +144,21 @@ bool lookahead_enabled() {
     return on;
 }
 
+// FP32: the QR update of the rows below each row block fused with the LQ
+// projection (one pass over X instead of two).  Off by default (NLA_FUSED=1): the
+// fused pass does 2b FMAs per element and is bound by instruction issue, so at 8192
+// it took 60 ms per SVD where the two passes it replaces take 48 (206.2 vs 193.5 ms).
+bool fused_enabled() {
+    static const bool on = [] {
+        const char *v = getenv("NLA_FUSED");
+        return v && atoi(v) != 0;
+    }();
+    return on;
+}
+
+nla_status run_stage1_fused(float *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
+                            float *tauq_all, float *taup_all, int *dInfo, cudaStream_t st);
+
 template <typename T>
 nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
                       T *tauq_all, T *taup_all, int *dInfo, cudaStream_t st) {
@@ -154,6 +169,8 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
                 return run_stage1_lookahead(X, ldx, M, N, p, bufs, tauq_all, taup_all, dInfo, st, *ax);
             }
         }
+        if (p.update == NLA_UPD_NATIVE && (p.b == 16 || p.b == 32 || p.b == 64) && fused_enabled())
+            return run_stage1_fused(X, ldx, M, N, p, bufs, tauq_all, taup_all, dInfo, st);
     }
     const int b = p.b;
     nla::PanelCtl ctl{bufs.bar, bufs.part, dInfo};
@@ -316,6 +333,61 @@ nla_status run_stage1_lookahead(float *X, long ldx, int M, int N, const Stage1Pl
                        nla::trail_right<float>(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.right, usc, st),
                        "LQ trailing update");
         }
+    }
+    return NLA_OK;
+}
+
+// Algorithm 1 for FP32 with the TMA-streamed update and one fused pass per step:
+// QR panel; QR projection (W' = T^T V^T X); QR update of the b rows the LQ panel
+// factors; LQ panel; fused pass (QR update of the rows below + LQ projection
+// Y' = X U T); LQ update X -= Y' U^T.  Steps the TMA kernels cannot take (ragged
+// band, unaligned blocks) run the separate passes.
+nla_status run_stage1_fused(float *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
+                            float *tauq_all, float *taup_all, int *dInfo, cudaStream_t st) {
+    const int b = p.b;
+    nla::PanelCtl ctl{bufs.bar, bufs.part, dInfo};
+    const nla::UpdScratch usc{bufs.upd_work, bufs.tickets, dInfo};
+    float *Tq = reinterpret_cast<float *>(bufs.Tq), *Tp = reinterpret_cast<float *>(bufs.Tp);
+    for (int kb = 0; kb < N; kb += b) {
+        const int nb = std::min(b, N - kb);
+        float *tq = tauq_all ? tauq_all + kb : reinterpret_cast<float *>(bufs.tauq);
+        float *tp = taup_all ? taup_all + kb : reinterpret_cast<float *>(bufs.taup);
+        float *panel = X + kb + (long)kb * ldx;
+        NLA_LAUNCH(nla::kTrPanelQR, st, nla::panel_factor<float>(panel, 1, ldx, M - kb, nb, tq, Tq, ctl, st), "QR panel");
+        const int c0 = kb + nb;
+        if (c0 >= N) break;
+        float *Xl = X + kb + (long)c0 * ldx;  // rows kb.., columns c0..
+        float *rowp = Xl;                      // LQ panel(r, c) = rowp[c + r*ldx]
+        float *Xr = X + c0 + (long)c0 * ldx;
+        const bool fuse = M - c0 > 0 && nb == b && nla::trail_tma_fused_ok(nb, p.right) &&
+                          nla::tma_cfg_valid(nb, p.left) && nla::trail_tma_eligible(Xl, ldx, panel, ldx, nb, usc) &&
+                          nla::trail_tma_eligible(Xr, ldx, rowp, ldx, nb, usc);
+        if (!fuse) {
+            NLA_LAUNCH(nla::kTrTrailLeft, st,
+                       nla::trail_left<float>(Xl, ldx, M - kb, N - c0, panel, ldx, nb, Tq, p.left, usc, st),
+                       "QR trailing update");
+            NLA_LAUNCH(nla::kTrPanelLQ, st, nla::panel_factor<float>(rowp, ldx, 1, N - c0, nb, tp, Tp, ctl, st),
+                       "LQ panel");
+            if (M - c0 > 0)
+                NLA_LAUNCH(nla::kTrTrailRight, st,
+                           nla::trail_right<float>(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.right, usc, st),
+                           "LQ trailing update");
+            continue;
+        }
+        NLA_LAUNCH(nla::kTrTrailLeft, st,
+                   nla::trail_tma_project(0, Xl, ldx, M - kb, N - c0, panel, ldx, nb, Tq, p.left, usc, st),
+                   "QR projection");
+        NLA_LAUNCH(nla::kTrTrailLeft, st,
+                   nla::trail_tma_apply(0, Xl, ldx, M - kb, N - c0, panel, ldx, nb, 0, nb, p.left, usc, st),
+                   "QR update of the row block");
+        NLA_LAUNCH(nla::kTrPanelLQ, st, nla::panel_factor<float>(rowp, ldx, 1, N - c0, nb, tp, Tp, ctl, st), "LQ panel");
+        const float *ylq = nullptr;
+        NLA_LAUNCH(nla::kTrTrailFused, st,
+                   nla::trail_tma_fused(Xl, ldx, M - kb, N - c0, panel, ldx, nb, rowp, ldx, Tp, p.right, usc, st, &ylq),
+                   "QR update + LQ projection");
+        NLA_LAUNCH(nla::kTrTrailRight, st,
+                   nla::trail_tma_apply(1, Xr, ldx, M - c0, N - c0, rowp, ldx, nb, 0, N - c0, p.right, usc, st, ylq),
+                   "LQ trailing update");
     }
     return NLA_OK;
 }

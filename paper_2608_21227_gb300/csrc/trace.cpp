@@ -10,7 +10,8 @@
 namespace {
 
 const char *const kNames[nla::kTraceClasses] = {"panel_qr",     "panel_lq", "trail_left", "trail_right", "stage_copy",
-                                                "band_extract", "band2bd",  "bisect",     "batched"};
+                                                "band_extract", "band2bd",  "bisect",     "batched",
+                                                "trail_fused"};
 
 struct Rec {
     int cls;

@@ -14,6 +14,7 @@ enum TraceClass {
     kTrBand2bd,
     kTrBisect,
     kTrBatched,
+    kTrTrailFused,
     kTraceClasses
 };
 
