@@ -500,6 +500,222 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
     cluster.sync();  // no block leaves while another may still write to its shared memory
 }
 
+// ------------------------------------------------------------------ register-resident cluster variant
+// The same factorisation with each thread holding its panel rows in registers
+// (thread t of block p owns rows r0 + t + 512 q, q < RP; nb = NB fixed).  With
+// column indices instead of item indices, the partial sums of column j are
+//   x . a_c over rows below j, for every column c:
+//   c == j: ||x||^2;  c > j: x . a_c (trailing);  c < j: x . v_c (finished reflector c),
+// so one product per owned entry gives them all.  Per column: products and a warp
+// reduce-scatter in registers, per-warp sums into shared memory, a block barrier;
+// warp 0 adds the warps, pushes the block's sums (and row j, by its owner) to every
+// block over DSMEM, arrives on their barriers, waits for its own, forms beta / tau
+// and the coefficients; a block barrier; every thread updates its own rows.  Two
+// block barriers per column and no shared-memory pass over the panel.
+
+// Sum v[0..NB-1] over the warp's lanes, leaving the sum of column (NB == 32 ? lane
+// : lane >> 1) in the return value: halving exchanges (upper lanes keep the upper half).
+template <typename T, int NB>
+NLA_DEV T warp_reduce_scatter(T (&v)[NB], int lane) {
+#pragma unroll
+    for (int h = NB / 2, o = 16; h >= 1; h /= 2, o /= 2) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T send = up ? v[i] : v[i + h];
+            const T keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    if (NB == 16) v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    return v[0];
+}
+
+template <typename T, int NB>
+NLA_DEV T select_col(const T (&a)[NB], int j) {
+    T x = T(0);
+#pragma unroll
+    for (int c = 0; c < NB; ++c) x = c == j ? a[c] : x;
+    return x;
+}
+
+template <typename T, int NB, int RP>
+__global__ void __launch_bounds__(kClusterThreads, 1)
+panel_reg_kernel(T *__restrict__ P, long rs, long cs, int M, int R, T *__restrict__ tau, T *__restrict__ Tm,
+                 int *info) {
+    static_assert(NB == 16 || NB == 32, "NB");
+    cg::cluster_group cluster = cg::this_cluster();
+    const int p = (int)cluster.block_rank(), nP = (int)cluster.num_blocks();
+    constexpr int kWarps = kClusterThreads / 32;
+    __shared__ T red[kWarps][NB];   // per-warp column sums
+    __shared__ T inbox[2][16][NB];  // by column parity and source block
+    __shared__ T rowin[2][NB];
+    __shared__ T myrow[NB];
+    __shared__ T wcoef[NB];  // tau (v . a_c) for c > j, 0 otherwise
+    __shared__ T taus[NB];
+    // block 0: T(i, k), i <= k, at Tsh[i + k*NB]; G(i, k) = v_i . v_k, i < k, at Tsh[k + i*NB]
+    __shared__ T Tsh[NB * NB];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ T sh_scale, sh_beta;
+    __shared__ int sh_abort;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int r0 = p * R;
+    const int nr = max(0, min(M, r0 + R) - r0);
+    const int kmax = min(NB, M);
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], nP);
+        tc::mbar_init(&mbar[1], nP);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        sh_abort = 0;
+    }
+    if (p == 0) {
+        for (int j = kmax + tid; j < NB; j += blockDim.x) tau[j] = T(0);
+        for (int i = tid; i < NB * NB; i += blockDim.x) Tsh[i] = T(0);
+    }
+    T a[RP][NB];
+#pragma unroll
+    for (int q = 0; q < RP; ++q) {
+        const int rr = tid + kClusterThreads * q;
+#pragma unroll
+        for (int c = 0; c < NB; ++c) a[q][c] = rr < nr ? P[(long)(r0 + rr) * rs + (long)c * cs] : T(0);
+    }
+    cluster.sync();  // every block's barriers are initialised before the first remote arrive
+    for (int j = 0; j < kmax; ++j) {
+        const int buf = j & 1;
+        T prod[NB];
+#pragma unroll
+        for (int c = 0; c < NB; ++c) prod[c] = T(0);
+#pragma unroll
+        for (int q = 0; q < RP; ++q) {
+            const int rr = tid + kClusterThreads * q;
+            const T x = (rr < nr && r0 + rr > j) ? select_col<T, NB>(a[q], j) : T(0);
+#pragma unroll
+            for (int c = 0; c < NB; ++c) prod[c] = fma(x, a[q][c], prod[c]);
+        }
+        const T wsum = warp_reduce_scatter<T, NB>(prod, lane);
+        if (NB == 32 || (lane & 1) == 0) red[warp][NB == 32 ? lane : lane >> 1] = wsum;
+        if (j >= r0 && j < r0 + nr) {  // the owner of row j publishes it
+            const int rr = j - r0;
+            if (tid == rr % kClusterThreads) {
+#pragma unroll
+                for (int q = 0; q < RP; ++q)
+                    if (q == rr / kClusterThreads) {
+#pragma unroll
+                        for (int c = 0; c < NB; ++c) myrow[c] = a[q][c];
+                    }
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const bool owner = j >= r0 && j < r0 + nr;
+            T sblk = T(0);
+            if (lane < NB) {
+#pragma unroll 4
+                for (int w = 0; w < kWarps; ++w) sblk += red[w][lane];
+                const T rv = owner ? myrow[lane] : T(0);
+                for (int q = 0; q < nP; ++q) {
+                    cluster.map_shared_rank(&inbox[buf][p][0], q)[lane] = sblk;
+                    if (owner) cluster.map_shared_rank(&rowin[buf][0], q)[lane] = rv;
+                }
+            }
+            __syncwarp();  // the warp's pushes precede the arrivals below
+            if (lane < nP) mbar_arrive_remote(cluster_addr(&mbar[buf], lane));
+            if (lane == 0 && !sh_abort) {
+                const uint32_t par = (uint32_t)((j >> 1) & 1);
+                if (!mbar_try_wait_cluster(&mbar[buf], par)) {
+                    const unsigned long long t0 = global_ns();
+                    while (!mbar_try_wait_cluster(&mbar[buf], par)) {
+                        if (global_ns() - t0 > kSpinBudgetNs) {
+                            if (info) atomicExch(info, kInfoTimeout);
+                            sh_abort = 1;
+                            break;
+                        }
+                    }
+                }
+            }
+            __syncwarp();  // lane 0's acquire orders the warp's reads below
+            T sc_ = T(0), wc_ = T(0);
+            if (lane < NB) {
+                for (int q = 0; q < nP; ++q) sc_ += inbox[buf][q][lane];
+                wc_ = rowin[buf][lane];
+            }
+            const T alpha = __shfl_sync(0xffffffffu, wc_, j), xn2 = __shfl_sync(0xffffffffu, sc_, j);
+            T tj = T(0), beta = alpha, scale = T(0);
+            if (xn2 > T(0)) {
+                if constexpr (sizeof(T) == 4) {  // a few ulp, far inside the FP32 path's tolerance
+                    const float q = alpha * alpha + xn2;
+                    const float r = q * rsqrtf(q);
+                    beta = alpha >= 0.f ? -r : r;
+                    tj = __fdividef(beta - alpha, beta);
+                    scale = __fdividef(1.f, alpha - beta);
+                } else {
+                    const T r = sqrt(alpha * alpha + xn2);
+                    beta = alpha >= T(0) ? -r : r;
+                    tj = (beta - alpha) / beta;
+                    scale = T(1) / (alpha - beta);
+                }
+            }
+            if (lane < NB) {
+                const T vdot = wc_ + scale * sc_;  // v . a_c (c > j) or G(c, j) = v_c . v_j (c < j)
+                wcoef[lane] = lane > j ? tj * vdot : T(0);
+                if (p == 0 && lane < j) Tsh[j + lane * NB] = vdot;
+            }
+            if (lane == 0) {
+                sh_scale = scale;
+                sh_beta = beta;
+                taus[j] = tj;
+                if (p == 0) tau[j] = tj;
+            }
+        }
+        __syncthreads();
+        const T tj = taus[j];
+        if (tj != T(0)) {
+            const T scl = sh_scale, bt = sh_beta;
+            T w[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) w[c] = wcoef[c];
+#pragma unroll
+            for (int q = 0; q < RP; ++q) {
+                const int rr = tid + kClusterThreads * q, gr = r0 + rr;
+                if (rr < nr && gr >= j) {
+                    // rows below j: a_c -= v w_c with v = x / (alpha - beta), and v into column j;
+                    // row j: a_c -= w_c (v_j = 1), beta into column j
+                    const T v = gr > j ? select_col<T, NB>(a[q], j) * scl : T(1);
+#pragma unroll
+                    for (int c = 0; c < NB; ++c) a[q][c] = c == j ? (gr > j ? v : bt) : fma(-v, w[c], a[q][c]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < RP; ++q) {
+        const int rr = tid + kClusterThreads * q;
+        if (rr < nr) {
+#pragma unroll
+            for (int c = 0; c < NB; ++c) P[(long)(r0 + rr) * rs + (long)c * cs] = a[q][c];
+        }
+    }
+    if (p == 0) {
+        __syncthreads();
+        // T(0:k, k) = -tau_k T(0:k, 0:k) G(0:k, k), T(k, k) = tau_k -- one warp, column by column
+        if (warp == 0) {
+            for (int kk = 0; kk < kmax; ++kk) {
+                const T tk = taus[kk];
+                for (int i = lane; i < kk; i += 32) {
+                    T t = T(0);
+                    for (int q = i; q < kk; ++q) t += Tsh[i + q * NB] * Tsh[kk + q * NB];  // T(i, q) G(q, kk)
+                    Tsh[i + kk * NB] = -tk * t;
+                }
+                if (lane == 0) Tsh[kk + kk * NB] = tk;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int idx = tid; idx < NB * NB; idx += blockDim.x) Tm[idx] = (idx % NB) <= (idx / NB) ? Tsh[idx] : T(0);
+    }
+    cluster.sync();  // no block leaves while another may still write to its shared memory
+}
+
 // Cluster size and rows per block for an M x nb panel, or 0 if it does not fit one cluster.
 // Which cluster sizes the device can schedule (one block per SM at the largest
 // dynamic shared memory) is asked once; smaller allocations schedule as well.
@@ -561,6 +777,52 @@ static int cluster_plan(int M, int nb, int &R, size_t &dyn) {
     return best;
 }
 
+// Register-resident cluster panel for the shapes it is built for (nb 16 or 32, one
+// row per thread: at most 512 rows per block); cudaErrorNotSupported otherwise.
+// NLA_PANEL_REG=0 keeps the shared-memory variant.
+template <typename T, int NB, int RP>
+cudaError_t panel_reg_launch_nb(T *P, long rs, long cs, int M, int R, int C, T *tau, T *Tm, int *info,
+                                cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        attr = true;
+        cudaFuncSetAttribute(panel_reg_kernel<T, NB, RP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kClusterThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, panel_reg_kernel<T, NB, RP>, P, rs, cs, M, R, tau, Tm, info);
+}
+
+template <typename T>
+cudaError_t panel_reg_launch(T *P, long rs, long cs, int M, int nb, int R, int C, T *tau, T *Tm, int *info,
+                             cudaStream_t st) {
+    static const bool on = [] {
+        const char *v = getenv("NLA_PANEL_REG");
+        return !v || atoi(v) != 0;
+    }();
+    if (!on || C > 16) return cudaErrorNotSupported;
+    const int rp = (R + kClusterThreads - 1) / kClusterThreads;
+    if constexpr (sizeof(T) == 4) {
+        // (two or more rows per thread spill at the 128-register limit of 512 threads)
+        if (nb == 16 && rp == 1) return panel_reg_launch_nb<T, 16, 1>(P, rs, cs, M, R, C, tau, Tm, info, st);
+        if (nb == 32 && rp == 1) return panel_reg_launch_nb<T, 32, 1>(P, rs, cs, M, R, C, tau, Tm, info, st);
+    } else {
+        if (nb == 16 && rp == 1) return panel_reg_launch_nb<T, 16, 1>(P, rs, cs, M, R, C, tau, Tm, info, st);
+    }
+    return cudaErrorNotSupported;
+}
+
 template <typename T>
 cudaError_t panel_factor(T *P, long rs, long cs, int M, int nb, T *tau, T *Tm, const PanelCtl &ctl,
                          cudaStream_t st) {
@@ -570,6 +832,11 @@ cudaError_t panel_factor(T *P, long rs, long cs, int M, int nb, T *tau, T *Tm, c
         int R = 0;
         size_t dyn = 0;
         const int C = cluster_plan<T>(M, nb, R, dyn);
+        if (C > 0) {
+            cudaError_t e = panel_reg_launch<T>(P, rs, cs, M, nb, R, C, tau, Tm, ctl.info, st);
+            if (e == cudaSuccess) return e;
+            cudaGetLastError();  // not available for this shape: shared-memory variant
+        }
         if (C > 0) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(C);

@@ -1,8 +1,8 @@
 """Alternative execution paths that environment switches select (read once per
 process, so each runs in a subprocess): the SIMT QR projection instead of the
 tensor-core one, the look-ahead stage-1 driver, the fused FP32 update pass
-(QR update below the row block + LQ projection), the one-sweep-per-block bulge chase, the grid-wide panel and
-other sweep-group sizes.  Each must give the same
+(QR update below the row block + LQ projection), the one-sweep-per-block bulge chase, the grid-wide panel, the
+shared-memory cluster panel and other sweep-group sizes.  Each must give the same
 singular values as the FP64 oracle within the parity tolerance."""
 import json
 import os
@@ -41,6 +41,7 @@ VARIANTS = {
     "chase_one_sweep_per_block": {"NLA_CHASE_GROUP": "0"},
     "chase_group_4": {"NLA_CHASE_GROUP": "4"},
     "grid_panel": {"NLA_PANEL_CLUSTER": "0"},
+    "shared_memory_cluster_panel": {"NLA_PANEL_REG": "0"},
     "fused_fp32_update": {"NLA_FUSED": "1"},
 }
 
