@@ -91,4 +91,32 @@ NLA_DEV double warp_max(double v) {
 NLA_DEV double ld_cg(const double *p) { return __ldcg(p); }
 NLA_DEV float ld_cg(const float *p) { return __ldcg(p); }
 
+// Programmatic dependent launch.  A kernel launched with launch_pdl may start while
+// its predecessor in the stream is still running; pdl_wait() returns once the
+// predecessor has completed and its memory operations are visible, so it comes
+// before the kernel's first global-memory access.  pdl_trigger() lets the next
+// kernel start launching (it will wait in its own pdl_wait()).  Both are no-ops
+// for a kernel launched without the attribute.
+NLA_DEV void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+NLA_DEV void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// NLA_PDL=1 adds the attribute (default: plain stream order).
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                       Args &&...args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 }  // namespace nla

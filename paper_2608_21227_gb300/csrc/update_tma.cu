@@ -129,6 +129,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int M, int N,
                const float *__restrict__ Tm, int BR, int RW, int S, int Ms, float *part, float *fin,
                unsigned int *tickets, int *info) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int RG = NB / 16;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], done[kMaxStages];
@@ -297,6 +299,8 @@ __global__ void __launch_bounds__(32 * kTcWarps, 1)
 qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int M, int N,
                   const float *__restrict__ Tm, int S, int Ms, float *part, float *fin, unsigned int *tickets,
                   int *info) {
+    pdl_wait();
+    pdl_trigger();
     constexpr uint32_t kCols = NB < 32 ? 32 : NB;  // TMEM columns (power of two >= 32)
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], conv[kMaxStages], empty[kMaxStages], accdone;
@@ -468,6 +472,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1)
 lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int M, int N,
                const float *__restrict__ Tm, int tcols, int NC, int S, int Ns, float *part, float *fin,
                unsigned int *tickets, int *info) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int RL = 64 / NB, H = 32 * RL;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], done[kMaxStages];
@@ -618,6 +624,8 @@ template <int NB, int SIDE>
 __global__ void __launch_bounds__(kMaxThreads, 1)
 strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int M, int N,
                     const float *__restrict__ Pv, long ldp, int tcols, int NC, int S, int Ns, int moff, int *info) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int RL = 64 / NB, H = 32 * RL;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], done[kMaxStages];
@@ -775,6 +783,8 @@ qr_update_lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_c
                          const __grid_constant__ CUtensorMap tmU, int M, int N, const float *__restrict__ Pv, long ldp,
                          int moff, const float *__restrict__ Tm, int tcols, int NC, int S, int Ns, float *part,
                          float *fin_out, unsigned int *tickets, int *info) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int RL = 64 / NB, H = 32 * RL;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], done[kMaxStages];
@@ -1029,9 +1039,8 @@ cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long 
         const int Ms = ((M + nsplit - 1) / nsplit + kBoxRows - 1) / kBoxRows * kBoxRows;
         nsplit = (M + Ms - 1) / Ms;
         const size_t smem = (size_t)S * stage + 1024;
-        qr_proj_tc_kernel<NB><<<dim3(nstrip, nsplit), 32 * kTcWarps, smem, st>>>(mX, mVs, M, N, Tm, S, Ms, part, fin,
-                                                                              sc.tickets, sc.info);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(qr_proj_tc_kernel<NB>, dim3(nstrip, nsplit), dim3(32 * kTcWarps), smem, st, mX, mVs,
+                                   M, N, Tm, S, Ms, part, fin, sc.tickets, sc.info);
         if (e != cudaSuccess) return e;
     } else {
         static bool attr = false;
@@ -1043,9 +1052,8 @@ cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long 
         const int Ms = ((M + nsplit - 1) / nsplit + th - 1) / th * th;
         nsplit = (M + Ms - 1) / Ms;
         const size_t smem = (size_t)sh.stages * stage + 1024;
-        qr_proj_kernel<NB><<<dim3(nstrip, nsplit), 32 * (sh.nc + 1), smem, st>>>(
-            mX, mV, M, N, Tm, sh.br, sh.rw, sh.stages, Ms, part, fin, sc.tickets, sc.info);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(qr_proj_kernel<NB>, dim3(nstrip, nsplit), dim3(32 * (sh.nc + 1)), smem, st, mX, mV,
+                                   M, N, Tm, sh.br, sh.rw, sh.stages, Ms, part, fin, sc.tickets, sc.info);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -1073,9 +1081,8 @@ cudaError_t left_apply_nb(float *X, long ldx, int M, int N, const float *V, long
     const int Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
     ncs = (N + Ns - 1) / Ns;
     const size_t smem = (size_t)sh.stages * stage + 1024;
-    strip_update_kernel<NB, 0><<<dim3(nstrip, ncs), 32 * (sh.nc + 1), smem, st>>>(mX2, mQ, len, N, Vo, ldv, sh.tc,
-                                                                                sh.nc, sh.stages, Ns, off, sc.info);
-    return cudaGetLastError();
+    return launch_pdl(strip_update_kernel<NB, 0>, dim3(nstrip, ncs), dim3(32 * (sh.nc + 1)), smem, st, mX2, mQ, len, N,
+                      Vo, ldv, sh.tc, sh.nc, sh.stages, Ns, off, sc.info);
 }
 
 template <int NB>
@@ -1097,9 +1104,8 @@ cudaError_t right_proj_nb(float *X, long ldx, int M, int N, const float *Vt, lon
     int nsplit = splits_for(nstrip, (N + sh.tc - 1) / sh.tc, sh.waves);
     const int Ns = ((N + nsplit - 1) / nsplit + sh.tc - 1) / sh.tc * sh.tc;
     nsplit = (N + Ns - 1) / Ns;
-    lq_proj_kernel<NB><<<dim3(nstrip, nsplit), 32 * (sh.nc + 1), smem, st>>>(mX, mQ, M, N, Tm, sh.tc, sh.nc, sh.stages,
-                                                                             Ns, part, fin, sc.tickets, sc.info);
-    return cudaGetLastError();
+    return launch_pdl(lq_proj_kernel<NB>, dim3(nstrip, nsplit), dim3(32 * (sh.nc + 1)), smem, st, mX, mQ, M, N, Tm,
+                      sh.tc, sh.nc, sh.stages, Ns, part, fin, sc.tickets, sc.info);
 }
 
 // pass 2 on columns [off, off + len) of the M x N trailing block: X -= Y' V^T
@@ -1124,9 +1130,8 @@ cudaError_t right_apply_nb(float *X, long ldx, int M, int N, const float *Vt, lo
     int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (len + sh.tc - 1) / sh.tc));
     const int Ns = ((len + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
     ncs = (len + Ns - 1) / Ns;
-    strip_update_kernel<NB, 1><<<dim3(nstrip, ncs), 32 * (sh.nc + 1), smem, st>>>(mX, mQ, M, len, fin, 0, sh.tc, sh.nc,
-                                                                                sh.stages, Ns, off, sc.info);
-    return cudaGetLastError();
+    return launch_pdl(strip_update_kernel<NB, 1>, dim3(nstrip, ncs), dim3(32 * (sh.nc + 1)), smem, st, mX, mQ, M, len,
+                      fin, 0L, sh.tc, sh.nc, sh.stages, Ns, off, sc.info);
 }
 
 // QR update of the M x N block below the row block + LQ projection (Y' -> fout)
@@ -1156,9 +1161,8 @@ cudaError_t fused_nb(float *X, long ldx, int M, int N, const float *V, long ldv,
     int nsplit = splits_for(nstrip, (N + sh.tc - 1) / sh.tc, sh.waves);
     const int Ns = ((N + nsplit - 1) / nsplit + sh.tc - 1) / sh.tc * sh.tc;
     nsplit = (N + Ns - 1) / Ns;
-    qr_update_lq_proj_kernel<NB><<<dim3(nstrip, nsplit), 32 * (sh.nc + 1), fused_smem<NB>(sh, S), st>>>(
-        mX, mQ, mU, M, N, V, ldv, moff, Tm, sh.tc, sh.nc, S, Ns, part, fout, sc.tickets, sc.info);
-    return cudaGetLastError();
+    return launch_pdl(qr_update_lq_proj_kernel<NB>, dim3(nstrip, nsplit), dim3(32 * (sh.nc + 1)), fused_smem<NB>(sh, S),
+                      st, mX, mQ, mU, M, N, V, ldv, moff, Tm, sh.tc, sh.nc, S, Ns, part, fout, sc.tickets, sc.info);
 }
 
 }  // namespace

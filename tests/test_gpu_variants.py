@@ -2,7 +2,7 @@
 process, so each runs in a subprocess): the SIMT QR projection instead of the
 tensor-core one, the look-ahead stage-1 driver, the fused FP32 update pass
 (QR update below the row block + LQ projection), the one-sweep-per-block bulge chase, the grid-wide panel, the
-shared-memory cluster panel and other sweep-group sizes.  Each must give the same
+shared-memory cluster panel, programmatic dependent launch and other sweep-group sizes.  Each must give the same
 singular values as the FP64 oracle within the parity tolerance."""
 import json
 import os
@@ -42,6 +42,7 @@ VARIANTS = {
     "chase_group_4": {"NLA_CHASE_GROUP": "4"},
     "grid_panel": {"NLA_PANEL_CLUSTER": "0"},
     "shared_memory_cluster_panel": {"NLA_PANEL_REG": "0"},
+    "programmatic_dependent_launch": {"NLA_PDL": "1"},
     "fused_fp32_update": {"NLA_FUSED": "1"},
 }
 
