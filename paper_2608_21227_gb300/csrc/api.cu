@@ -89,6 +89,10 @@ struct Stage1Plan {
     int b;
     nla::UpdCfg left, right;
     int update;  // nla_update
+    // per-step configurations: the tuned table's entry for each step's trailing block
+    // (set when the caller fixed no update parameters and a table is installed)
+    bool adaptive = false;
+    nla_dtype dt = NLA_F64;
 };
 
 struct Stage1Bufs {
@@ -130,10 +134,36 @@ nla_status check_upd(const Stage1Plan &p, int elem) {
     return NLA_OK;
 }
 
+// Auxiliary stream (high priority) and fork/join events for the look-ahead panels,
+// one set per device, created on first use.
+struct Aux {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    std::mutex use;  // held while a call enqueues work on s (events are re-recorded per step)
+};
+Aux *aux_for_device() {
+    static std::mutex mu;
+    static Aux per_dev[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    Aux &a = per_dev[dev];
+    if (!a.s) {
+        int lo = 0, hi = 0;
+        cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (cudaStreamCreateWithPriority(&a.s, cudaStreamNonBlocking, hi) != cudaSuccess) {
+            a.s = nullptr;
+            cudaGetLastError();
+            return nullptr;
+        }
+        for (auto &e : a.ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    }
+    return &a;
+}
+
 // Algorithm 1 on the column-major M x N matrix X (M >= N), band width b.
 nla_status run_stage1_lookahead(float *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
-                                float *tauq_all, float *taup_all, int *dInfo, cudaStream_t st, struct Aux &ax);
-struct Aux *aux_for_device();
+                                float *tauq_all, float *taup_all, int *dInfo, cudaStream_t st, Aux &ax);
 // Off by default: measured no gain at 8192 (the update kernels occupy every SM, so the
 // panel's cluster competes with them instead of filling idle SMs).  NLA_LOOKAHEAD=1 enables it.
 bool lookahead_enabled() {
@@ -158,6 +188,7 @@ bool fused_enabled() {
 
 nla_status run_stage1_fused(float *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
                             float *tauq_all, float *taup_all, int *dInfo, cudaStream_t st);
+void step_cfgs(const Stage1Plan &p, int Mt, int Nt, nla::UpdCfg &l, nla::UpdCfg &r);
 
 template <typename T>
 nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
@@ -185,6 +216,9 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
         NLA_LAUNCH(nla::kTrPanelQR, st, nla::panel_factor<T>(panel, 1, ldx, M - kb, nb, tq, Tq, ctl, st), "QR panel");
         const int c0 = kb + nb;
         if (c0 >= N) break;
+        nla::UpdCfg cfl, cfr, unused;
+        step_cfgs(p, M - kb, N - c0, cfl, unused);
+        step_cfgs(p, M - c0, N - c0, unused, cfr);
         if constexpr (sizeof(T) == 8) {
             if (p.update != NLA_UPD_NATIVE) {
                 NLA_LAUNCH(nla::kTrTrailLeft, st, nla::trail_left_tc(X + kb + (long)c0 * ldx, ldx, M - kb, N - c0, panel, ldx, nb, Tq,
@@ -192,11 +226,11 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
                          "QR trailing update (tensor core)");
             } else {
                 NLA_LAUNCH(nla::kTrTrailLeft, st, nla::trail_left<T>(X + kb + (long)c0 * ldx, ldx, M - kb, N - c0, panel, ldx, nb, Tq,
-                                            p.left, usc, st),
+                                            cfl, usc, st),
                          "QR trailing update");
             }
         } else {
-            NLA_LAUNCH(nla::kTrTrailLeft, st, nla::trail_left<T>(X + kb + (long)c0 * ldx, ldx, M - kb, N - c0, panel, ldx, nb, Tq, p.left,
+            NLA_LAUNCH(nla::kTrTrailLeft, st, nla::trail_left<T>(X + kb + (long)c0 * ldx, ldx, M - kb, N - c0, panel, ldx, nb, Tq, cfl,
                                         usc, st),
                      "QR trailing update");
         }
@@ -212,38 +246,11 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
                     continue;
                 }
             }
-            NLA_LAUNCH(nla::kTrTrailRight, st, nla::trail_right<T>(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.right, usc, st),
+            NLA_LAUNCH(nla::kTrTrailRight, st, nla::trail_right<T>(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, cfr, usc, st),
                      "LQ trailing update");
         }
     }
     return NLA_OK;
-}
-
-// Auxiliary stream (high priority) and fork/join events for the look-ahead panels,
-// one set per device, created on first use.
-struct Aux {
-    cudaStream_t s = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    std::mutex use;  // held while a call enqueues work on s (events are re-recorded per step)
-};
-Aux *aux_for_device() {
-    static std::mutex mu;
-    static Aux per_dev[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lk(mu);
-    Aux &a = per_dev[dev];
-    if (!a.s) {
-        int lo = 0, hi = 0;
-        cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        if (cudaStreamCreateWithPriority(&a.s, cudaStreamNonBlocking, hi) != cudaSuccess) {
-            a.s = nullptr;
-            cudaGetLastError();
-            return nullptr;
-        }
-        for (auto &e : a.ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-    }
-    return &a;
 }
 
 // Algorithm 1 for FP32 with the TMA-streamed update, panels looked ahead: the
@@ -429,8 +436,24 @@ Stage1Plan make_plan(int M, int N, nla_dtype dt, const nla_opts *opts, int band_
         const int es = (int)elem_size(dt);
         p.left = fallback_upd(0, es, p.b, p.left);
         p.right = fallback_upd(1, es, p.b, p.right);
+        nla_cfg probe;
+        p.adaptive = p.update == NLA_UPD_NATIVE && nla_tuned_lookup(M, N, (int)dt, 0, 0, &probe);
+        p.dt = dt;
     }
     return p;
+}
+
+// The update configurations of one stage-1 step whose trailing block is Mt x Nt: the
+// tuned entry nearest to that size (kernel-level parameters only; the band stays the
+// plan's), made valid for the band.
+void step_cfgs(const Stage1Plan &p, int Mt, int Nt, nla::UpdCfg &l, nla::UpdCfg &r) {
+    l = p.left;
+    r = p.right;
+    if (!p.adaptive) return;
+    const int es = (int)elem_size(p.dt);
+    nla_cfg t;
+    if (nla_tuned_lookup(Mt, Nt, (int)p.dt, 0, 0, &t)) l = fallback_upd(0, es, p.b, {t.tile, t.threads, t.cols_per_block, t.unroll});
+    if (nla_tuned_lookup(Mt, Nt, (int)p.dt, 0, 1, &t)) r = fallback_upd(1, es, p.b, {t.tile, t.threads, t.cols_per_block, t.unroll});
 }
 
 nla_status check_common(nla_dtype dt, const nla_opts *opts) {
