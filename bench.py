@@ -170,7 +170,7 @@ def fused_update_bytes_per_step(M, N, b, elem=4):
 # trailing update: projection + update in one region, or -- fused schedule -- one kernel
 # per region; chase: sweeps + bidiagonal extraction; bisection: preparation + multisection)
 KERNELS_PER_REGION = {"panel_qr": 1, "panel_lq": 1, "trail_left": 2, "trail_right": 2, "trail_fused": 1,
-                      "stage_copy": 1, "band_extract": 1, "band2bd": 2, "bisect": 2, "batched": 2}
+                      "stage_copy": 1, "band_extract": 1, "band2bd": 2, "bisect": 2, "batched": 3}
 
 
 def run_reference(args, rank):

@@ -57,10 +57,19 @@ nla_status berr(nla_status s, const char *m) {
 }
 
 // ---------------------------------------------------------------- prep
+// counter[0]: next position of the main kernel, counter[1]: next position of the
+// large-matrix kernel, counter[2]: number of matrices above the shared-memory size
+// (the sorted order's first counter[2] entries; the main kernel starts after them).
 __global__ void batched_prep_kernel(int batch, const int *dM, const int *dN, int *order, unsigned int *counter) {
     extern __shared__ unsigned long long keys[];
+    __shared__ unsigned int sh_large;
     const int tid = threadIdx.x, nt = blockDim.x;
-    if (tid == 0) *counter = 0u;
+    if (tid == 0) {
+        counter[0] = 0u;
+        counter[1] = 0u;
+        counter[2] = 0u;
+        sh_large = 0u;
+    }
     if (batch > kSortMax) {
         for (int i = tid; i < batch; i += nt) order[i] = i;
         return;
@@ -92,7 +101,17 @@ __global__ void batched_prep_kernel(int batch, const int *dM, const int *dN, int
             }
             __syncthreads();
         }
-    for (int i = tid; i < batch; i += nt) order[i] = (int)(keys[i] & 0xFFFFFFFFull);
+    unsigned int large = 0;
+    for (int i = tid; i < batch; i += nt) {
+        order[i] = (int)(keys[i] & 0xFFFFFFFFull);
+        large += (0xFFFFFFFFull - (keys[i] >> 32)) > (unsigned long long)kBSmemElems ? 1u : 0u;
+    }
+    atomicAdd(&sh_large, large);
+    __syncthreads();
+    if (tid == 0) {
+        counter[0] = sh_large;
+        counter[2] = sh_large;
+    }
 }
 
 // ---------------------------------------------------------------- group primitives
@@ -289,6 +308,47 @@ batched_svd_kernel(int batch, const int *__restrict__ dM, const int *__restrict_
     }
 }
 
+// blocks per SM of the large-matrix kernel (global scratch slots: one per block)
+constexpr int kLargePerSm = 4;
+
+// The matrices too large for shared memory (the sorted order's first counter[2]):
+// one per block of 256 threads, working in the block's global scratch slot (L2),
+// with several blocks per SM (no matrix shared memory) so that more of these
+// latency-bound reductions run at once.
+__global__ void __launch_bounds__(kBThreads, kLargePerSm)
+batched_large_kernel(const int *__restrict__ dM, const int *__restrict__ dN, const int *__restrict__ dLda,
+                     float *const *dA, float *const *dS, const int *__restrict__ order, unsigned int *counter,
+                     float *scratch, size_t scratch_elems, int *dInfo) {
+    __shared__ float aux[800];
+    __shared__ int sh_item;
+    const int tid = threadIdx.x;
+    const int nlarge = (int)counter[2];
+    while (true) {
+        if (tid == 0) sh_item = (int)atomicAdd(&counter[1], 1u);
+        __syncthreads();
+        const int item = sh_item;
+        if (item >= nlarge) break;
+        const int i = order[item];
+        const int m = dM[i], n = dN[i], lda = dLda[i];
+        const float *A = dA[i];
+        const int M = max(m, n), N = min(m, n);
+        const bool tr = m < n;
+        float *W = scratch + (size_t)blockIdx.x * scratch_elems;
+        if ((size_t)M * N <= scratch_elems && N <= 256) {
+            for (int idx = tid; idx < M * N; idx += kBThreads) {
+                const int r = idx % M, c = idx / M;  // W(r, c)
+                W[idx] = tr ? A[c + (size_t)r * lda] : A[r + (size_t)c * lda];
+            }
+            gsync(0, kBThreads);
+            if (N > 0) group_svd(W, M, N, aux, aux + 256, aux + 512, aux + 768, dS[i], 0, kBThreads, tid);
+            if (tid == 0) dInfo[i] = 0;
+        } else if (tid == 0) {
+            dInfo[i] = -NLA_ERR_UNSUPPORTED;
+        }
+        __syncthreads();
+    }
+}
+
 BatchCfg default_cfg() {
     BatchCfg c;
     for (int b = 0; b < kBuckets; ++b) c.group[b] = kMinGroup[b];
@@ -307,7 +367,7 @@ extern "C" {
 nla_status nla_gesvd_vals_batched_workspace(int batch, nla_dtype dtype, int max_m, int max_n, size_t *bytes) {
     if (!bytes || batch < 0 || max_m < 0 || max_n < 0) return berr(NLA_ERR_ARG, "bad arguments");
     if (dtype != NLA_F32) return berr(NLA_ERR_UNSUPPORTED, "the batched kernel supports FP32 only");
-    const size_t blocks = (size_t)nla::device_sm_count() * 2;
+    const size_t blocks = (size_t)nla::device_sm_count() * std::max(2, kLargePerSm);
     const size_t slot = (size_t)std::max(max_m, 1) * std::max(max_n, 1);
     size_t b = 256;                                    // counter
     b += ((size_t)std::max(batch, 1) * 4 + 255) / 256 * 256;  // order
@@ -353,6 +413,10 @@ nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *dM, con
         nla::TraceScope ts(nla::kTrBatched, st);
         batched_prep_kernel<<<1, 1024, batch <= kSortMax ? sort_smem : 0, st>>>(batch, dM, dN, order, counter);
         int blocks = nla::device_sm_count();
+        if (batch <= kSortMax)  // (unsorted batches leave counter[2] = 0: the main kernel takes all)
+            batched_large_kernel<<<blocks * kLargePerSm, kBThreads, 0, st>>>(
+                dM, dN, dLda, (float *const *)dA_array, (float *const *)dS_array, order, counter, scratch, slot,
+                dInfo);
         batched_svd_kernel<<<blocks, kBThreads, main_smem, st>>>(batch, dM, dN, dLda, (float *const *)dA_array,
                                                                  (float *const *)dS_array, order, counter, scratch, slot,
                                                                  dInfo, cfg, batch <= kSortMax ? 1 : 0);
