@@ -39,7 +39,8 @@ constexpr int kSortMax = 16384;             // batches up to this size are sorte
 constexpr int kBuckets = 5;
 // Buckets by element count m*n: <= 1/8, 1/4, 1/2, 1 of the block's matrix shared memory, or more
 // (global scratch).  A bucket-b matrix fits one group's share when g >= kMinGroup[b].
-const int kMinGroup[kBuckets] = {32, 64, 128, 256, 256};
+// (the largest bucket runs in the large-matrix kernel, which takes 128 or 256)
+const int kMinGroup[kBuckets] = {32, 64, 128, 256, 128};
 
 struct BatchCfg {
     int group[kBuckets];  // threads per matrix for each bucket
@@ -269,7 +270,8 @@ batched_svd_kernel(int batch, const int *__restrict__ dM, const int *__restrict_
             if (sorted && pos < (unsigned)batch) {
                 const int i0 = order[pos];
                 const long el = (long)dM[i0] * dN[i0];
-                gsz = cfg.group[bucket_of(el)];
+                const int bk = bucket_of(el);
+                gsz = bk == kBuckets - 1 ? kBThreads : cfg.group[bk];  // global scratch: one matrix per block
             }
             const int ng = kBThreads / gsz;
             sh_groups = ng;
@@ -308,14 +310,17 @@ batched_svd_kernel(int batch, const int *__restrict__ dM, const int *__restrict_
     }
 }
 
-// blocks per SM of the large-matrix kernel (global scratch slots: one per block)
-constexpr int kLargePerSm = 4;
+// threads per block of the large-matrix kernel: 1024 per SM in blocks of G
+// (global scratch slots: one per block)
+constexpr int kLargeThreadsPerSm = 1024;
+constexpr int kLargeSlotsPerSm = kLargeThreadsPerSm / 128;
 
 // The matrices too large for shared memory (the sorted order's first counter[2]):
 // one per block of 256 threads, working in the block's global scratch slot (L2),
 // with several blocks per SM (no matrix shared memory) so that more of these
 // latency-bound reductions run at once.
-__global__ void __launch_bounds__(kBThreads, kLargePerSm)
+template <int G>
+__global__ void __launch_bounds__(G, kLargeThreadsPerSm / G)
 batched_large_kernel(const int *__restrict__ dM, const int *__restrict__ dN, const int *__restrict__ dLda,
                      float *const *dA, float *const *dS, const int *__restrict__ order, unsigned int *counter,
                      float *scratch, size_t scratch_elems, int *dInfo) {
@@ -335,12 +340,12 @@ batched_large_kernel(const int *__restrict__ dM, const int *__restrict__ dN, con
         const bool tr = m < n;
         float *W = scratch + (size_t)blockIdx.x * scratch_elems;
         if ((size_t)M * N <= scratch_elems && N <= 256) {
-            for (int idx = tid; idx < M * N; idx += kBThreads) {
+            for (int idx = tid; idx < M * N; idx += G) {
                 const int r = idx % M, c = idx / M;  // W(r, c)
                 W[idx] = tr ? A[c + (size_t)r * lda] : A[r + (size_t)c * lda];
             }
-            gsync(0, kBThreads);
-            if (N > 0) group_svd(W, M, N, aux, aux + 256, aux + 512, aux + 768, dS[i], 0, kBThreads, tid);
+            gsync(0, G);
+            if (N > 0) group_svd(W, M, N, aux, aux + 256, aux + 512, aux + 768, dS[i], 0, G, tid);
             if (tid == 0) dInfo[i] = 0;
         } else if (tid == 0) {
             dInfo[i] = -NLA_ERR_UNSUPPORTED;
@@ -352,6 +357,7 @@ batched_large_kernel(const int *__restrict__ dM, const int *__restrict__ dN, con
 BatchCfg default_cfg() {
     BatchCfg c;
     for (int b = 0; b < kBuckets; ++b) c.group[b] = kMinGroup[b];
+    c.group[kBuckets - 1] = kBThreads;
     return c;
 }
 
@@ -367,7 +373,7 @@ extern "C" {
 nla_status nla_gesvd_vals_batched_workspace(int batch, nla_dtype dtype, int max_m, int max_n, size_t *bytes) {
     if (!bytes || batch < 0 || max_m < 0 || max_n < 0) return berr(NLA_ERR_ARG, "bad arguments");
     if (dtype != NLA_F32) return berr(NLA_ERR_UNSUPPORTED, "the batched kernel supports FP32 only");
-    const size_t blocks = (size_t)nla::device_sm_count() * std::max(2, kLargePerSm);
+    const size_t blocks = (size_t)nla::device_sm_count() * std::max(2, kLargeSlotsPerSm);
     const size_t slot = (size_t)std::max(max_m, 1) * std::max(max_n, 1);
     size_t b = 256;                                    // counter
     b += ((size_t)std::max(batch, 1) * 4 + 255) / 256 * 256;  // order
@@ -413,10 +419,17 @@ nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *dM, con
         nla::TraceScope ts(nla::kTrBatched, st);
         batched_prep_kernel<<<1, 1024, batch <= kSortMax ? sort_smem : 0, st>>>(batch, dM, dN, order, counter);
         int blocks = nla::device_sm_count();
-        if (batch <= kSortMax)  // (unsorted batches leave counter[2] = 0: the main kernel takes all)
-            batched_large_kernel<<<blocks * kLargePerSm, kBThreads, 0, st>>>(
-                dM, dN, dLda, (float *const *)dA_array, (float *const *)dS_array, order, counter, scratch, slot,
-                dInfo);
+        if (batch <= kSortMax) {  // (unsorted batches leave counter[2] = 0: the main kernel takes all)
+            // threads per large matrix: the tuned group of the largest bucket (128 or 256)
+            if (cfg.group[kBuckets - 1] == 128)
+                batched_large_kernel<128><<<blocks * (kLargeThreadsPerSm / 128), 128, 0, st>>>(
+                    dM, dN, dLda, (float *const *)dA_array, (float *const *)dS_array, order, counter, scratch, slot,
+                    dInfo);
+            else
+                batched_large_kernel<256><<<blocks * (kLargeThreadsPerSm / 256), 256, 0, st>>>(
+                    dM, dN, dLda, (float *const *)dA_array, (float *const *)dS_array, order, counter, scratch, slot,
+                    dInfo);
+        }
         batched_svd_kernel<<<blocks, kBThreads, main_smem, st>>>(batch, dM, dN, dLda, (float *const *)dA_array,
                                                                  (float *const *)dS_array, order, counter, scratch, slot,
                                                                  dInfo, cfg, batch <= kSortMax ? 1 : 0);

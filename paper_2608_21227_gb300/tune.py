@@ -85,7 +85,7 @@ def batched(args):
     # bucket b holds matrices with m*n in ((48K >> (4 - b)), 48K >> (3 - b)]; representative batches
     elems = 48 * 1024
     bounds = [0, elems // 8, elems // 4, elems // 2, elems, 1 << 30]
-    min_group = [32, 64, 128, 256, 256]
+    min_group = [32, 64, 128, 256, 128]  # the largest bucket: threads per matrix of the large-matrix kernel
     ms, ns = inputs.batch_shapes(20000, seed=args.seed)
     out = []
     for b in range(5):
