@@ -849,7 +849,13 @@ cudaError_t panel_factor(T *P, long rs, long cs, int M, int nb, T *tau, T *Tm, c
         size_t dyn = 0;
         const int C = cluster_plan<T>(M, nb, R, dyn);
         if (C > 0) {
-            cudaError_t e = panel_reg_launch<T>(P, rs, cs, M, nb, R, C, tau, Tm, ctl.info, st);
+            // rows in registers: one row per thread, so the smallest cluster with at
+            // most 512 rows per block (fewer blocks, fewer exchanges per column)
+            int Cr = 1;
+            while (Cr < 16 && (long)Cr * kClusterThreads < M) Cr *= 2;
+            const int Rr = (M + Cr - 1) / Cr;
+            cudaError_t e = Rr <= kClusterThreads ? panel_reg_launch<T>(P, rs, cs, M, nb, Rr, Cr, tau, Tm, ctl.info, st)
+                                                  : cudaErrorNotSupported;
             if (e == cudaSuccess) return e;
             cudaGetLastError();  // not available for this shape: shared-memory variant
         }
