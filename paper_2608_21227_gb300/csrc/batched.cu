@@ -3,11 +3,17 @@
 //
 //  1. prep kernel (one block): orders the batch by element count, largest first
 //     (bitonic sort of (count, index) keys in shared memory), so that blocks
-//     draw similar matrices together and the long ones start first; clears the
-//     work counter.  Everything stays on the device, so the whole call can be
-//     captured into a CUDA graph.
-//  2. persistent kernel (a grid of #SMs x 2 blocks of 256 threads): each block
-//     takes rounds of work from an atomic counter.  In a round it splits into
+//     draw similar matrices together and the long ones start first; counts the
+//     matrices too large for shared memory and sets the work counters.
+//     Everything stays on the device, so the whole call can be captured into a
+//     CUDA graph.
+//  2. large-matrix kernel (4 blocks of 256 threads per SM, no matrix shared
+//     memory): one of those large matrices per block, in the block's global
+//     scratch slot (L2-resident); with several blocks per SM more of these
+//     latency-bound reductions are in flight.
+//  3. persistent kernel (one block of 256 threads per SM, 192 KiB of shared
+//     memory for matrices): each block takes rounds of the remaining work from
+//     an atomic counter.  In a round it splits into
 //     groups of g threads -- g chosen per size bucket (kt_load_config installs
 //     tuned values; defaults otherwise) -- and each group reduces one matrix:
 //       * the matrix (or its transpose, so that m >= n) is copied into the
