@@ -28,6 +28,7 @@
 //         the FP64 pipe is 64x slower on this GPU).
 //     Groups synchronise with named barriers (bar.sync id, g).
 #include <algorithm>
+#include <cstdlib>
 #include <cfloat>
 #include <vector>
 
@@ -426,13 +427,18 @@ nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *dM, con
         batched_prep_kernel<<<1, 1024, batch <= kSortMax ? sort_smem : 0, st>>>(batch, dM, dN, order, counter);
         int blocks = nla::device_sm_count();
         if (batch <= kSortMax) {  // (unsorted batches leave counter[2] = 0: the main kernel takes all)
+            static const int per_sm_threads = [] {  // NLA_BATCH_LARGE_THREADS: threads per SM of the kernel
+                const char *v = getenv("NLA_BATCH_LARGE_THREADS");
+                const int t = v ? atoi(v) : kLargeThreadsPerSm;
+                return std::max(256, std::min(t, kLargeThreadsPerSm));
+            }();
             // threads per large matrix: the tuned group of the largest bucket (128 or 256)
             if (cfg.group[kBuckets - 1] == 128)
-                batched_large_kernel<128><<<blocks * (kLargeThreadsPerSm / 128), 128, 0, st>>>(
+                batched_large_kernel<128><<<blocks * (per_sm_threads / 128), 128, 0, st>>>(
                     dM, dN, dLda, (float *const *)dA_array, (float *const *)dS_array, order, counter, scratch, slot,
                     dInfo);
             else
-                batched_large_kernel<256><<<blocks * (kLargeThreadsPerSm / 256), 256, 0, st>>>(
+                batched_large_kernel<256><<<blocks * (per_sm_threads / 256), 256, 0, st>>>(
                     dM, dN, dLda, (float *const *)dA_array, (float *const *)dS_array, order, counter, scratch, slot,
                     dInfo);
         }

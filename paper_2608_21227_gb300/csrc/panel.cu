@@ -495,11 +495,20 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
     if (p == 0) {
         // T(0:k, k) = -tau_k T(0:k, 0:k) G(0:k, k), T(k, k) = tau_k -- one warp, column by column
         if (warp == 0) {
+            // lane i (and i + 32) forms T(i, kk) = -tau_kk sum_{i <= q < kk} T(i, q) G(q, kk); the
+            // q loop is unrolled in blocks of 16 with the range as a predicate
             for (int kk = 0; kk < kmax; ++kk) {
                 const T tk = taus[kk];
                 for (int i = lane; i < kk; i += 32) {
                     T t = T(0);
-                    for (int q = i; q < kk; ++q) t += Tsh[i + q * nb] * Tsh[kk + q * nb];  // T(i, q) G(q, kk)
+                    for (int q0 = i & ~15; q0 < kk; q0 += 16) {
+#pragma unroll
+                        for (int u = 0; u < 16; ++u) {
+                            const int q = q0 + u;
+                            const T tv = q < nb ? Tsh[i + q * nb] : T(0), gv = q < nb ? Tsh[kk + q * nb] : T(0);
+                            t = (q >= i && q < kk) ? fma(tv, gv, t) : t;  // T(i, q) G(q, kk)
+                        }
+                    }
                     Tsh[i + kk * nb] = -tk * t;
                 }
                 if (lane == 0) Tsh[kk + kk * nb] = tk;
@@ -543,6 +552,24 @@ NLA_DEV T warp_reduce_scatter(T (&v)[NB], int lane) {
     return v[0];
 }
 
+// Asynchronous store into another block's shared memory that completes as bytes on
+// that block's mbarrier (release at cluster scope); addresses from cluster_addr.
+NLA_DEV void st_async_remote(uint32_t addr, float v, uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f32 [%0], %1, [%2];" ::"r"(addr), "f"(v),
+                 "r"(mbar)
+                 : "memory");
+}
+NLA_DEV void st_async_remote(uint32_t addr, double v, uint32_t mbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.f64 [%0], %1, [%2];" ::"r"(addr), "d"(v),
+                 "r"(mbar)
+                 : "memory");
+}
+// This block's arrival on its own barrier, announcing the bytes the phase waits for.
+NLA_DEV void mbar_arrive_expect_tx(uint64_t *mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(mbar)), "r"(bytes)
+                 : "memory");
+}
+
 template <typename T, int NB>
 NLA_DEV T select_col(const T (&a)[NB], int j) {
     T x = T(0);
@@ -577,8 +604,10 @@ panel_reg_kernel(T *__restrict__ P, long rs, long cs, int M, int R, T *__restric
     const int nr = max(0, min(M, r0 + R) - r0);
     const int kmax = min(NB, M);
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], nP);
-        tc::mbar_init(&mbar[1], nP);
+        // one arrival per phase (this block's expect_tx); the other blocks' partial sums
+        // and the owner's row j complete it as transaction bytes
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         sh_abort = 0;
     }
@@ -622,18 +651,18 @@ panel_reg_kernel(T *__restrict__ P, long rs, long cs, int M, int R, T *__restric
         __syncthreads();
         if (warp == 0) {
             const bool owner = j >= r0 && j < r0 + nr;
+            if (lane == 0) mbar_arrive_expect_tx(&mbar[buf], (uint32_t)((nP + 1) * NB * sizeof(T)));
+            // lane l pushes column c = l mod NB to blocks l / NB, l / NB + 32 / NB, ...
+            const int c = lane % NB;
             T sblk = T(0);
-            if (lane < NB) {
 #pragma unroll 4
-                for (int w = 0; w < kWarps; ++w) sblk += red[w][lane];
-                const T rv = owner ? myrow[lane] : T(0);
-                for (int q = 0; q < nP; ++q) {
-                    cluster.map_shared_rank(&inbox[buf][p][0], q)[lane] = sblk;
-                    if (owner) cluster.map_shared_rank(&rowin[buf][0], q)[lane] = rv;
-                }
+            for (int w = 0; w < kWarps; ++w) sblk += red[w][c];
+            const T rv = owner ? myrow[c] : T(0);
+            for (int q = lane / NB; q < nP; q += 32 / NB) {
+                const uint32_t mb = cluster_addr(&mbar[buf], q);
+                st_async_remote(cluster_addr(&inbox[buf][p][c], q), sblk, mb);
+                if (owner) st_async_remote(cluster_addr(&rowin[buf][c], q), rv, mb);
             }
-            __syncwarp();  // the warp's pushes precede the arrivals below
-            if (lane < nP) mbar_arrive_remote(cluster_addr(&mbar[buf], lane));
             if (lane == 0 && !sh_abort) {
                 const uint32_t par = (uint32_t)((j >> 1) & 1);
                 if (!mbar_try_wait_cluster(&mbar[buf], par)) {
@@ -713,12 +742,18 @@ panel_reg_kernel(T *__restrict__ P, long rs, long cs, int M, int R, T *__restric
         __syncthreads();
         // T(0:k, k) = -tau_k T(0:k, 0:k) G(0:k, k), T(k, k) = tau_k -- one warp, column by column
         if (warp == 0) {
+            // lane i forms T(i, kk) = -tau_kk sum_{i <= q < kk} T(i, q) G(q, kk); the q loop is
+            // unrolled over the whole width with the range as a predicate, so its loads issue at once
             for (int kk = 0; kk < kmax; ++kk) {
                 const T tk = taus[kk];
-                for (int i = lane; i < kk; i += 32) {
+                if (lane < kk) {
                     T t = T(0);
-                    for (int q = i; q < kk; ++q) t += Tsh[i + q * NB] * Tsh[kk + q * NB];  // T(i, q) G(q, kk)
-                    Tsh[i + kk * NB] = -tk * t;
+#pragma unroll
+                    for (int q = 0; q < NB; ++q) {
+                        const T tv = Tsh[lane + q * NB], gv = Tsh[kk + q * NB];  // T(i, q), G(q, kk)
+                        t = (q >= lane && q < kk) ? fma(tv, gv, t) : t;
+                    }
+                    Tsh[lane + kk * NB] = -tk * t;
                 }
                 if (lane == 0) Tsh[kk + kk * NB] = tk;
                 __syncwarp();

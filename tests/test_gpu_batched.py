@@ -94,3 +94,25 @@ def test_graph_capture_replay(nla):
             assert np.all(np.isfinite(sv))
             assert err_rel(sv, a.cpu().numpy().astype(np.float64)) <= 5e-6 * max(A.shape)
     check(b.S, b.info, mats[:40])
+
+
+def test_unsorted_batch_over_the_sort_limit(nla):
+    # above 16,384 matrices the batch is not sorted: the persistent kernel then also takes
+    # the matrices too large for shared memory (global scratch); every 1000th is one
+    g = np.random.default_rng(11)
+    count = 16400
+    mats = []
+    for i in range(count):
+        if i % 1000 == 500:
+            mats.append(g.standard_normal((300, 200)).astype(np.float32))  # 60,000 elements
+        else:
+            n = int(g.integers(2, 9))
+            mats.append(g.standard_normal((n + int(g.integers(0, 5)), n)).astype(np.float32))
+    b = make_batch(nla, mats)
+    S, info = nla.gesvd_vals_batched(b)
+    torch.cuda.synchronize()
+    assert np.all(info.cpu().numpy() == 0)
+    check_ids = [i for i in range(count) if i % 1000 == 500] + list(range(0, count, 997))
+    for i in check_ids:
+        ref = oracle.svdvals(mats[i].astype(np.float64))
+        assert err_rel(S[i].cpu().numpy(), ref) <= 5e-6 * max(mats[i].shape), (i, mats[i].shape)
