@@ -587,6 +587,9 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
             // ---------------- chase warps
             T *v = vbase + warp * 64;
             int wslot = 0;  // window slot of this warp's current c0 (advanced by b per step)
+            // the loaded-up-to column this warp last observed (and fenced after): columns up
+            // to it are in the window and stay there while any sweep of the group needs them
+            int seen = -1;
             for (int tau = 0;; ++tau) {
                 int lo, hi;
                 bool active;
@@ -595,10 +598,17 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                 const int s = s0 + warp, k = tau - kLag * warp;
                 const bool mine = warp < g && k >= 0 && s + k * b + 1 <= n - 1;  // this warp steps now
                 bool ok = true;
-                if (mine) {  // wait for the last column of this warp's own footprint
-                    if (lane == 0) ok = wait_loaded(vhi, min(s + (k + 2) * b, n - 1), vabort, info);
+                const int need = min(s + (k + 2) * b, n - 1);  // last column of this warp's footprint
+                if (mine && need > seen) {  // not yet observed loaded: wait for it
+                    int hv = 0;
+                    if (lane == 0) {
+                        ok = wait_loaded(vhi, need, vabort, info);
+                        hv = *vhi;
+                    }
                     ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+                    hv = __shfl_sync(0xffffffffu, hv, 0);
                     __threadfence_block();
+                    if (ok) seen = hv;
                 }
                 if (ok && mine) {
                     {
