@@ -413,9 +413,10 @@ panel_cluster_kernel(T *__restrict__ P, long rs, long cs, int M, int nb, int R, 
             __syncwarp();  // lane 0's acquire orders the warp's reads below
             const int i0 = lane, i1 = lane + 32;  // nb <= kNbMax = 64
             T s0 = T(0), s1 = T(0), w0 = T(0), w1 = T(0);
-            for (int q = 0; q < nP; ++q) {
-                if (i0 < nb) s0 += inbox[buf][q][i0];
-                if (i1 < nb) s1 += inbox[buf][q][i1];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {  // (the cluster size as a predicate: the loads issue together)
+                if (q < nP && i0 < nb) s0 += inbox[buf][q][i0];
+                if (q < nP && i1 < nb) s1 += inbox[buf][q][i1];
             }
             if (i0 < nb) w0 = rowin[buf][i0];
             if (i1 < nb) w1 = rowin[buf][i1];
@@ -655,7 +656,7 @@ panel_reg_kernel(T *__restrict__ P, long rs, long cs, int M, int R, T *__restric
             // lane l pushes column c = l mod NB to blocks l / NB, l / NB + 32 / NB, ...
             const int c = lane % NB;
             T sblk = T(0);
-#pragma unroll 4
+#pragma unroll
             for (int w = 0; w < kWarps; ++w) sblk += red[w][c];
             const T rv = owner ? myrow[c] : T(0);
             for (int q = lane / NB; q < nP; q += 32 / NB) {
@@ -679,7 +680,10 @@ panel_reg_kernel(T *__restrict__ P, long rs, long cs, int M, int R, T *__restric
             __syncwarp();  // lane 0's acquire orders the warp's reads below
             T sc_ = T(0), wc_ = T(0);
             if (lane < NB) {
-                for (int q = 0; q < nP; ++q) sc_ += inbox[buf][q][lane];
+                // unrolled over the largest cluster with the size as a predicate: the loads
+                // issue together instead of one load-to-add latency per block
+#pragma unroll
+                for (int q = 0; q < 16; ++q) sc_ += q < nP ? inbox[buf][q][lane] : T(0);
                 wc_ = rowin[buf][lane];
             }
             const T alpha = __shfl_sync(0xffffffffu, wc_, j), xn2 = __shfl_sync(0xffffffffu, sc_, j);
