@@ -350,7 +350,9 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
         const int l = idx % kStrip, k = idx / kStrip;
         float sum = 0.f;
         if (l < lw)
-            for (int qq = 0; qq < S; ++qq) sum += __ldcg(part + ((size_t)qq * nbp + k) * Lext + L0 + l);
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq)  // (S <= 8 splits; all partial loads in flight at once)
+                if (qq < S) sum += __ldcg(part + ((size_t)qq * nbp + k) * Lext + L0 + l);
         Wsh[k * kStrip + l] = sum;
     }
     __syncthreads();

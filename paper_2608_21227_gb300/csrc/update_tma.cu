@@ -265,14 +265,18 @@ qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         const int k = idx >> 7, c = idx & 127;
         float sum = 0.f;
         if (c < wc)
-            for (int q = 0; q < nsplit; ++q) sum += __ldcg(part + ((size_t)q * NB + k) * N + c0 + c);
+#pragma unroll
+            for (int q = 0; q < kMaxSplitTma; ++q)  // (all partial loads in flight at once)
+                if (q < nsplit) sum += __ldcg(part + ((size_t)q * NB + k) * N + c0 + c);
         W[idx] = sum;
     }
     __syncthreads();
     for (int idx = tid; idx < NB * wc; idx += blockDim.x) {
         const int k = idx % NB, c = idx / NB;
         float sum = 0.f;
-        for (int j = 0; j <= k; ++j) sum = fmaf(Tm[j + (size_t)k * NB], W[j * 128 + c], sum);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (j <= k) sum = fmaf(__ldg(Tm + j + (size_t)k * NB), W[j * 128 + c], sum);
         fin[(size_t)(c0 + c) * NB + k] = sum;
     }
     if (tid == 0) tickets[blockIdx.x] = 0u;
@@ -451,14 +455,18 @@ qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
         const int k = idx >> 7, c = idx & 127;
         float sum = 0.f;
         if (c < wc)
-            for (int qq = 0; qq < nsplit; ++qq) sum += __ldcg(part + ((size_t)qq * NB + k) * N + c0 + c);
+#pragma unroll
+            for (int qq = 0; qq < kMaxSplitTma; ++qq)  // (all partial loads in flight at once)
+                if (qq < nsplit) sum += __ldcg(part + ((size_t)qq * NB + k) * N + c0 + c);
         W[idx] = sum;
     }
     __syncthreads();
     for (int idx = tid; idx < NB * wc; idx += blockDim.x) {
         const int k = idx % NB, c = idx / NB;
         float sum = 0.f;
-        for (int j = 0; j <= k; ++j) sum = fmaf(Tm[j + (size_t)k * NB], W[j * 128 + c], sum);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (j <= k) sum = fmaf(__ldg(Tm + j + (size_t)k * NB), W[j * 128 + c], sum);
         fin[(size_t)(c0 + c) * NB + k] = sum;
     }
     if (tid == 0) tickets[blockIdx.x] = 0u;
@@ -601,7 +609,9 @@ lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         const int k = idx / H, i = idx % H;
         float sum = 0.f;
         if (i < hr)
-            for (int q = 0; q < nsplit; ++q) sum += __ldcg(part + ((size_t)q * NB + k) * M + i0 + i);
+#pragma unroll
+            for (int q = 0; q < kMaxSplitTma; ++q)  // (all partial loads in flight at once)
+                if (q < nsplit) sum += __ldcg(part + ((size_t)q * NB + k) * M + i0 + i);
         Y[idx] = sum;
     }
     __syncthreads();
@@ -609,7 +619,9 @@ lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
         const int k = idx / H, i = idx % H;
         if (i >= hr) continue;
         float sum = 0.f;
-        for (int j = 0; j <= k; ++j) sum = fmaf(Y[j * H + i], Tm[j + (size_t)k * NB], sum);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (j <= k) sum = fmaf(Y[j * H + i], __ldg(Tm + j + (size_t)k * NB), sum);
         fin[(size_t)k * M + i0 + i] = sum;
     }
     if (tid == 0) tickets[blockIdx.x] = 0u;
@@ -950,7 +962,9 @@ qr_update_lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_c
         const int k = idx / H, i = idx % H;
         float sum = 0.f;
         if (i < hr)
-            for (int q = 0; q < nsplit; ++q) sum += __ldcg(part + ((size_t)q * NB + k) * M + i0 + i);
+#pragma unroll
+            for (int q = 0; q < kMaxSplitTma; ++q)  // (all partial loads in flight at once)
+                if (q < nsplit) sum += __ldcg(part + ((size_t)q * NB + k) * M + i0 + i);
         Y[idx] = sum;
     }
     __syncthreads();
@@ -958,7 +972,9 @@ qr_update_lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_c
         const int k = idx / H, i = idx % H;
         if (i >= hr) continue;
         float sum = 0.f;
-        for (int j = 0; j <= k; ++j) sum = fmaf(Y[j * H + i], Tm[j + (size_t)k * NB], sum);
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (j <= k) sum = fmaf(Y[j * H + i], __ldg(Tm + j + (size_t)k * NB), sum);
         fin_out[(size_t)k * M + i0 + i] = sum;
     }
     if (tid == 0) tickets[blockIdx.x] = 0u;
