@@ -617,11 +617,32 @@ panel_reg_kernel(T *__restrict__ P, long rs, long cs, int M, int R, T *__restric
         for (int i = tid; i < NB * NB; i += blockDim.x) Tsh[i] = T(0);
     }
     T a[RP][NB];
+    // a row whose NB entries are contiguous and 16-byte aligned (the LQ panel: rs = ldx,
+    // cs = 1) moves as 16-byte vectors
+    const bool vec = cs == 1 && (rs * (long)sizeof(T)) % 16 == 0 && reinterpret_cast<uintptr_t>(P) % 16 == 0;
 #pragma unroll
     for (int q = 0; q < RP; ++q) {
         const int rr = tid + kClusterThreads * q;
+        if (vec && rr < nr) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 *src = reinterpret_cast<const float4 *>(P + (long)(r0 + rr) * rs);
 #pragma unroll
-        for (int c = 0; c < NB; ++c) a[q][c] = rr < nr ? P[(long)(r0 + rr) * rs + (long)c * cs] : T(0);
+                for (int u = 0; u < NB / 4; ++u) {
+                    const float4 f = src[u];
+                    a[q][4 * u] = f.x, a[q][4 * u + 1] = f.y, a[q][4 * u + 2] = f.z, a[q][4 * u + 3] = f.w;
+                }
+            } else {
+                const double2 *src = reinterpret_cast<const double2 *>(P + (long)(r0 + rr) * rs);
+#pragma unroll
+                for (int u = 0; u < NB / 2; ++u) {
+                    const double2 f = src[u];
+                    a[q][2 * u] = f.x, a[q][2 * u + 1] = f.y;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < NB; ++c) a[q][c] = rr < nr ? P[(long)(r0 + rr) * rs + (long)c * cs] : T(0);
+        }
     }
     cluster.sync();  // every block's barriers are initialised before the first remote arrive
     for (int j = 0; j < kmax; ++j) {
@@ -738,8 +759,21 @@ panel_reg_kernel(T *__restrict__ P, long rs, long cs, int M, int R, T *__restric
     for (int q = 0; q < RP; ++q) {
         const int rr = tid + kClusterThreads * q;
         if (rr < nr) {
+            if (vec) {
+                if constexpr (sizeof(T) == 4) {
+                    float4 *dst = reinterpret_cast<float4 *>(P + (long)(r0 + rr) * rs);
 #pragma unroll
-            for (int c = 0; c < NB; ++c) P[(long)(r0 + rr) * rs + (long)c * cs] = a[q][c];
+                    for (int u = 0; u < NB / 4; ++u)
+                        dst[u] = make_float4(a[q][4 * u], a[q][4 * u + 1], a[q][4 * u + 2], a[q][4 * u + 3]);
+                } else {
+                    double2 *dst = reinterpret_cast<double2 *>(P + (long)(r0 + rr) * rs);
+#pragma unroll
+                    for (int u = 0; u < NB / 2; ++u) dst[u] = make_double2(a[q][2 * u], a[q][2 * u + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) P[(long)(r0 + rr) * rs + (long)c * cs] = a[q][c];
+            }
         }
     }
     if (p == 0) {
