@@ -18,6 +18,12 @@
 //   strip_update  X -= P Q^T (QR: P = V, Q = W'^T; LQ: P = Y', Q = V).  A lane
 //                 keeps P(its 64/nb rows, :) in registers and streams columns;
 //                 the producer writes each finished stage back with a TMA store.
+//   qr_proj_tc    W = V^T X on the tensor cores (the default QR projection):
+//                 tcgen05 kind::tf32 MMAs on the TMA boxes, FP32 accuracy from
+//                 the three-term hi/lo split, accumulator in TMEM.
+//   qr_update_lq_proj  (opt-in) the QR update of the rows below the LQ panel's
+//                 row block and, from the updated values, the LQ projection, in
+//                 one pass over X.
 //
 // The projections are split over the long dimension; the last block of each
 // strip (atomic ticket, nobody waits) sums the partials in a fixed order and
