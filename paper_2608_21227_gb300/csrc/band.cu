@@ -677,7 +677,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                     idle = 32;
                 } else {
                     __nanosleep(idle);
-                    idle = min(idle * 2, 512u);
+                    idle = min(idle * 2, 64u);
                 }
             }
         } else {
@@ -727,7 +727,7 @@ __global__ void band2bd_group_kernel(T *AB, long ldab, int n, int b, int G, int 
                     idle = 32;
                 } else {
                     __nanosleep(idle);
-                    idle = min(idle * 2, 512u);
+                    idle = min(idle * 2, 64u);
                 }
             }
             __syncwarp();
