@@ -300,6 +300,7 @@ def main():
     import torch
 
     from paper_2608_21227_gb300 import inputs, nla
+    from paper_2608_21227_gb300.dist import max_over_ranks
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -361,10 +362,7 @@ def main():
     nla.trace_enable(False)
     trace = nla.trace_read()
     ms = e0.elapsed_time(e1) / args.steps
-    t_max = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if pg is not None:
-        pg.all_reduce(t_max, op=pg.ReduceOp.MAX)
-    ms_max = float(t_max.item())
+    ms_max = max_over_ranks(ms, pg, dev)
     value = world * flops(n, n) / (ms_max / 1e3) / 1e9
 
     # ---------------- end-to-end through the C ABI with host buffers
@@ -385,10 +383,7 @@ def main():
     torch.cuda.synchronize(dev)
     barrier()
     e2e_ms = f0.elapsed_time(f1) / e2e_steps
-    t_e2e = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-    if pg is not None:
-        pg.all_reduce(t_e2e, op=pg.ReduceOp.MAX)
-    e2e_value = world * flops(n, n) / (float(t_e2e.item()) / 1e3) / 1e9
+    e2e_value = world * flops(n, n) / (max_over_ranks(e2e_ms, pg, dev) / 1e3) / 1e9
 
     # ---------------- roofline of the dominant kernel (live CUDA-event timing of its launches)
     fused = "trail_fused" in trace
