@@ -103,8 +103,10 @@ nla_status nla_gesvd_vals(int m, int n, nla_dtype dtype, void *dA, int lda, void
                           const nla_opts *opts, nla_stream_t stream);
 
 /* Batched singular values of `batch` independent FP32 matrices of uneven
- * shapes in one persistent launch (the batched form of the method of Section
- * 5.1.1).  dM, dN, dLda: DEVICE int arrays of shapes and leading dimensions;
+ * shapes in one call (the batched form of the method of Section 5.1.1): a sort
+ * kernel, a kernel for the matrices above 48K elements (one per block, several
+ * blocks per SM, global scratch) and a persistent kernel for the rest (shared
+ * memory).  dM, dN, dLda: DEVICE int arrays of shapes and leading dimensions;
  * dA_array / dS_array: DEVICE arrays of device pointers; matrix i is column
  * major m_i x n_i and is read, not modified; dS_array[i] receives
  * min(m_i, n_i) values, descending.  max_m, max_n bound every m_i, n_i
@@ -113,7 +115,9 @@ nla_status nla_gesvd_vals(int m, int n, nla_dtype dtype, void *dA, int lda, void
  * ordered by size on the device and reduced by groups of threads whose size
  * per size bucket comes from the tuned table (kt_load_config) or defaults.
  * Nothing is read from the host at run time, so the call can be captured in
- * a CUDA graph and replayed.  Only NLA_F32 is supported. */
+ * a CUDA graph and replayed.  Only NLA_F32 is supported.  The workspace holds
+ * the sort keys and one max_m x max_n scratch slot per block of the large-
+ * matrix kernel (4 per SM). */
 nla_status nla_gesvd_vals_batched_workspace(int batch, nla_dtype dtype, int max_m, int max_n,
                                             size_t *bytes);
 nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *dM, const int *dN,
