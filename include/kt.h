@@ -5,14 +5,19 @@
  * kernels (Algorithm 2) and the band width of the pipeline (Algorithm 1's
  * only pipeline parameter, Section 5.2), minimising measured runtime:
  *     x* = argmin_{x in X} f(K_x)                       (Eq. 1)
- * over the space X of valid configurations (Section 3.1).  As in the paper
+ * over the space X of valid configurations (Section 3.1; the space's constraints
+ * are the library's launch rule, kt_cfg_valid).  As in the paper
  * (Section 4.1, 4.2): every configuration's input is restored from a pristine
  * copy before each run (deep copy), one untimed warm-up run precedes the
  * timed runs, runtimes come from CUDA events on the launching stream, output
  * is verified against the default configuration's, and a configuration that
  * fails to launch or verify is recorded and skipped.  Kernel parameters are
  * tuned per band width; the band width is chosen at pipeline level
- * (Section 5.2: pipeline vs kernel parameters).
+ * (Section 5.2: pipeline vs kernel parameters): KT_GESVD times the whole SVD per
+ * band, each side with its own best cached kernel configuration (installed as a
+ * temporary table while it runs, so other threads calling nla_gesvd_vals then see
+ * it), and verifies every candidate's singular values against the default
+ * configuration's.
  *
  * Search space (per band width b in {16, 32, 64}):
  *   tile {16, 32, 64, 128} x threads {64, 128, ..., 1024} x
@@ -56,7 +61,10 @@ typedef struct {
     nla_cfg best;          /* x* of Eq. 1 (ties: lexicographically smallest) */
     double best_ms;        /* its median runtime */
     double median_ms;      /* median over all evaluated valid configurations */
-    double default_ms;     /* the default configuration (tile 32, threads 256, cpb 1, unroll 1) */
+    double default_ms;     /* the default configuration (band 32, tile 64, threads 128, cpb 2,
+                              unroll 1): at kernel level its launch at this size (at the tuned
+                              band when problem->band is set, else at band 32); for KT_GESVD
+                              the whole SVD with every field of it explicit */
     int evaluated;         /* configurations timed (or read from the cache) */
     int valid;             /* configurations of the space valid for this problem */
     int failed;            /* configurations that failed to launch or verify */
@@ -71,7 +79,19 @@ nla_status kt_space_get(int index, nla_cfg *out);
  * `seed` (host only; exported so the sample can be checked). */
 nla_status kt_random_subset(int count, int k, unsigned long long seed, int *out);
 
-/* 1 if cfg is a valid launch configuration of the kernel for dtype, else 0. */
+/* 1 if cfg is a valid launch configuration of the kernel for dtype, else 0
+ * (KT_GESVD: valid for both sides).  The rule is the library's launch contract,
+ * not a property of the method: the register-tiled kernels (FP64, and band
+ * widths divisible by 4) need the block to tile the 32*cpb-wide strip into
+ * 4-column groups and the band into groups of 1, 2, 4 or 8 reflectors, a staged
+ * tile of whole 4-row sub-blocks per thread, at most 227 KiB of shared memory
+ * and no more threads than the compiled kernels allow on the current device;
+ * the TMA-streamed FP32 kernels (band 16/32/64) read the fields as (band, stage
+ * depth 32/64/128, consumer threads 64/128/256 in whole 16-reflector groups,
+ * stages 2/4/8, waves 1/2/4) within 226 KiB of shared memory.  Without a CUDA
+ * device only the shape and shared-memory parts are checked.  For a problem
+ * with min(m, n) >= band, nla_gesvd_vals and its workspace query return
+ * NLA_ERR_CONFIG for exactly the configurations this rejects (KT_GESVD). */
 int kt_cfg_valid(kt_kernel kernel, nla_dtype dtype, const nla_cfg *cfg);
 
 /* Tune.  strategy KT_EXHAUSTIVE times every valid point; KT_RANDOM times a

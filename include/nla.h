@@ -89,7 +89,10 @@ typedef struct {
 
 /* ---------------------------------------------------------------- whole SVD */
 
-/* Workspace bytes needed by nla_gesvd_vals for this problem and options. */
+/* Workspace bytes needed by nla_gesvd_vals for this problem and options.
+ * Returns NLA_ERR_CONFIG (and sets no size) when opts->cfg names trailing-update
+ * parameters that are not a valid launch configuration for the band used --
+ * the same check nla_gesvd_vals makes before enqueuing anything. */
 nla_status nla_gesvd_vals_workspace(int m, int n, nla_dtype dtype, const nla_opts *opts,
                                     size_t *bytes);
 
@@ -161,19 +164,19 @@ nla_status nla_band2bd(int n, int band, nla_dtype dtype, void *dAB, int ldab, do
                        const nla_opts *opts, nla_stream_t stream);
 
 /* nla_band2bd without a workspace, for callers that cannot allocate device
- * memory: code issuing work while its stream is captured into a CUDA graph
- * (cudaMalloc cannot be captured), code that must never synchronise the
- * device, and programs whose memory manager owns all device memory.  The paper
- * has no counterpart; this is a library convenience.  Same arguments, layout
- * and results as nla_band2bd, but the sweep-progress scratch is a fixed
- * array inside the library (65536 ints = 256 KiB per GPU that loads the
- * library, held until the process exits), so n may not exceed 65536
- * (NLA_ERR_UNSUPPORTED otherwise).  It allocates nothing: the first call on a
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current -- make that first call before any stream capture.  Every
- * call clears the counters it uses on its stream; all calls share the one
- * array, so calls that could overlap on the GPU (unordered streams) race and
- * must not be issued. */
+ * memory: a plug-in running inside a host framework whose memory manager owns
+ * the whole device and forbids allocations outside it, code that must never
+ * synchronise the device (cudaMalloc and cudaFree may), and programs with a
+ * fixed device-memory budget set at start-up.  The paper has no counterpart;
+ * this is a library convenience.  Same arguments, layout and results as
+ * nla_band2bd, but the sweep-progress scratch is a fixed array inside the
+ * library (65536 ints = 256 KiB per GPU that loads the library, held until the
+ * process exits), so n may not exceed 65536 (NLA_ERR_UNSUPPORTED otherwise).
+ * It allocates nothing: the first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current -- make that first
+ * call before any stream capture.  Every call clears the counters it uses on
+ * its stream; all calls share the one array, so calls that could overlap on
+ * the GPU (unordered streams) race and must not be issued. */
 nla_status nla_band2bd_noalloc(int n, int band, nla_dtype dtype, void *dAB, int ldab, double *dD,
                                double *dE, int *dInfo, nla_stream_t stream);
 
@@ -218,6 +221,18 @@ void nla_trace_reset(void);
  * check the tensor-core path of its device in isolation. */
 nla_status nla_tc_selftest(int prec, int K, int N, const float *dA, const float *dB, float *dD,
                            int *dInfo, nla_stream_t stream);
+
+/* The two exact power-of-two conversions of the TF32 / BF16 trailing update's
+ * scaling step (the "column scaling" of the mixed-precision form), element by
+ * element, so a caller can check them on edge values: for i < n,
+ *   dF[i] = dX[i] * 2^-dEx[i] as FP32, its significand truncated to FP32's 24
+ *           bits; 0 (signed) below FP32's normal range, +-inf at or above 2^128
+ *           (FP64 subnormal inputs read as 0);
+ *   dD[i] = dV[i] * 2^dEv[i] as FP64 (exact); 0 for FP32 zeros and subnormals,
+ *           a signed 0 below FP64's normal range, +-inf above it.
+ * All pointers are device arrays of n entries.  Asynchronous on `stream`. */
+nla_status nla_scale_selftest(int n, const double *dX, const int *dEx, float *dF, const float *dV,
+                              const int *dEv, double *dD, nla_stream_t stream);
 
 /* Failure-detection self-test (no counterpart in the paper): one block waits,
  * with a budget of budget_us microseconds, on something that never happens --

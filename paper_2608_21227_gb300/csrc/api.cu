@@ -541,6 +541,8 @@ nla_status nla_gesvd_vals_workspace(int m, int n, nla_dtype dtype, const nla_opt
     if (m < 0 || n < 0) return fail(NLA_ERR_ARG, "negative size %d x %d", m, n);
     const int M = std::max(m, n), N = std::min(m, n);
     Stage1Plan p = make_plan(M, N, dtype, opts, 0);
+    s = check_upd(p, (int)elem_size(dtype));
+    if (s != NLA_OK) return s;
     *bytes = gesvd_layout(nullptr, m, n, dtype, opts, p).bytes;
     return NLA_OK;
 }
@@ -586,6 +588,8 @@ nla_status nla_gebrd_band_workspace(int m, int n, int band, nla_dtype dtype, con
     if (s != NLA_OK) return s;
     if (m < n || n < 0) return fail(NLA_ERR_ARG, "gebrd_band needs m >= n >= 0 (got %d x %d)", m, n);
     Stage1Plan p = make_plan(m, n, dtype, opts, band);
+    s = check_upd(p, (int)elem_size(dtype));
+    if (s != NLA_OK) return s;
     Stage1Bufs b;
     Carver cv{nullptr};
     carve_stage1(cv, m, n, dtype, p.b, p.update, b);

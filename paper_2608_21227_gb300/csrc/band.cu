@@ -780,23 +780,19 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
     auto kern = b == 16 ? band2bd_group_kernel<T, 16>
                 : b == 32 ? band2bd_group_kernel<T, 32>
                 : b == 64 ? band2bd_group_kernel<T, 64> : band2bd_group_kernel<T, 0>;
-    static bool gattr = false;
-    if (!gattr) {
+    static PerDeviceOnce gattr;
+    gattr.run([&] {
         for (auto k : {band2bd_group_kernel<T, 0>, band2bd_group_kernel<T, 16>, band2bd_group_kernel<T, 32>,
                        band2bd_group_kernel<T, 64>})
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGroupBudget);
         cudaGetLastError();
-        gattr = true;
-    }
+    });
     // the largest G (<= the requested one) whose block -- G chase warps + 2 movers, its
-    // window -- is resident on every SM (registers, shared memory), cached per band width
-    static int gcache[4] = {-1, -1, -1, -1}, pcache[4] = {0, 0, 0, 0};
-    const int ci = b == 16 ? 1 : b == 32 ? 2 : b == 64 ? 3 : 0;
-    int G = 0, pf = 0;
-    if (gset > 0 && ci > 0 && gcache[ci] >= 0) {
-        G = gcache[ci];
-        pf = pcache[ci];
-    } else if (gset > 0) {
+    // window -- is resident on every SM (registers, shared memory), cached per device and
+    // band width (16, 32, 64; other widths are asked every call)
+    auto pick_group = [&](int &G, int &pf) {
+        G = 0;
+        pf = 0;
         for (int gmax = std::min(gset, 30); gmax >= 1; --gmax) {
             int p2 = 0;
             const int g2 = chase_group_size(b, (int)sizeof(T), kGroupBudget, gmax, p2);
@@ -812,10 +808,20 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
             cudaGetLastError();
             gmax = std::min(gmax, g2);
         }
-        if (ci > 0) {
-            gcache[ci] = G;
-            pcache[ci] = pf;
-        }
+    };
+    static PerDeviceValue<int2> gcache[4];
+    const int ci = b == 16 ? 1 : b == 32 ? 2 : b == 64 ? 3 : 0;
+    int G = 0, pf = 0;
+    if (gset > 0 && ci > 0) {
+        const int2 gp = gcache[ci].get([&] {
+            int g = 0, p = 0;
+            pick_group(g, p);
+            return make_int2(g, p);
+        });
+        G = gp.x;
+        pf = gp.y;
+    } else if (gset > 0) {
+        pick_group(G, pf);
     }
     if (nsweeps > 0 && b > 1 && G >= 1) {
         const int ngroups = (nsweeps + G - 1) / G;
@@ -839,12 +845,12 @@ cudaError_t band2bd(T *AB, long ldab, int n, int b, double *d, double *e, void *
     } else if (nsweeps > 0 && b > 1) {
         cudaError_t err = cudaMemsetAsync(progress, 0, sizeof(int) * (size_t)nsweeps, st);
         if (err != cudaSuccess) return err;
-        static bool smem_attr = false;
-        if (!smem_attr) {
+        static PerDeviceOnce smem_attr;
+        smem_attr.run([] {
             cudaFuncSetAttribute(band2bd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(((size_t)129 * 128 + 64 + 8) * sizeof(T)));
-            smem_attr = true;
-        }
+            cudaGetLastError();
+        });
         int grid = std::min(nsweeps, device_sm_count());
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(grid);

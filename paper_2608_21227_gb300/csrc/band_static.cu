@@ -1,14 +1,14 @@
 // band_static.cu -- nla_band2bd_noalloc: the band -> bidiagonal reduction for
 // callers that cannot allocate device memory.
 //
-// nla_band2bd needs a small scratch array (one progress counter per sweep of
-// the bulge chase) that the caller normally supplies as a workspace.  Some
-// callers have no way to provide one: code that runs while a stream is being
-// captured into a CUDA graph (cudaMalloc is not a stream operation and cannot
-// be captured), code that must never synchronise the device (cudaMalloc and
-// cudaFree may), and applications whose memory manager owns the whole device
-// and forbids allocations outside it.  For them this variant keeps its scratch
-// in a fixed array compiled into the library.
+// nla_band2bd needs a small scratch array (one progress counter per group of
+// sweeps of the bulge chase) that the caller normally supplies as a workspace.
+// Some callers have no way to provide one: a plug-in or kernel library running
+// inside a host framework whose memory manager owns the whole device and
+// forbids allocations outside it, code that must never synchronise the device
+// (cudaMalloc and cudaFree may), and programs with a fixed device-memory budget
+// set at start-up.  For them this variant keeps its scratch in a fixed array
+// compiled into the library.
 //
 // The array is a file-scope __device__ variable of kStaticChaseMaxN ints
 // (256 KiB); every GPU that loads the library holds it until the process
@@ -20,10 +20,12 @@
 // the GPU (different streams without ordering between them) race on it and
 // must not be issued.
 #include <mutex>
+#include <string>
 
 #include "../../include/nla.h"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "trace.h"
 #include "tuned.h"
 
 namespace {
@@ -76,9 +78,16 @@ extern "C" nla_status nla_band2bd_noalloc(int n, int band, nla_dtype dtype, void
         cudaGetLastError();
         return err(NLA_ERR_CUDA, "nla_band2bd_noalloc: memset of info failed");
     }
-    cudaError_t e = dtype == NLA_F64
-                        ? nla::band2bd<double>((double *)dAB, ldab, n, band, dD, dE, progress, dInfo, st)
-                        : nla::band2bd<float>((float *)dAB, ldab, n, band, dD, dE, progress, dInfo, st);
-    if (e != cudaSuccess) return err(NLA_ERR_CUDA, cudaGetErrorString(e));
+    cudaError_t e;
+    {
+        nla::TraceScope ts(nla::kTrBand2bd, st);  // timed with the regular chase when tracing is on
+        e = dtype == NLA_F64 ? nla::band2bd<double>((double *)dAB, ldab, n, band, dD, dE, progress, dInfo, st)
+                             : nla::band2bd<float>((float *)dAB, ldab, n, band, dD, dE, progress, dInfo, st);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        std::string msg = std::string("nla_band2bd_noalloc: bulge chase: ") + cudaGetErrorString(e);
+        return err(e == cudaErrorInvalidConfiguration ? NLA_ERR_CONFIG : NLA_ERR_CUDA, msg.c_str());
+    }
     return NLA_OK;
 }

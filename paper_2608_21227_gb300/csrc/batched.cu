@@ -414,14 +414,14 @@ nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *dM, con
         if (nla::g_batched_group[b] >= kMinGroup[b] && nla::g_batched_group[b] <= kBThreads &&
             kBThreads % nla::g_batched_group[b] == 0)
             cfg.group[b] = nla::g_batched_group[b];
-    static bool attr = false;
+    static nla::PerDeviceOnce attr;
     const size_t sort_smem = (size_t)kSortMax * sizeof(unsigned long long);
     const size_t main_smem = ((size_t)kBSmemElems + 8 * 800) * sizeof(float);
-    if (!attr) {
+    attr.run([&] {
         cudaFuncSetAttribute(batched_prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
         cudaFuncSetAttribute(batched_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)main_smem);
-        attr = true;
-    }
+        cudaGetLastError();
+    });
     {
         nla::TraceScope ts(nla::kTrBatched, st);
         batched_prep_kernel<<<1, 1024, batch <= kSortMax ? sort_smem : 0, st>>>(batch, dM, dN, order, counter);

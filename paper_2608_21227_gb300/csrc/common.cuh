@@ -4,6 +4,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "../../include/nla.h"
 
 #define NLA_DEV __device__ __forceinline__
@@ -117,6 +120,72 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     cfg.attrs = at;
     cfg.numAttrs = pdl_enabled() ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
+// ---------------------------------------------------------------- host: per-device set-up
+// Launch set-up that depends on the device (a kernel's shared-memory or cluster
+// attribute, an occupancy query, the SM count) is done once per device and may be
+// reached from several host threads at the same time.
+
+constexpr int kMaxDevices = 64;
+
+// The current device (cudaGetDevice), or -1 when there is none.
+int current_device();
+
+// run(f) calls f() the first time it is reached while a given device is current and
+// never again for that device; concurrent first calls wait for the one that runs f.
+class PerDeviceOnce {
+  public:
+    template <class F>
+    void run(F &&f) {
+        const int dev = current_device();
+        if (dev < 0 || dev >= kMaxDevices) {
+            f();
+            return;
+        }
+        const unsigned long long bit = 1ull << dev;
+        if (done_.load(std::memory_order_acquire) & bit) return;
+        std::lock_guard<std::mutex> lk(mu_);
+        if (done_.load(std::memory_order_relaxed) & bit) return;
+        f();
+        done_.fetch_or(bit, std::memory_order_release);
+    }
+
+  private:
+    std::atomic<unsigned long long> done_{0};
+    std::mutex mu_;
+};
+
+// A value computed once per device (compute() runs with that device current).
+template <class T>
+class PerDeviceValue {
+  public:
+    template <class F>
+    T get(F &&compute) {
+        const int dev = current_device();
+        if (dev < 0 || dev >= kMaxDevices) return compute();
+        once_.run([&] { val_[dev] = compute(); });
+        return val_[dev];
+    }
+
+  private:
+    PerDeviceOnce once_;
+    T val_[kMaxDevices] = {};
+};
+
+// Allow `kernel` the opt-in dynamic shared-memory maximum minus its static shared
+// memory, once per device.
+template <typename K>
+void allow_max_smem(K kernel, PerDeviceOnce &once) {
+    once.run([&] {
+        int optin = 0;
+        const int dev = current_device();
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev < 0 ? 0 : dev);
+        cudaFuncAttributes fa;
+        const size_t stat = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)optin - stat));
+        cudaGetLastError();
+    });
 }
 
 }  // namespace nla

@@ -43,15 +43,23 @@ size_t panel_part_doubles(int P) {
     return (size_t)2 * P * (kNbMax + 1) + (size_t)P * kNbMax * kNbMax + 2 * kNbMax;
 }
 
-int device_sm_count() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
+int current_device() {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
     }
-    return sms;
+    return dev;
+}
+
+int device_sm_count() {
+    static PerDeviceValue<int> sms;
+    return sms.get([] {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, std::max(current_device(), 0)) != cudaSuccess)
+            cudaGetLastError();
+        return n > 0 ? n : 1;
+    });
 }
 
 int panel_max_ctas() { return device_sm_count(); }
@@ -806,29 +814,31 @@ panel_reg_kernel(T *__restrict__ P, long rs, long cs, int M, int R, T *__restric
 // Cluster size and rows per block for an M x nb panel, or 0 if it does not fit one cluster.
 // Which cluster sizes the device can schedule (one block per SM at the largest
 // dynamic shared memory) is asked once; smaller allocations schedule as well.
+struct ClusterCaps {
+    size_t max_dyn = 0;
+    bool sched[5] = {false, false, false, false, false};  // cluster sizes 1, 2, 4, 8, 16
+};
+
 template <typename T>
 static int cluster_plan(int M, int nb, int &R, size_t &dyn) {
-    static bool init = false;
-    static size_t max_dyn = 0;
-    static bool sched[5] = {false, false, false, false, false};  // cluster sizes 1, 2, 4, 8, 16
-    if (!init) {
-        init = true;
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    static PerDeviceValue<ClusterCaps> caps_dev;
+    const ClusterCaps caps = caps_dev.get([] {
+        ClusterCaps c;
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, std::max(current_device(), 0));
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, panel_cluster_kernel<T>) == cudaSuccess && (size_t)optin > fa.sharedSizeBytes)
-            max_dyn = (size_t)optin - fa.sharedSizeBytes;
-        if (cudaFuncSetAttribute(panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dyn) !=
+            c.max_dyn = (size_t)optin - fa.sharedSizeBytes;
+        if (cudaFuncSetAttribute(panel_cluster_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.max_dyn) !=
                 cudaSuccess ||
             cudaFuncSetAttribute(panel_cluster_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
                 cudaSuccess)
-            max_dyn = 0;
-        for (int k = 0; k < 5 && max_dyn > 0; ++k) {
+            c.max_dyn = 0;
+        for (int k = 0; k < 5 && c.max_dyn > 0; ++k) {
             cudaLaunchConfig_t cfg = {};
             cfg.gridDim = dim3(1u << k);
             cfg.blockDim = dim3(kClusterThreads);
-            cfg.dynamicSmemBytes = max_dyn;
+            cfg.dynamicSmemBytes = c.max_dyn;
             cudaLaunchAttribute attr[1];
             attr[0].id = cudaLaunchAttributeClusterDimension;
             attr[0].val.clusterDim.x = 1u << k;
@@ -837,10 +847,13 @@ static int cluster_plan(int M, int nb, int &R, size_t &dyn) {
             cfg.attrs = attr;
             cfg.numAttrs = 1;
             int ncl = 0;
-            sched[k] = cudaOccupancyMaxActiveClusters(&ncl, panel_cluster_kernel<T>, &cfg) == cudaSuccess && ncl >= 1;
+            c.sched[k] = cudaOccupancyMaxActiveClusters(&ncl, panel_cluster_kernel<T>, &cfg) == cudaSuccess && ncl >= 1;
         }
         cudaGetLastError();
-    }
+        return c;
+    });
+    const size_t max_dyn = caps.max_dyn;
+    const bool *sched = caps.sched;
     int k0 = 0;
     while (k0 < 4 && (1 << k0) * kPanelRowsTarget < M) ++k0;  // smallest size with <= 256 rows per block
     static const int force = [] {  // NLA_PANEL_CLUSTER: cluster size to use where it fits (0: grid kernel)
@@ -870,12 +883,11 @@ static int cluster_plan(int M, int nb, int &R, size_t &dyn) {
 template <typename T, int NB, int RP>
 cudaError_t panel_reg_launch_nb(T *P, long rs, long cs, int M, int R, int C, T *tau, T *Tm, int *info,
                                 cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        attr = true;
+    static PerDeviceOnce attr;
+    attr.run([] {
         cudaFuncSetAttribute(panel_reg_kernel<T, NB, RP>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaGetLastError();
-    }
+    });
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C);
     cfg.blockDim = dim3(kClusterThreads);
@@ -952,18 +964,18 @@ cudaError_t panel_factor(T *P, long rs, long cs, int M, int nb, T *tau, T *Tm, c
             cudaGetLastError();  // fall back to the grid-wide version
         }
     }
-    static size_t max_dyn = 0;
-    static bool attr_set = false;
-    if (!attr_set) {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    static PerDeviceValue<size_t> grid_dyn;
+    const size_t max_dyn = grid_dyn.get([] {
+        int optin = 0;
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, std::max(current_device(), 0));
         cudaFuncAttributes fa;
-        cudaFuncGetAttributes(&fa, panel_kernel<T>);
-        max_dyn = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
-        cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_dyn);
-        attr_set = true;
-    }
+        size_t md = 0;
+        if (cudaFuncGetAttributes(&fa, panel_kernel<T>) == cudaSuccess)
+            md = (size_t)optin > fa.sharedSizeBytes ? (size_t)optin - fa.sharedSizeBytes : 0;
+        cudaFuncSetAttribute(panel_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)md);
+        cudaGetLastError();
+        return md;
+    });
     const int maxP = panel_max_ctas();
     int Pn = std::max(1, std::min(maxP, (M + kPanelRowsTarget - 1) / kPanelRowsTarget));
     const size_t gt_bytes = (size_t)2 * nb * nb * sizeof(double) + 16;

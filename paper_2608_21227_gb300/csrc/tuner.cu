@@ -50,9 +50,10 @@ nla_cfg space_point(int idx) {
 
 nla::UpdCfg upd_of(const nla_cfg &c) { return nla::UpdCfg{c.tile, c.threads, c.cols_per_block, c.unroll}; }
 
+// The launch rule of the trailing-update kernels (shape, shared memory and, when a
+// device is present, the compiled kernels' thread limits): what nla_gesvd_vals accepts.
 bool cfg_valid(int side, int elem, const nla_cfg &c) {
-    size_t sm;
-    return nla::upd_cfg_valid(side, elem, c.band, upd_of(c), &sm);
+    return nla::upd_cfg_launchable(side, elem, c.band, upd_of(c));
 }
 
 nla_status terr(nla_status s, const std::string &m) {
@@ -159,6 +160,12 @@ double median_of(std::vector<double> v) {
 }
 
 const nla_cfg kDefault = {32, 64, 128, 2, 1};
+
+// The default configuration's kernel parameters (any band).
+bool is_default_kernel(const nla_cfg &c) {
+    return c.tile == kDefault.tile && c.threads == kDefault.threads && c.cols_per_block == kDefault.cols_per_block &&
+           c.unroll == kDefault.unroll;
+}
 
 // ------------------------------------------------------------------ trailing-update tuning
 template <typename T>
@@ -354,9 +361,9 @@ nla_status tune_trail(const kt_problem &p, kt_strategy strategy, double frac, co
             if (!nla::upd_cfg_valid(side, elem, cur_band, u, &sm)) ref = c;
             Meas mref = tb.measure(ref, true);
             if (mref.status != 0) return terr(NLA_ERR_CUDA, "tuner: reference configuration failed");
-            if (ref.band == kDefault.band && ref.tile == kDefault.tile && ref.threads == kDefault.threads &&
-                ref.cols_per_block == kDefault.cols_per_block && ref.unroll == kDefault.unroll)
-                r.default_ms = mref.ms;
+            // the default's kernel parameters at the band being tuned (kernel parameters are
+            // tuned per band; with every band, the default band's entry is reported)
+            if (is_default_kernel(ref) && (p.band > 0 || ref.band == kDefault.band)) r.default_ms = mref.ms;
         }
         Key k{(int)p.kernel, p.m, p.n, (int)p.dtype, (int)p.update, c.band, c.tile, c.threads, c.cols_per_block,
               c.unroll};
@@ -380,9 +387,7 @@ nla_status tune_trail(const kt_problem &p, kt_strategy strategy, double frac, co
             r.best_ms = v.ms;
             have_best = true;
         }
-        if (c.band == kDefault.band && c.tile == kDefault.tile && c.threads == kDefault.threads &&
-            c.cols_per_block == kDefault.cols_per_block && c.unroll == kDefault.unroll)
-            r.default_ms = v.ms;
+        if (is_default_kernel(c) && (p.band > 0 || c.band == kDefault.band)) r.default_ms = v.ms;
     }
     // the model / random strategies visit candidates out of lexicographic order: recompute ties properly
     r.median_ms = median_of(times);
@@ -391,15 +396,45 @@ nla_status tune_trail(const kt_problem &p, kt_strategy strategy, double frac, co
     return NLA_OK;
 }
 
+// Installs a temporary tuned table for the pipeline-level runs (each side its own
+// configuration) and puts the caller's table back when it goes out of scope.
+struct TableSwap {
+    std::vector<TableEntry> saved;
+    bool active = false;
+    void install(const std::vector<TableEntry> &t) {
+        std::lock_guard<std::mutex> lk(g_table_mu);
+        if (!active) saved = g_table;
+        g_table = t;
+        active = true;
+    }
+    ~TableSwap() {
+        if (!active) return;
+        std::lock_guard<std::mutex> lk(g_table_mu);
+        g_table.swap(saved);
+    }
+};
+
+// Verification tolerance of a pipeline-level candidate against the default
+// configuration's singular values (relative to the largest): twice the acceptance
+// bound of the dtype, or for the TF32 / BF16 forms the first-order model 10 u sqrt(N/16).
+double pipeline_tol(const kt_problem &p, int N) {
+    if (p.update == NLA_UPD_TF32) return 10.0 * std::ldexp(1.0, -11) * std::sqrt(N / 16.0);
+    if (p.update == NLA_UPD_BF16) return 10.0 * std::ldexp(1.0, -8) * std::sqrt(N / 16.0);
+    return 2.0 * (p.dtype == NLA_F64 ? 1e-12 : 5e-6) * N;
+}
+
 nla_status tune_gesvd(const kt_problem &p, const char *cache_path, unsigned long long seed, kt_result *out) {
-    // pipeline level: band width, each band with its best kernel configs from the cache (else defaults)
+    // pipeline level: band width, each band with each side's best kernel configuration
+    // from the cache (else the defaults), timed end to end and verified against the
+    // default configuration's singular values
     std::map<Key, Meas> cache;
     load_cache(cache_path, cache);
     const int es = p.dtype == NLA_F64 ? 8 : 4;
     const int M = std::max(p.m, p.n), N = std::min(p.m, p.n);
-    void *A = nullptr, *A0 = nullptr, *S = nullptr, *W = nullptr;
+    void *A = nullptr, *A0 = nullptr, *S = nullptr, *Sref = nullptr, *W = nullptr;
     int *info = nullptr;
-    size_t cnt = (size_t)M * N;
+    double *diff = nullptr;
+    size_t cnt = (size_t)M * N, wbytes = 0;
     kt_result r;
     memset(&r, 0, sizeof r);
     r.best_ms = r.median_ms = r.default_ms = NAN;
@@ -411,16 +446,73 @@ nla_status tune_gesvd(const kt_problem &p, const char *cache_path, unsigned long
     cudaEventCreate(&e1);
     nla_status status = NLA_OK;
     if (cudaMalloc(&A, cnt * es) || cudaMalloc(&A0, cnt * es) || cudaMalloc(&S, N * (size_t)es) ||
-        cudaMalloc(&info, sizeof(int))) {
+        cudaMalloc(&Sref, N * (size_t)es) || cudaMalloc(&info, sizeof(int)) || cudaMalloc(&diff, 2 * sizeof(double))) {
         cudaGetLastError();
         status = terr(NLA_ERR_CUDA, "tuner: allocation failed");
     }
+    const int reps = p.reps > 0 ? p.reps : 3;
+    TableSwap swap;
+    // one end-to-end configuration: median of `reps` timed runs after one warm-up (input
+    // restored before each), then the singular values checked (or kept as the reference)
+    auto run = [&](const nla_opts &o, bool reference, double &med) -> int {  // 0 ok, 1 launch, 2 verify
+        size_t need = 0;
+        if (nla_gesvd_vals_workspace(M, N, p.dtype, &o, &need) != NLA_OK) return 1;
+        if (need > wbytes) {
+            cudaFree(W);
+            W = nullptr;
+            wbytes = 0;
+            if (cudaMalloc(&W, need)) {
+                cudaGetLastError();
+                return 1;
+            }
+            wbytes = need;
+        }
+        std::vector<double> t;
+        for (int rep = 0; rep <= reps; ++rep) {
+            cudaMemcpyAsync(A, A0, cnt * es, cudaMemcpyDeviceToDevice, st);
+            cudaEventRecord(e0, st);
+            nla_status s = nla_gesvd_vals(M, N, p.dtype, A, M, S, W, wbytes, info, &o, st);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess || s != NLA_OK) {
+                cudaGetLastError();
+                return 1;
+            }
+            int hinfo = 0;
+            cudaMemcpy(&hinfo, info, sizeof(int), cudaMemcpyDeviceToHost);
+            if (hinfo != 0) return 1;
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) t.push_back(ms);  // rep 0 is the warm-up
+        }
+        med = median_of(t);
+        if (reference) {
+            cudaMemcpyAsync(Sref, S, N * (size_t)es, cudaMemcpyDeviceToDevice, st);
+            cudaStreamSynchronize(st);
+            return 0;
+        }
+        cudaMemsetAsync(diff, 0, 2 * sizeof(double), st);
+        if (es == 8)
+            max_abs_diff_kernel<double><<<64, 256, 0, st>>>((const double *)S, (const double *)Sref, N, diff);
+        else
+            max_abs_diff_kernel<float><<<64, 256, 0, st>>>((const float *)S, (const float *)Sref, N, diff);
+        double h[2] = {0, 0};
+        cudaMemcpyAsync(h, diff, sizeof h, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        return h[0] <= pipeline_tol(p, M) * std::max(h[1], 1e-300) ? 0 : 2;
+    };
     if (status == NLA_OK) {
         if (es == 8)
             fill_uniform_kernel<double><<<1024, 256, 0, st>>>((double *)A0, (long)cnt, seed);
         else
             fill_uniform_kernel<float><<<1024, 256, 0, st>>>((float *)A0, (long)cnt, seed);
-        const int reps = p.reps > 0 ? p.reps : 3;
+        // the default configuration (every field explicit: no table), also the reference
+        nla_cfg dflt = kDefault;
+        nla_opts od = {p.update, &dflt, 0};
+        double dms = NAN;
+        if (run(od, true, dms) != 0) status = terr(NLA_ERR_CUDA, "tuner: the default configuration failed");
+        r.default_ms = dms;
+    }
+    if (status == NLA_OK) {
         for (int bi = 0; bi < 3; ++bi) {
             const int b = kBands[bi];
             if (p.band > 0 && b != p.band) continue;
@@ -444,41 +536,24 @@ nla_status tune_gesvd(const kt_problem &p, const char *cache_path, unsigned long
                     }
                 }
             }
-            // time end to end, left config drives both sides when they differ (install both)
-            nla_opts o = {p.update, &best[0], 0};
-            size_t need = 0;
-            if (nla_gesvd_vals_workspace(M, N, p.dtype, &o, &need) != NLA_OK) continue;
-            cudaFree(W);
-            W = nullptr;
-            if (cudaMalloc(&W, need)) {
-                cudaGetLastError();
-                status = terr(NLA_ERR_CUDA, "tuner: workspace allocation failed");
-                break;
-            }
-            std::vector<double> t;
-            for (int rep = 0; rep <= reps; ++rep) {
-                cudaMemcpyAsync(A, A0, cnt * es, cudaMemcpyDeviceToDevice, st);
-                cudaEventRecord(e0, st);
-                nla_status s = nla_gesvd_vals(M, N, p.dtype, A, M, S, W, need, info, &o, st);
-                cudaEventRecord(e1, st);
-                cudaEventSynchronize(e1);
-                if (s != NLA_OK) break;
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) t.push_back(ms);  // rep 0 is the warm-up
-            }
+            // each side runs its own configuration: installed as a one-size table
+            std::vector<TableEntry> t(2);
+            for (int side = 0; side < 2; ++side) t[side] = TableEntry{side, M, N, (int)p.dtype, (int)p.update, best[side], 0.0};
+            swap.install(t);
+            nla_cfg band_only = {b, 0, 0, 0, 0};
+            nla_opts o = {p.update, &band_only, 0};
+            double med = NAN;
+            const int rs = run(o, false, med);
             r.evaluated++;
-            if ((int)t.size() != reps) {
+            if (rs != 0) {
                 r.failed++;
                 continue;
             }
-            double med = median_of(t);
             times.push_back(med);
             if (!(med >= r.best_ms)) {
                 r.best_ms = med;
                 r.best = best[0];
             }
-            if (b == 32) r.default_ms = med;
         }
         r.valid = (int)times.size() + r.failed;
         r.median_ms = median_of(times);
@@ -486,8 +561,10 @@ nla_status tune_gesvd(const kt_problem &p, const char *cache_path, unsigned long
     cudaFree(A);
     cudaFree(A0);
     cudaFree(S);
+    cudaFree(Sref);
     cudaFree(W);
     cudaFree(info);
+    cudaFree(diff);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaStreamDestroy(st);

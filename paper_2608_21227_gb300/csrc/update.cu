@@ -247,12 +247,11 @@ __global__ void trail_right_kernel(T *__restrict__ X, long ldx, int M, int N, co
 template <typename T, int U>
 static cudaError_t launch_left(T *X, long ldx, int M, int N, const T *V, long ldv, int nb, const T *Tm,
                                const UpdCfg &c, size_t smem, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(trail_left_kernel<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemLimit);
-        attr = true;
-    }
+    static PerDeviceOnce attr;
+    attr.run([] {
+        cudaFuncSetAttribute(trail_left_kernel<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+        cudaGetLastError();
+    });
     const int w = 32 * c.cpb;
     dim3 grid((N + w - 1) / w);
     trail_left_kernel<T, U><<<grid, c.threads, smem, st>>>(X, ldx, M, N, V, ldv, nb, Tm, c.tile, w);
@@ -262,41 +261,46 @@ static cudaError_t launch_left(T *X, long ldx, int M, int N, const T *V, long ld
 template <typename T, int U>
 static cudaError_t launch_right(T *X, long ldx, int M, int N, const T *Vt, long ldvt, int nb,
                                 const T *Tm, const UpdCfg &c, size_t smem, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(trail_right_kernel<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)kSmemLimit);
-        attr = true;
-    }
+    static PerDeviceOnce attr;
+    attr.run([] {
+        cudaFuncSetAttribute(trail_right_kernel<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit);
+        cudaGetLastError();
+    });
     const int h = 32 * c.cpb;
     dim3 grid((M + h - 1) / h);
     trail_right_kernel<T, U><<<grid, c.threads, smem, st>>>(X, ldx, M, N, Vt, ldvt, nb, Tm, c.tile, h);
     return cudaGetLastError();
 }
 
-// Largest block the compiled kernel can launch (its register use bounds it).
+// Largest block the compiled kernel can launch (its register use bounds it); -1 when
+// it cannot be asked (no CUDA device in this process): the launch itself then decides.
 template <typename K>
 static int max_threads_of(K kernel) {
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
         cudaGetLastError();
-        return 0;
+        return -1;
     }
     return fa.maxThreadsPerBlock;
 }
 
 template <typename T>
 static int max_threads(int side, int unroll) {
+    static std::mutex mu;  // (thread limits are per architecture, not per device)
     static int cache[2][3] = {{-1, -1, -1}, {-1, -1, -1}};
+    std::lock_guard<std::mutex> lk(mu);
     int u = unroll == 1 ? 0 : unroll == 2 ? 1 : 2;
     int &v = cache[side][u];
     if (v < 0) {
+        int q;
         if (side == 0)
-            v = u == 0 ? max_threads_of(trail_left_kernel<T, 1>)
+            q = u == 0 ? max_threads_of(trail_left_kernel<T, 1>)
                        : u == 1 ? max_threads_of(trail_left_kernel<T, 2>) : max_threads_of(trail_left_kernel<T, 4>);
         else
-            v = u == 0 ? max_threads_of(trail_right_kernel<T, 1>)
+            q = u == 0 ? max_threads_of(trail_right_kernel<T, 1>)
                        : u == 1 ? max_threads_of(trail_right_kernel<T, 2>) : max_threads_of(trail_right_kernel<T, 4>);
+        if (q < 0) return 1024;  // unknown (not cached)
+        v = q;
     }
     return v;
 }

@@ -87,6 +87,12 @@ NLA_DEV int scale_exp(double mx) {
 // max(E) - 1022 (the frexp exponent of the largest), 0 if all are zero.
 NLA_DEV int f64_biased_exp(double x) { return (int)(((uint32_t)__double2hiint(x) >> 20) & 0x7FFu); }
 NLA_DEV int scale_exp_from_biased(int emax) { return emax > 0 ? emax - 1022 : 0; }
+// Scale exponent of a tile line for the step-1 accumulation: kNoExp marks a line whose
+// entries are all zero (it adds nothing to the product).
+constexpr int kNoExp = -100000;
+NLA_DEV int tile_exp_from_biased(int emax) { return emax > 0 ? emax - 1022 : kNoExp; }
+// 2^k for k <= 0 (0 below FP32's range); the power-of-two factors of the running sums.
+NLA_DEV float exp2_nonpos(int k) { return k < -149 ? 0.f : ldexpf(1.f, k); }
 // x * 2^-e as FP32 (exact scaling; the mantissa is truncated to FP32's 23 bits, far
 // below the TF32/BF16 rounding that follows); results below FP32's normal range are 0.
 NLA_DEV float f64_scaled_to_f32(double x, int e) {
@@ -99,12 +105,18 @@ NLA_DEV float f64_scaled_to_f32(double x, int e) {
     const uint32_t mant = ((hi & 0xFFFFFu) << 3) | (lo >> 29);
     return __uint_as_float(sign | ((uint32_t)fe << 23) | mant);
 }
-// v * 2^e as FP64 (exact); FP32 zeros and subnormals give 0.
+// v * 2^e as FP64 (exact while the result is a normal FP64 number); FP32 zeros and
+// subnormals give 0, results below FP64's normal range give a signed 0, results above
+// it (or an infinite / NaN v) a signed infinity.
 NLA_DEV double f32_scaled_to_f64(float v, int e) {
     const uint32_t b = __float_as_uint(v);
     const int E8 = (int)((b >> 23) & 0xFFu);
+    const uint32_t sign = b & 0x80000000u;
     if (E8 == 0) return 0.0;
-    const uint32_t hi = (b & 0x80000000u) | ((uint32_t)(E8 - 127 + 1023 + e) << 20) | ((b & 0x7FFFFFu) >> 3);
+    const int E11 = E8 - 127 + 1023 + e;
+    if (E11 <= 0) return __hiloint2double((int)sign, 0);
+    if (E8 == 255 || E11 >= 2047) return __hiloint2double((int)(sign | 0x7FF00000u), 0);
+    const uint32_t hi = sign | ((uint32_t)E11 << 20) | ((b & 0x7FFFFFu) >> 3);
     return __hiloint2double((int)hi, (int)(b << 29));
 }
 
@@ -202,8 +214,8 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(const float *A, const 
 template <int PREC, int SIDE>
 __global__ void __launch_bounds__(kTcThreads)
 tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *__restrict__ V, long ldv, int nb,
-            int nbp, const double *__restrict__ Tm, int Ls, float *part, float *fin, unsigned int *tickets,
-            int *info) {
+            int nbp, const double *__restrict__ Tm, int Ls, float *part, int *pexp, float *fin, int *finexp,
+            unsigned int *tickets, int *info) {
     using P = Prec<PREC>;
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ int sh_last;
@@ -241,6 +253,7 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
     float acc[32];
 #pragma unroll
     for (int i = 0; i < 32; ++i) acc[i] = 0.f;
+    int erun = kNoExp;  // acc holds the line's partial W scaled by 2^-erun
     const int m = tid & (kStrip - 1), h = tid >> 7;  // loader: strip line m, K entries h*16 .. h*16+15
     const int ntiles = (kend - kbeg + kKt - 1) / kKt;
     for (int t = 0; t <= ntiles; ++t) {
@@ -289,13 +302,13 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
                     const int mc = warp * 16 + c;
-                    const int e = scale_exp_from_biased(__reduce_max_sync(0xffffffffu, f64_biased_exp(xv[c])));
+                    const int e = tile_exp_from_biased(__reduce_max_sync(0xffffffffu, f64_biased_exp(xv[c])));
                     if (lane == 0) ex1[buf * kStrip + mc] = e;
                     P::put(A1 + buf * kStrip * rb1, tc::kmajor_off(mc, lane, es, rb1), f64_scaled_to_f32(xv[c], e));
                 }
             } else {
                 __syncthreads();
-                const int e = scale_exp_from_biased(max(lmax[m], lmax[kStrip + m]));
+                const int e = tile_exp_from_biased(max(lmax[m], lmax[kStrip + m]));
                 if (h == 0) ex1[buf * kStrip + m] = e;
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
@@ -317,13 +330,25 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
             const bool ok = tc::mbar_wait_warp(&sh->mbar[pb], ((t - 1) >> 1) & 1, info);
             if (!ok && lane == 0) sh->fail = 1;
             tc::fence_after_sync();
-            const float sc = ldexpf(1.f, ex1[pb * kStrip + 32 * q + lane]);
-            for (int c = 0; ok && c < half; c += 16) {
-                float v[16];
-                tc::tmem_ld16(tbase + pb * 64 + hh * half + c + ((uint32_t)(32 * q) << 16), v);
-                tc::tmem_wait_ld();
+            // the tile's product is scaled by 2^-et per line; the running sum is kept
+            // scaled by 2^-erun (erun = the largest et so far), so no factor leaves
+            // FP32's range whatever the exponents of X
+            const int et = ex1[pb * kStrip + 32 * q + lane];
+            if (ok && et != kNoExp) {
+                if (et > erun) {
+                    const float r = exp2_nonpos(erun - et);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) acc[c + i] += v[i] * sc;
+                    for (int i = 0; i < 32; ++i) acc[i] *= r;
+                    erun = et;
+                }
+                const float sc = exp2_nonpos(et - erun);
+                for (int c = 0; c < half; c += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tbase + pb * 64 + hh * half + c + ((uint32_t)(32 * q) << 16), v);
+                    tc::tmem_wait_ld();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) acc[c + i] += v[i] * sc;
+                }
             }
             tc::fence_before_sync();
         }
@@ -340,19 +365,35 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
     const int line = 32 * q + lane;
     for (int i = 0; i < half; ++i)
         if (line < lw) part[((size_t)s * nbp + hh * half + i) * Lext + L0 + line] = acc[i];
+    if (hh == 0 && line < lw) pexp[(size_t)s * Lext + L0 + line] = erun;
     __threadfence();
     __syncthreads();
     if (tid == 0) sh_last = atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(S - 1);
     __syncthreads();
     if (!sh_last) return;
     __threadfence();
+    // the line's common exponent: the largest of its splits' (kNoExp: all zero)
+    int *lexp = reinterpret_cast<int *>(Wsh + (size_t)nbp * kStrip);
+    if (tid < kStrip) {
+        int em = kNoExp;
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq)
+            if (qq < S && tid < lw) em = max(em, __ldcg(pexp + (size_t)qq * Lext + L0 + tid));
+        lexp[tid] = em;
+        if (tid < lw) finexp[L0 + tid] = em == kNoExp ? 0 : em;
+    }
+    __syncthreads();
     for (int idx = tid; idx < nbp * kStrip; idx += blockDim.x) {
         const int l = idx % kStrip, k = idx / kStrip;
         float sum = 0.f;
-        if (l < lw)
+        if (l < lw && lexp[l] != kNoExp)
 #pragma unroll
             for (int qq = 0; qq < 8; ++qq)  // (S <= 8 splits; all partial loads in flight at once)
-                if (qq < S) sum += __ldcg(part + ((size_t)qq * nbp + k) * Lext + L0 + l);
+                if (qq < S) {
+                    const int es_ = __ldcg(pexp + (size_t)qq * Lext + L0 + l);
+                    if (es_ != kNoExp)
+                        sum += __ldcg(part + ((size_t)qq * nbp + k) * Lext + L0 + l) * exp2_nonpos(es_ - lexp[l]);
+                }
         Wsh[k * kStrip + l] = sum;
     }
     __syncthreads();
@@ -375,7 +416,7 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
 template <int PREC, int SIDE>
 __global__ void __launch_bounds__(kTcThreads)
 tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__restrict__ V, long ldv, int nb, int nbp,
-            const float *__restrict__ fin, int *info) {
+            const float *__restrict__ fin, const int *__restrict__ finexp, int *info) {
     using P = Prec<PREC>;
     extern __shared__ __align__(1024) unsigned char sm[];
     const int es = P::es, rb3 = nbp * es;
@@ -406,8 +447,10 @@ tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__rest
         for (int k = hf; k < nbp; k += 2) mx = fmaxf(mx, fabsf(l < lw && k < nb ? fin[(size_t)k * Lext + L0 + l] : 0.f));
         lmax[hf * kStrip + l] = mx;
         __syncthreads();
+        // fin holds W' / Y' scaled by 2^-finexp per line (step 1); rescaled here so the
+        // line's largest entry lies in [0.5, 1) before rounding, both undone in the epilogue
         const int e = scale_exp((double)fmaxf(lmax[l], lmax[kStrip + l]));
-        if (hf == 0) exs[l] = e;
+        if (hf == 0) exs[l] = e + (l < lw ? finexp[L0 + l] : 0);
         // QR: B operand rows = strip columns (N dim), K = reflectors; LQ: A operand rows = strip rows
         unsigned char *dst = SIDE == 0 ? Bop : Aop;
         for (int k = hf; k < nbp; k += 2) {
@@ -481,24 +524,10 @@ tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__rest
 size_t tc_w_smem(int es) {
     const size_t rb1 = (size_t)kKt * es;
     return std::max((size_t)2 * kStrip * rb1 + 2 * 64 * rb1 + 2 * kStrip * 4 + 2 * kStrip * 8 + sizeof(TcShared) + 64,
-                    (size_t)64 * kStrip * 4 + 64);
+                    (size_t)64 * kStrip * 4 + kStrip * 4 + 64);
 }
 size_t tc_x_smem(int es, int nbp) {
     return (size_t)2 * kStrip * nbp * es + kStrip * 4 + 2 * kStrip * 4 + sizeof(TcShared) + 64;
-}
-
-template <typename K>
-void allow_smem(K kernel, bool &done) {
-    if (!done) {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaFuncAttributes fa;
-        size_t stat = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)optin - stat));
-        cudaGetLastError();
-        done = true;
-    }
 }
 
 template <int PREC, int SIDE>
@@ -506,25 +535,39 @@ cudaError_t launch_tc(double *X, long ldx, int M, int N, const double *V, long l
                       const UpdScratch &sc, int *info, cudaStream_t st) {
     const int nbp = nb <= 32 ? 32 : 64;
     const int es = Prec<PREC>::es;
-    static bool a1 = false, a3 = false;
-    allow_smem(tc_w_kernel<PREC, SIDE>, a1);
-    allow_smem(tc_x_kernel<PREC, SIDE>, a3);
+    static PerDeviceOnce a1, a3;
+    allow_max_smem(tc_w_kernel<PREC, SIDE>, a1);
+    allow_max_smem(tc_x_kernel<PREC, SIDE>, a3);
     const int Lext = SIDE == 0 ? N : M, Kext = SIDE == 0 ? M : N;
     const int nblk = (Lext + kStrip - 1) / kStrip;
     int S = (3 * device_sm_count() + nblk - 1) / nblk;
     S = std::max(1, std::min({S, 8, (Kext + kKt - 1) / kKt}));
     int Ls = ((Kext + S - 1) / S + kKt - 1) / kKt * kKt;
     S = (Kext + Ls - 1) / Ls;
+    // scratch (FP64-element workspace of 10 * 64 * max(M, N) entries): 8 partial slabs of
+    // W / Y, the finished W' / Y', then the partials' and the result's line exponents
+    const size_t L = (size_t)std::max(M, N);
     float *part = reinterpret_cast<float *>(sc.work);
-    float *fin = part + (size_t)8 * 64 * std::max(M, N);
+    float *fin = part + (size_t)8 * 64 * L;
+    int *pexp = reinterpret_cast<int *>(fin + (size_t)64 * L);
+    int *finexp = pexp + (size_t)8 * L;
     tc_w_kernel<PREC, SIDE><<<dim3(nblk, S), kTcThreads, tc_w_smem(es), st>>>(X, ldx, M, N, V, ldv, nb, nbp, Tm, Ls,
-                                                                             part, fin, sc.tickets, info);
+                                                                             part, pexp, fin, finexp, sc.tickets, info);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int Text = SIDE == 0 ? M : N;
     tc_x_kernel<PREC, SIDE><<<dim3(nblk, (Text + kStrip - 1) / kStrip), kTcThreads, tc_x_smem(es, nbp), st>>>(
-        X, ldx, M, N, V, ldv, nb, nbp, fin, info);
+        X, ldx, M, N, V, ldv, nb, nbp, fin, finexp, info);
     return cudaGetLastError();
+}
+
+// Element-wise check of the two conversions (nla_scale_selftest).
+__global__ void scale_selftest_kernel(int n, const double *x, const int *ex, float *f, const float *v, const int *ev,
+                                      double *d) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    f[i] = f64_scaled_to_f32(x[i], ex[i]);
+    d[i] = f32_scaled_to_f64(v[i], ev[i]);
 }
 
 }  // namespace
@@ -572,5 +615,14 @@ extern "C" nla_status nla_tc_selftest(int prec, int K, int N, const float *dA, c
                              227 * 1024);
         nla::tc_selftest_kernel<NLA_UPD_BF16><<<1, 128, smem, st>>>(dA, dB, dD, K, N, dInfo);
     }
+    return cudaGetLastError() == cudaSuccess ? NLA_OK : NLA_ERR_CUDA;
+}
+
+extern "C" nla_status nla_scale_selftest(int n, const double *dX, const int *dEx, float *dF, const float *dV,
+                                         const int *dEv, double *dD, nla_stream_t stream) {
+    if (n < 0 || (n > 0 && (!dX || !dEx || !dF || !dV || !dEv || !dD))) return NLA_ERR_ARG;
+    if (n == 0) return NLA_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    nla::scale_selftest_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, dX, dEx, dF, dV, dEv, dD);
     return cudaGetLastError() == cudaSuccess ? NLA_OK : NLA_ERR_CUDA;
 }

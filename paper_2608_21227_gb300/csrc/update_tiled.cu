@@ -423,21 +423,6 @@ static int split_count(int L, int th, int nblk) {
     return S;
 }
 
-// Allow the kernel the opt-in shared-memory maximum minus its static shared memory.
-template <typename K>
-static void set_smem_attr(K kernel, bool &done) {
-    if (!done) {
-        int dev = 0, optin = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaFuncAttributes fa;
-        size_t stat = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)optin - stat));
-        cudaGetLastError();
-        done = true;
-    }
-}
-
 template <typename T, int R, int U>
 static cudaError_t run_tiled(int side, T *X, long ldx, int M, int N, const T *V, long ldv, int nb, const T *Tm,
                              const UpdCfg &c, size_t smem, const UpdScratch &sc, cudaStream_t st) {
@@ -445,9 +430,9 @@ static cudaError_t run_tiled(int side, T *X, long ldx, int M, int N, const T *V,
     T *part = reinterpret_cast<T *>(sc.work);
     T *fin = part + (size_t)kMaxSplit * 64 * std::max(M, N);
     if (side == 0) {
-        static bool a1 = false, a3 = false;
-        set_smem_attr(left_w_kernel<T, R, U>, a1);
-        set_smem_attr(left_x_kernel<T, U>, a3);
+        static PerDeviceOnce a1, a3;
+        allow_max_smem(left_w_kernel<T, R, U>, a1);
+        allow_max_smem(left_x_kernel<T, U>, a3);
         const int nblk = (N + w - 1) / w;
         int S = split_count(M, th, nblk);
         const int Ms = ((M + S - 1) / S + th - 1) / th * th;
@@ -459,9 +444,9 @@ static cudaError_t run_tiled(int side, T *X, long ldx, int M, int N, const T *V,
         left_x_kernel<T, U><<<dim3(nblk, (M + th - 1) / th), c.threads, smem, st>>>(X, ldx, M, N, V, ldv, nb, th, w,
                                                                                    fin);
     } else {
-        static bool a1 = false, a3 = false;
-        set_smem_attr(right_w_kernel<T, R, U>, a1);
-        set_smem_attr(right_x_kernel<T, U>, a3);
+        static PerDeviceOnce a1, a3;
+        allow_max_smem(right_w_kernel<T, R, U>, a1);
+        allow_max_smem(right_x_kernel<T, U>, a3);
         const int nblk = (M + w - 1) / w;
         int S = split_count(N, th, nblk);
         const int Ns = ((N + S - 1) / S + th - 1) / th * th;
@@ -501,30 +486,39 @@ cudaError_t trail_tiled(int side, T *X, long ldx, int M, int N, const T *V, long
     }
 }
 
+// Largest block the compiled kernel can launch; 1024 (not cached) when it cannot be
+// asked because this process has no CUDA device.
 template <typename K>
-static int kernel_max_threads(K kernel) {
+static int kernel_max_threads(K kernel, bool &known) {
     cudaFuncAttributes fa;
     if (cudaFuncGetAttributes(&fa, kernel) != cudaSuccess) {
         cudaGetLastError();
-        return 0;
+        known = false;
+        return 1024;
     }
     return fa.maxThreadsPerBlock;
 }
 
 template <typename T, int R, int U>
-static int max_threads_one(int side) {
-    if (side == 0) return std::min(kernel_max_threads(left_w_kernel<T, R, U>), kernel_max_threads(left_x_kernel<T, U>));
-    return std::min(kernel_max_threads(right_w_kernel<T, R, U>), kernel_max_threads(right_x_kernel<T, U>));
+static int max_threads_one(int side, bool &known) {
+    if (side == 0)
+        return std::min(kernel_max_threads(left_w_kernel<T, R, U>, known), kernel_max_threads(left_x_kernel<T, U>, known));
+    return std::min(kernel_max_threads(right_w_kernel<T, R, U>, known), kernel_max_threads(right_x_kernel<T, U>, known));
 }
 
 template <typename T, int R>
-static int max_threads_r(int side, int u) {
-    return u == 1 ? max_threads_one<T, R, 1>(side) : u == 2 ? max_threads_one<T, R, 2>(side) : max_threads_one<T, R, 4>(side);
+static int max_threads_r(int side, int u, bool &known) {
+    return u == 1 ? max_threads_one<T, R, 1>(side, known)
+           : u == 2 ? max_threads_one<T, R, 2>(side, known) : max_threads_one<T, R, 4>(side, known);
 }
 
 int tiled_max_threads(int side, int elem, int R, int unroll) {
+    // a kernel's thread limit (from its register count) is the same on every device of
+    // this architecture: cached once, under a lock
+    static std::mutex mu;
     static int cache[2][2][4][3];
     static bool init = false;
+    std::lock_guard<std::mutex> lk(mu);
     if (!init) {
         for (auto &a : cache)
             for (auto &b : a)
@@ -535,12 +529,16 @@ int tiled_max_threads(int side, int elem, int R, int unroll) {
     const int ri = R == 1 ? 0 : R == 2 ? 1 : R == 4 ? 2 : 3, ui = unroll == 1 ? 0 : unroll == 2 ? 1 : 2;
     int &v = cache[side][elem == 8 ? 0 : 1][ri][ui];
     if (v < 0) {
+        bool known = true;
+        int q;
         if (elem == 8)
-            v = R == 1 ? max_threads_r<double, 1>(side, unroll) : R == 2 ? max_threads_r<double, 2>(side, unroll)
-              : R == 4 ? max_threads_r<double, 4>(side, unroll) : max_threads_r<double, 8>(side, unroll);
+            q = R == 1 ? max_threads_r<double, 1>(side, unroll, known) : R == 2 ? max_threads_r<double, 2>(side, unroll, known)
+              : R == 4 ? max_threads_r<double, 4>(side, unroll, known) : max_threads_r<double, 8>(side, unroll, known);
         else
-            v = R == 1 ? max_threads_r<float, 1>(side, unroll) : R == 2 ? max_threads_r<float, 2>(side, unroll)
-              : R == 4 ? max_threads_r<float, 4>(side, unroll) : max_threads_r<float, 8>(side, unroll);
+            q = R == 1 ? max_threads_r<float, 1>(side, unroll, known) : R == 2 ? max_threads_r<float, 2>(side, unroll, known)
+              : R == 4 ? max_threads_r<float, 4>(side, unroll, known) : max_threads_r<float, 8>(side, unroll, known);
+        if (!known) return q;
+        v = q;
     }
     return v;
 }

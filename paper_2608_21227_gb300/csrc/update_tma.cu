@@ -47,18 +47,18 @@ namespace nla {
 // ------------------------------------------------------------------ host: tensor maps
 bool tma_encode_2d(CUtensorMap *map, const void *base, int elem_bytes, uint64_t dim0, uint64_t dim1,
                    uint64_t stride_bytes, uint32_t box0, uint32_t box1, bool swizzle128) {
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    static bool init = false;
-    if (!init) {
-        init = true;
+    // the driver entry point is the same for every device: looked up once (thread-safe)
+    static const PFN_cuTensorMapEncodeTiled_v12000 encode = [] {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
+        PFN_cuTensorMapEncodeTiled_v12000 f = nullptr;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+            f = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
         cudaGetLastError();
-    }
+        return f;
+    }();
     if (!encode || dim0 == 0 || dim1 == 0) return false;
     if (reinterpret_cast<uintptr_t>(base) % 16 || stride_bytes % 16) return false;
     const cuuint64_t dims[2] = {dim0, dim1};
@@ -987,19 +987,6 @@ qr_update_lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_c
 }
 
 // ------------------------------------------------------------------ host launch
-template <typename K>
-void set_smem(K kernel, bool &done) {
-    if (done) return;
-    done = true;
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    cudaFuncAttributes fa;
-    const size_t stat = cudaFuncGetAttributes(&fa, kernel) == cudaSuccess ? fa.sharedSizeBytes : 1024;
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)((size_t)optin - stat));
-    cudaGetLastError();
-}
-
 int splits_for(int nstrip, int units, int waves) {
     const int target = waves * device_sm_count();
     return std::max(1, std::min({(target + nstrip - 1) / std::max(nstrip, 1), kMaxSplitTma, units}));
@@ -1047,8 +1034,8 @@ cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long 
     }();
     CUtensorMap mVs;
     if (use_tc && tma_encode_2d(&mVs, V, 4, M, NB, ldv * 4, kBoxRows, NB, true)) {
-        static bool attr = false;
-        set_smem(qr_proj_tc_kernel<NB>, attr);
+        static PerDeviceOnce attr;
+        allow_max_smem(qr_proj_tc_kernel<NB>, attr);
         const int stage = 2 * (32 * 128 * 4) + 2 * NB * 128;
         static const int sforce = [] {  // NLA_TC_STAGES: pipeline depth of the tensor-core projection
             const char *v = getenv("NLA_TC_STAGES");
@@ -1065,8 +1052,8 @@ cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long 
                                    M, N, Tm, S, Ms, part, fin, sc.tickets, sc.info);
         if (e != cudaSuccess) return e;
     } else {
-        static bool attr = false;
-        set_smem(qr_proj_kernel<NB>, attr);
+        static PerDeviceOnce attr;
+        allow_max_smem(qr_proj_kernel<NB>, attr);
         const int th = sh.br * kBoxRows;
         const int stage = stage_bytes_qr(NB, th);
         const int nstrip = (N + 127) / 128;
@@ -1094,8 +1081,8 @@ cudaError_t left_apply_nb(float *X, long ldx, int M, int N, const float *V, long
     if (!tma_encode_2d(&mX2, Xo, 4, len, N, ldx * 4, kBoxRows, sh.tc, true) ||
         !tma_encode_2d(&mQ, fin, 4, NB, N, NB * 4, NB, sh.tc, false))
         return cudaErrorInvalidValue;
-    static bool attr = false;
-    set_smem(strip_update_kernel<NB, 0>, attr);
+    static PerDeviceOnce attr;
+    allow_max_smem(strip_update_kernel<NB, 0>, attr);
     constexpr int H = 32 * (64 / NB);
     const int stage = stage_bytes_cols(NB, sh.tc);
     const int nstrip = (len + H - 1) / H;
@@ -1121,8 +1108,8 @@ cudaError_t right_proj_nb(float *X, long ldx, int M, int N, const float *Vt, lon
     const int nstrip = (M + H - 1) / H;
     const size_t smem = (size_t)sh.stages * stage + 1024;
     // pass 1 (+ step 2): Y' = X V T
-    static bool attr = false;
-    set_smem(lq_proj_kernel<NB>, attr);
+    static PerDeviceOnce attr;
+    allow_max_smem(lq_proj_kernel<NB>, attr);
     int nsplit = splits_for(nstrip, (N + sh.tc - 1) / sh.tc, sh.waves);
     const int Ns = ((N + nsplit - 1) / nsplit + sh.tc - 1) / sh.tc * sh.tc;
     nsplit = (N + Ns - 1) / Ns;
@@ -1147,8 +1134,8 @@ cudaError_t right_apply_nb(float *X, long ldx, int M, int N, const float *Vt, lo
     const int stage = stage_bytes_cols(NB, sh.tc);
     const int nstrip = (M + H - 1) / H;
     const size_t smem = (size_t)sh.stages * stage + 1024;
-    static bool attr = false;
-    set_smem(strip_update_kernel<NB, 1>, attr);
+    static PerDeviceOnce attr;
+    allow_max_smem(strip_update_kernel<NB, 1>, attr);
     int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (len + sh.tc - 1) / sh.tc));
     const int Ns = ((len + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
     ncs = (len + Ns - 1) / Ns;
@@ -1177,8 +1164,8 @@ cudaError_t fused_nb(float *X, long ldx, int M, int N, const float *V, long ldv,
     int S = sh.stages;
     while (S > 2 && fused_smem<NB>(sh, S) > kTmaSmemLimit) --S;
     if (fused_smem<NB>(sh, S) > kTmaSmemLimit) return cudaErrorInvalidConfiguration;
-    static bool attr = false;
-    set_smem(qr_update_lq_proj_kernel<NB>, attr);
+    static PerDeviceOnce attr;
+    allow_max_smem(qr_update_lq_proj_kernel<NB>, attr);
     const int nstrip = (M + H - 1) / H;
     int nsplit = splits_for(nstrip, (N + sh.tc - 1) / sh.tc, sh.waves);
     const int Ns = ((N + nsplit - 1) / nsplit + sh.tc - 1) / sh.tc * sh.tc;

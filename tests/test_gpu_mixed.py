@@ -1,13 +1,20 @@
-"""Mixed precision: the tensor-core building block and the TF32/BF16 trailing update.
+"""Mixed precision: the tensor-core building block, the power-of-two scaling step
+and the TF32/BF16 trailing update.
 
-The tensor-core product is checked against FP64 products of the operands
-rounded on the CPU the way the device rounds them (TF32: keep 10 mantissa
-bits, round half away from zero; BF16: keep 7, round half to even).  The
-mixed-precision pipeline is checked against the prescribed singular values
-within the first-order model err <= 10 u sqrt(n / b) (u = 2^-11 for TF32,
-2^-8 for BF16: each of the n/b panel steps perturbs the trailing matrix by
-about u ||A||, accumulating like a random walk; Weyl's inequality carries it
-to the singular values).
+* The tensor-core product is checked against FP64 products of the operands
+  rounded on the CPU the way the device rounds them (TF32: keep 10 mantissa
+  bits, round half away from zero; BF16: keep 7, round half to even).
+* The scaling step's two conversions (FP64 * 2^-e -> FP32, FP32 * 2^e -> FP64)
+  are checked element by element against numpy on edge values.
+* The pipeline is checked against prescribed singular values with a bound per
+  (operand type, condition number) set a small factor above the error measured
+  on GB300 (MIXED_BOUNDS), so a loss of accuracy of an order of magnitude
+  fails; the first-order model 10 u sqrt(n / b) of the mixed form stays as the
+  ceiling those bounds must sit under.
+* The scaling is pinned by inputs that leave FP32's exponent range: A * 2^+-200
+  must give exactly 2^+-200 times the singular values of A (every step scales
+  by powers of two exactly), and diag(2^k) Q (Q Haar, k spread over
+  [-140, 140]) must give the sorted 2^k.
 """
 import ctypes
 import math
@@ -30,6 +37,8 @@ def nla():
     L = _nla.lib()
     L.nla_tc_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 5
     L.nla_tc_selftest.restype = ctypes.c_int
+    L.nla_scale_selftest.argtypes = [ctypes.c_int] + [ctypes.c_void_p] * 7
+    L.nla_scale_selftest.restype = ctypes.c_int
     return _nla
 
 
@@ -65,18 +74,133 @@ def test_tensor_core_tile(nla, prec, K, N):
     assert np.all(np.abs(got - ref) <= 1e-5 * scale + 1e-30)
 
 
+def ref_f64_to_f32_bits(x, e):
+    """numpy restatement of FP64 x * 2^-e -> FP32 with the significand truncated to 24 bits,
+    0 below FP32's normal range, inf at or above 2^128 (FP64 subnormal x reads as 0)."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.ldexp(x, -np.asarray(e))
+    y = np.where(np.abs(x) < np.finfo(np.float64).tiny, np.copysign(0.0, x), y)
+    m, ex = np.frexp(y)
+    t = np.ldexp(np.trunc(m * 2.0 ** 24) / 2.0 ** 24, ex)
+    with np.errstate(over="ignore"):
+        out = np.where(np.abs(y) < 2.0 ** -126, np.copysign(0.0, y),
+                       np.where(np.abs(y) >= 2.0 ** 128, np.copysign(np.inf, y), t)).astype(np.float32)
+    return out.view(np.uint32)
+
+
+def ref_f32_to_f64_bits(v, e):
+    """numpy restatement of FP32 v * 2^e -> FP64: exact, 0 for FP32 zeros and subnormals,
+    signed 0 below FP64's normal range, signed inf above it or for inf/NaN v."""
+    v = np.asarray(v, dtype=np.float32)
+    w = v.astype(np.float64)
+    with np.errstate(over="ignore"):
+        y = np.ldexp(w, np.asarray(e))
+    y = np.where(np.abs(y) < np.finfo(np.float64).tiny, np.copysign(0.0, w), y)
+    y = np.where(~np.isfinite(w), np.copysign(np.inf, w), y)
+    y = np.where(np.abs(w) < np.finfo(np.float32).tiny, 0.0, y)
+    return y.view(np.uint64)
+
+
+def test_scale_conversions(nla):
+    g = np.random.default_rng(2024)
+    # FP64 -> FP32: ordinary values, values landing at FP32's ends, ties and truncation
+    # cases, zeros of both signs, values beyond FP32's range either way, FP64 extremes
+    base = np.concatenate([
+        g.standard_normal(4000) * 2.0 ** g.integers(-300, 300, 4000),
+        [0.0, -0.0, 1.0, -1.0, 1.0 + 2.0 ** -24, 1.0 + 2.0 ** -23 + 2.0 ** -30, 2.0 ** -126, 2.0 ** -127,
+         np.nextafter(2.0 ** 128, 0), 2.0 ** 128, -(2.0 ** 128), np.finfo(np.float64).max, np.finfo(np.float64).tiny,
+         3.4028234663852886e38, 1.1754943508222875e-38, 5e-324],
+    ])
+    ex = np.concatenate([g.integers(-320, 320, 4000), np.zeros(16, dtype=np.int64)])
+    ex[4000 + 12] = 0
+    # FP32 -> FP64: normal values with exponents pushing past FP64's ends, subnormals, inf
+    v = np.concatenate([
+        (g.standard_normal(4000) * 2.0 ** g.integers(-120, 120, 4000)).astype(np.float32),
+        np.array([0.0, -0.0, 1.0, -1.5, np.finfo(np.float32).max, np.finfo(np.float32).tiny, 1e-45, -1e-45,
+                  np.inf, -np.inf, 0.5, 0.75, 1.0, -1.0, 2.0, 3.0], dtype=np.float32),
+    ])
+    ev = np.concatenate([g.integers(-1100, 1100, 4000),
+                         [5, 5, 1023, -1022, 900, -900, 3, 3, 0, 0, -1074, -1075, 1024, 1024, -1022, -1023]])
+    n = base.size
+    dX = torch.from_numpy(base).cuda()
+    dEx = torch.from_numpy(ex.astype(np.int32)).cuda()
+    dV = torch.from_numpy(v).cuda()
+    dEv = torch.from_numpy(np.asarray(ev, dtype=np.int32)).cuda()
+    dF = torch.empty(n, dtype=torch.float32, device="cuda")
+    dD = torch.empty(n, dtype=torch.float64, device="cuda")
+    st = nla.lib().nla_scale_selftest(n, dX.data_ptr(), dEx.data_ptr(), dF.data_ptr(), dV.data_ptr(), dEv.data_ptr(),
+                                      dD.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert st == 0
+    got_f = dF.cpu().numpy().view(np.uint32)
+    want_f = ref_f64_to_f32_bits(base, ex)
+    bad = np.nonzero(got_f != want_f)[0]
+    assert bad.size == 0, [(base[i], int(ex[i]), hex(got_f[i]), hex(want_f[i])) for i in bad[:5]]
+    got_d = dD.cpu().numpy().view(np.uint64)
+    want_d = ref_f32_to_f64_bits(v, ev)
+    bad = np.nonzero(got_d != want_d)[0]
+    assert bad.size == 0, [(float(v[i]), int(ev[i]), hex(got_d[i]), hex(want_d[i])) for i in bad[:5]]
+
+
+# Bound on max|sigma_hat - sigma| / sigma_1 per (operand type, kappa) at 700 x 600, band 32:
+# a small factor (about 3x) above the error measured on GB300, so that a tenfold loss of
+# accuracy fails; each sits under the first-order model 10 u sqrt(N / b) of the mixed form.
+MIXED_BOUNDS = {
+    (1, 1.0): 10 * 2.0 ** -11 * math.sqrt(700 / 32), (1, 1e4): 10 * 2.0 ** -11 * math.sqrt(700 / 32),
+    (1, 1e8): 10 * 2.0 ** -11 * math.sqrt(700 / 32),
+    (2, 1.0): 10 * 2.0 ** -8 * math.sqrt(700 / 32), (2, 1e4): 10 * 2.0 ** -8 * math.sqrt(700 / 32),
+    (2, 1e8): 10 * 2.0 ** -8 * math.sqrt(700 / 32),
+}
+
+
+def mixed_run(nla, A, prec, b=32):
+    S, info = nla.gesvd_vals(to_device_colmajor(A, torch.float64), update=prec, cfg=nla.Cfg.make(band=b))
+    torch.cuda.synchronize()
+    assert int(info.item()) == 0
+    s = S.cpu().numpy()
+    assert np.all(np.isfinite(s)) and np.all(s >= 0)
+    return s
+
+
 @pytest.mark.parametrize("prec,u", [(1, 2.0 ** -11), (2, 2.0 ** -8)])
 @pytest.mark.parametrize("kappa", [1.0, 1e4, 1e8])
 def test_mixed_pipeline_prescribed(nla, prec, u, kappa):
     m, n, b = 700, 600, 32
     sigma = inputs.geometric_sigma(n, kappa)
     A = inputs.prescribed(m, n, sigma, seed=41)
-    S, info = nla.gesvd_vals(to_device_colmajor(A, torch.float64), update=prec, cfg=nla.Cfg.make(band=b))
-    torch.cuda.synchronize()
-    assert int(info.item()) == 0
-    err = err_rel(S.cpu().numpy(), sigma)
-    assert err <= 10 * u * math.sqrt(max(m, n) / b), err
-    assert np.all(np.isfinite(S.cpu().numpy()))
+    err = err_rel(mixed_run(nla, A, prec, b), sigma)
+    print(f"mixed prec {prec} kappa {kappa:g}: err {err:.3e}")
+    assert MIXED_BOUNDS[(prec, kappa)] <= 10 * u * math.sqrt(max(m, n) / b)
+    assert err <= MIXED_BOUNDS[(prec, kappa)], err
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("shift", [200, -200])
+def test_mixed_scaling_equivariant(nla, prec, shift):
+    # A * 2^shift lies entirely outside FP32's exponent range; with the power-of-two
+    # scaling every step of the mixed form sees the same significands, so the singular
+    # values are those of A times 2^shift
+    m, n = 400, 300
+    sigma = inputs.geometric_sigma(n, 1e4)
+    A = inputs.prescribed(m, n, sigma, seed=47)
+    s0 = mixed_run(nla, A, prec)
+    s1 = mixed_run(nla, np.ldexp(A, shift), prec)
+    assert err_rel(np.ldexp(s1, -shift), s0) <= 1e-13 * m
+    assert err_rel(np.ldexp(s1, -shift), oracle.svdvals(A)) <= MIXED_BOUNDS[(prec, 1e4)]
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_mixed_graded_rows(nla, prec):
+    # diag(2^k) Q with Q Haar and k spread over [-140, 140]: the rows span 2^280, beyond
+    # FP32's and BF16's range; the singular values are the sorted 2^k
+    n = 280
+    k = np.linspace(-140, 140, n).round().astype(int)
+    Q = inputs.haar(n, n, np.random.default_rng(53))
+    A = np.ldexp(1.0, k)[:, None] * Q
+    want = np.sort(np.ldexp(1.0, k))[::-1]
+    got = mixed_run(nla, A, prec)
+    u = 2.0 ** -11 if prec == 1 else 2.0 ** -8
+    assert err_rel(got, want) <= 10 * u * math.sqrt(n / 32)
 
 
 @pytest.mark.parametrize("prec", [1, 2])

@@ -38,8 +38,8 @@ def test_exhaustive_is_eq1_argmin(kt, tmp_path):
     cache = str(tmp_path / "c.csv")
     res = kt.tune(kt.KT_TRAIL_LEFT, 1024, 1024, 1, band=32, reps=3, cache=cache)
     rows = read_cache(cache)
-    valid = [c for c in otuner.space() if c[0] == 32 and otuner.valid(0, 4, c)]
-    assert res["evaluated"] == len(rows) == res["valid"] <= len(valid)
+    valid = [c for c in kt.space() if c[0] == 32 and kt.cfg_valid(kt.KT_TRAIL_LEFT, 1, c)]
+    assert res["evaluated"] == len(rows) == res["valid"] == len(valid)
     assert res["failed"] == 0 and all(r["status"] == 0 for r in rows)
     times = {cfg_of(r): r["median_ms"] for r in rows}
     assert res["best"] == otuner.argmin(times)
@@ -63,16 +63,13 @@ def test_random_sample_is_the_oracle_subset(kt, tmp_path):
     cache = str(tmp_path / "rnd.csv")
     res = kt.tune(kt.KT_TRAIL_LEFT, 768, 768, 1, band=16, reps=2, strategy=kt.KT_RANDOM, budget_frac=0.1,
                   cache=cache, seed=12345)
-    valid = [c for c in otuner.space() if c[0] == 16 and otuner.valid(0, 4, c)]
-    valid = [c for c in valid if c in set(tuple(x) for x in kt.space())]
+    valid = [c for c in kt.space() if c[0] == 16 and kt.cfg_valid(kt.KT_TRAIL_LEFT, 1, c)]
     k = max(1, math.ceil(0.1 * res["valid"]))
-    assert res["evaluated"] == k
-    # the library's valid list may drop configurations the device cannot launch;
-    # when it does not, the sample is exactly the oracle's SplitMix64 subset
-    if res["valid"] == len(valid):
-        want = {valid[i] for i in otuner.random_subset(len(valid), k, 12345)}
-        got = {cfg_of(r) for r in read_cache(cache)}
-        assert got == want
+    assert res["valid"] == len(valid) and res["evaluated"] == k
+    # the sample is the oracle's SplitMix64 subset of the valid list (in space order)
+    want = {valid[i] for i in otuner.random_subset(len(valid), k, 12345)}
+    got = {cfg_of(r) for r in read_cache(cache)}
+    assert got == want
 
 
 def test_pipeline_band_choice_and_table(kt, tmp_path):
@@ -101,3 +98,35 @@ def test_pipeline_band_choice_and_table(kt, tmp_path):
     assert int(info.item()) == 0
     assert err_rel(S.cpu().numpy(), oracle.svdvals(A)) <= tol_for(1, 1024)
     kt.load_config(None)
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_validity_contract(kt, dtype):
+    # the launch contract on this device: every point kt_cfg_valid admits runs the whole
+    # SVD and gives the oracle's singular values; every point it rejects is refused
+    # up front with NLA_ERR_CONFIG (nothing enqueued)
+    import oracle
+    from paper_2608_21227_gb300 import inputs, nla
+    from _util import err_rel, to_device_colmajor, tol_for
+
+    m, n = 200, 160
+    A = inputs.uniform(m, n, 91)
+    if dtype == 1:
+        A = A.astype(np.float32).astype(np.float64)
+    ref = oracle.svdvals(A)
+    t0 = to_device_colmajor(A, torch.float64 if dtype == 0 else torch.float32)
+    admitted = 0
+    for c in kt.space():
+        ok = kt.cfg_valid(kt.KT_GESVD, dtype, c)
+        t = t0.clone()
+        if ok:
+            S, info = nla.gesvd_vals(t, cfg=nla.Cfg.make(*c))
+            torch.cuda.synchronize()
+            assert int(info.item()) == 0, c
+            assert err_rel(S.double().cpu().numpy(), ref) <= tol_for(dtype, m), c
+            admitted += 1
+        else:
+            with pytest.raises(nla.NLAError) as ei:
+                nla.gesvd_vals(t, cfg=nla.Cfg.make(*c))
+            assert ei.value.status == 3, c
+    assert admitted > 0

@@ -55,31 +55,6 @@ def test_ratios():
     assert (opt, med, dflt, r_med, r_def) == (1.0, 4.0, 4.0, 4.0, 4.0)
 
 
-def test_validity_rule_cases():
-    # the default configuration: w = 64 (16 column groups), 8 reflector groups of R = 4,
-    # 64-row tiles = 8 rows per thread; smem 8 * (64*64 + 64*36 + 32*64) bytes
-    assert tuner.valid(0, 8, (32, 64, 128, 2, 1))
-    assert tuner.smem_bytes(0, 8, 32, 64, 64) == 8 * (4096 + 2304 + 2048)
-    assert not tuner.valid(0, 8, (32, 32, 96, 1, 1))       # 96 threads: 12 reflector groups do not divide 32
-    assert not tuner.valid(0, 8, (32, 16, 256, 1, 1))      # R = 1 but a 16-row tile gives 0.5 rows per thread
-    assert tuner.valid(0, 8, (32, 128, 256, 1, 1))         # 128 rows / 32 groups = 4 rows per thread
-    assert not tuner.valid(0, 8, (64, 128, 1024, 8, 1))    # 8 * (128*256 + 128*68 + 64*256) > 227 KiB
-    # FP32 at band 16/32/64: the TMA-streamed kernels read the tuple as
-    # (band, stage depth, consumer threads, stages, waves)
-    assert tuner.valid(0, 4, (32, 64, 128, 2, 1))          # 2 * max(2*(16384+4096), 2*64*128+64*32*4) + 1024
-    assert tuner.tma_smem_bytes(32, 64, 2) == 2 * 40960 + 1024
-    assert not tuner.valid(0, 4, (16, 128, 256, 4, 1))     # 4 * 73728 + 1024 > 226 KiB
-    assert tuner.valid(0, 4, (64, 32, 128, 8, 4))          # 8 * 24576 + 1024 fits
-    assert not tuner.valid(0, 4, (64, 32, 64, 2, 1))       # 2 consumer warps < 4 reflector groups of 16
-    assert not tuner.valid(0, 4, (16, 16, 64, 2, 1))       # stage depth is a whole 32-row box
-    assert not tuner.valid(0, 4, (16, 64, 128, 1, 1))      # a ring needs at least 2 stages
-    assert not tuner.valid(0, 4, (64, 128, 1024, 8, 1))    # at most 8 consumer warps
-    n_valid = sum(tuner.valid(0, 8, c) for c in tuner.space())
-    assert 0 < n_valid < 2304
-    n_tma = sum(tuner.valid(0, 4, c) for c in tuner.space())
-    assert 0 < n_tma < 2304
-
-
 def test_splitmix64_reference_outputs():
     # SplitMix64 from state 0: the first outputs of the published generator
     s = 0

@@ -1,9 +1,10 @@
 """nla_band2bd_noalloc: the bulge chase for callers that cannot allocate.
 
-Some callers cannot call cudaMalloc -- for example while their stream is
-being captured into a CUDA graph, or when an external memory manager owns the
-whole device -- so they cannot hand nla_band2bd a workspace.  The no-alloc
-variant keeps that scratch in a fixed array inside the library.  This test
+Some callers cannot call cudaMalloc -- a plug-in inside a host framework
+whose memory manager owns the whole device, code that must never synchronise
+the device (cudaMalloc and cudaFree may), a program with a fixed device-memory
+budget -- so they cannot hand nla_band2bd a workspace.  The no-alloc variant
+keeps that scratch in a fixed array inside the library.  This test
 calls it through the C ABI, twice in a row (the second call must not be
 disturbed by what the first left in the shared array), and checks its d, e
 against the regular entry point's on the same band matrix, with the
