@@ -61,8 +61,19 @@ typedef enum { NLA_F64 = 0, NLA_F32 = 1 } nla_dtype;
  * the matrix dtype.  TF32 / BF16 round the (power-of-two column-scaled)
  * operands to that type and run the contraction on the tensor cores with FP32
  * accumulation; the matrix itself stays in its dtype, and panel
- * factorisation, bulge chasing and the singular-value solve are unchanged. */
-typedef enum { NLA_UPD_NATIVE = 0, NLA_UPD_TF32 = 1, NLA_UPD_BF16 = 2 } nla_update;
+ * factorisation, bulge chasing and the singular-value solve are unchanged.
+ * TF32X3 / BF16X3 are the compensated forms: each operand is split into a
+ * rounded high part and a rounded remainder and every product is formed from
+ * three tensor-core products (hi*hi + hi*lo + lo*hi), which keeps about twice
+ * the operand type's precision at three times the tensor-core work (the
+ * contraction is memory-bound either way).  All four need an FP64 matrix. */
+typedef enum {
+    NLA_UPD_NATIVE = 0,
+    NLA_UPD_TF32 = 1,
+    NLA_UPD_BF16 = 2,
+    NLA_UPD_TF32X3 = 3,
+    NLA_UPD_BF16X3 = 4
+} nla_update;
 
 /* Launch configuration of the trailing-update kernels (Algorithm 2's tunable
  * parameters, Section 5.2 search-space table, re-expressed for this GPU):

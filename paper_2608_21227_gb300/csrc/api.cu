@@ -458,7 +458,7 @@ void step_cfgs(const Stage1Plan &p, int Mt, int Nt, nla::UpdCfg &l, nla::UpdCfg 
 
 nla_status check_common(nla_dtype dt, const nla_opts *opts) {
     if (dt != NLA_F64 && dt != NLA_F32) return fail(NLA_ERR_ARG, "unknown dtype %d", (int)dt);
-    if (opts && (opts->update < NLA_UPD_NATIVE || opts->update > NLA_UPD_BF16))
+    if (opts && (opts->update < NLA_UPD_NATIVE || opts->update > NLA_UPD_BF16X3))
         return fail(NLA_ERR_ARG, "unknown update precision %d", (int)opts->update);
     if (opts && opts->update != NLA_UPD_NATIVE && dt != NLA_F64)
         return fail(NLA_ERR_ARG, "TF32/BF16 trailing updates are defined for FP64 matrices");

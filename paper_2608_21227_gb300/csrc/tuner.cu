@@ -416,10 +416,13 @@ struct TableSwap {
 
 // Verification tolerance of a pipeline-level candidate against the default
 // configuration's singular values (relative to the largest): twice the acceptance
-// bound of the dtype, or for the TF32 / BF16 forms the first-order model 10 u sqrt(N/16).
+// bound of the dtype, or for the TF32 / BF16 forms the first-order model 10 u sqrt(N/16)
+// (u = 2^-11, 2^-8; the compensated BF16X3 form u = 2^-16, TF32X3 the FP32 bound).
 double pipeline_tol(const kt_problem &p, int N) {
     if (p.update == NLA_UPD_TF32) return 10.0 * std::ldexp(1.0, -11) * std::sqrt(N / 16.0);
     if (p.update == NLA_UPD_BF16) return 10.0 * std::ldexp(1.0, -8) * std::sqrt(N / 16.0);
+    if (p.update == NLA_UPD_BF16X3) return 10.0 * std::ldexp(1.0, -16) * std::sqrt(N / 16.0);
+    if (p.update == NLA_UPD_TF32X3) return 2.0 * 5e-6 * N;
     return 2.0 * (p.dtype == NLA_F64 ? 1e-12 : 5e-6) * N;
 }
 

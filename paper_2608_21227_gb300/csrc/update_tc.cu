@@ -1,7 +1,8 @@
 // update_tc.cu -- mixed-precision trailing update on the 5th-generation tensor
-// cores: FP64 matrix, TF32 or BF16 operands, FP32 accumulation in TMEM, exact
-// power-of-two scaling of the converted operands (the trailing update of
-// Algorithm 2 with the mixed-precision form of the contraction).
+// cores: FP64 matrix, TF32 or BF16 operands (or their compensated three-product
+// forms TF32X3 / BF16X3), FP32 accumulation in TMEM, exact power-of-two scaling of
+// the converted operands (the trailing update of Algorithm 2 with the
+// mixed-precision form of the contraction).
 //
 // Two launches per side (as in the SIMT path): step 1 on a grid of
 // (128-wide strips) x (splits of the reduction dimension), the last block of a
@@ -50,12 +51,19 @@ constexpr int kStrip = 128;       // strip width = UMMA M
 constexpr int kKt = 32;           // rows (QR) / columns (LQ) of X per step-1 tile
 constexpr int kTmemCols = 256;    // self-test accumulator columns
 
+// Operand types.  The compensated forms (TF32X3, BF16X3) split each scaled FP32
+// operand v into hi = round(v) and lo = round(v - hi) in the operand type and form
+// every product from three MMAs, hi*hi + hi*lo + lo*hi (the lo*lo term and lo's own
+// rounding are below u^2 relative; Ootomo & Yokota 2022), so each product keeps about
+// twice the operand type's significand bits.
 template <int PREC>
 struct Prec;
 template <>
 struct Prec<NLA_UPD_TF32> {
     static constexpr int es = 4;
     static constexpr uint32_t fmt = 2;
+    static constexpr bool split = false;
+    NLA_DEV static float round(float v) { return __uint_as_float(tc::to_tf32(v)); }
     NLA_DEV static void put(unsigned char *base, uint32_t off, float v) {
         *reinterpret_cast<uint32_t *>(base + off) = tc::to_tf32(v);
     }
@@ -65,11 +73,30 @@ template <>
 struct Prec<NLA_UPD_BF16> {
     static constexpr int es = 2;
     static constexpr uint32_t fmt = 1;
+    static constexpr bool split = false;
+    NLA_DEV static float round(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
     NLA_DEV static void put(unsigned char *base, uint32_t off, float v) {
         *reinterpret_cast<uint16_t *>(base + off) = tc::to_bf16(v);
     }
     NLA_DEV static void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) { tc::mma_bf16(d, a, b, id, acc); }
 };
+template <>
+struct Prec<NLA_UPD_TF32X3> : Prec<NLA_UPD_TF32> {
+    static constexpr bool split = true;
+};
+template <>
+struct Prec<NLA_UPD_BF16X3> : Prec<NLA_UPD_BF16> {
+    static constexpr bool split = true;
+};
+
+// Store operand v at byte offset `off` of the hi tile (and, for the compensated
+// forms, its remainder at the same offset of the lo tile).
+template <int PREC>
+NLA_DEV void put_op(unsigned char *hi, unsigned char *lo, uint32_t off, float v) {
+    using P = Prec<PREC>;
+    P::put(hi, off, v);
+    if constexpr (P::split) P::put(lo, off, v - P::round(v));
+}
 
 // power-of-two scale exponent: x * 2^-e lies in [0.5, 1) for the largest |x|
 NLA_DEV int scale_exp(double mx) {
@@ -133,15 +160,25 @@ NLA_DEV void drain_after_failure(TcShared *sh) {
     if (sh->fail && sh->last_bar >= 0) tc::mbar_wait(&sh->mbar[sh->last_bar], sh->last_parity, nullptr);
 }
 
-// Issue `count` MMAs of 32 K-bytes each (one thread).
+// Issue the MMAs of one product over kbytes of K, 32 K-bytes each (one thread).
 template <int PREC>
-NLA_DEV void issue(uint32_t d, const unsigned char *A, int arowbytes, const unsigned char *B, int browbytes,
-                   int kbytes, uint32_t id, bool accumulate_first) {
+NLA_DEV void issue1(uint32_t d, const unsigned char *A, int arowbytes, const unsigned char *B, int browbytes,
+                    int kbytes, uint32_t id, bool accumulate_first) {
     const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(B);
     for (int kk = 0; kk < kbytes / 32; ++kk) {
         uint64_t ad = tc::sdesc(a0 + kk * 256, 128, 8 * arowbytes);
         uint64_t bd = tc::sdesc(b0 + kk * 256, 128, 8 * browbytes);
         Prec<PREC>::mma(d, ad, bd, id, (kk > 0 || accumulate_first) ? 1u : 0u);
+    }
+}
+// D (+)= A B^T; the compensated forms add the hi*lo and lo*hi products (Al, Bl: lo tiles).
+template <int PREC>
+NLA_DEV void issue(uint32_t d, const unsigned char *A, const unsigned char *Al, int arowbytes, const unsigned char *B,
+                   const unsigned char *Bl, int browbytes, int kbytes, uint32_t id, bool accumulate_first) {
+    issue1<PREC>(d, A, arowbytes, B, browbytes, kbytes, id, accumulate_first);
+    if constexpr (Prec<PREC>::split) {
+        issue1<PREC>(d, A, arowbytes, Bl, browbytes, kbytes, id, true);
+        issue1<PREC>(d, Al, arowbytes, B, browbytes, kbytes, id, true);
     }
 }
 
@@ -180,7 +217,7 @@ __global__ void __launch_bounds__(128) tc_selftest_kernel(const float *A, const 
     tc::fence_after_sync();
     const uint32_t tbase = sh->tmem_base;
     if (tid == 0) {
-        issue<PREC>(tbase, As, rowbytes, Bs, rowbytes, rowbytes, tc::idesc(P::fmt, 128, N), false);
+        issue1<PREC>(tbase, As, rowbytes, Bs, rowbytes, rowbytes, tc::idesc(P::fmt, 128, N), false);
         tc::mma_commit(&sh->mbar[0]);
         sh->last_bar = 0;
         sh->last_parity = 0;
@@ -220,9 +257,12 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ int sh_last;
     const int es = P::es, rb1 = kKt * es;
+    constexpr int nsp = P::split ? 2 : 1;                    // hi (and lo) copies of each tile
     unsigned char *A1 = sm;                                  // 2 x [128 x kKt]  X tile (strip line x K)
     unsigned char *B1 = A1 + 2 * kStrip * rb1;               // 2 x [64 x kKt]   V tile (reflector x K)
-    int *ex1 = reinterpret_cast<int *>(B1 + 2 * 64 * rb1);   // 2 x 128
+    unsigned char *A1l = B1 + 2 * 64 * rb1;                  // lo copies (compensated forms)
+    unsigned char *B1l = A1l + (nsp - 1) * 2 * kStrip * rb1;
+    int *ex1 = reinterpret_cast<int *>(B1l + (nsp - 1) * 2 * 64 * rb1);  // 2 x 128
     int *lmax = ex1 + 2 * kStrip;                            // 2 x 128 biased exponents
     TcShared *sh = reinterpret_cast<TcShared *>(lmax + 2 * kStrip);
     float *Wsh = reinterpret_cast<float *>(sm);              // reused after the MMAs: nbp x 128
@@ -296,7 +336,8 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
                     else
                         v = g > n ? V[n + (long)g * ldv] : (g == n ? 1.0 : 0.0);
                 }
-                P::put(B1 + buf * 64 * rb1, tc::kmajor_off(n, k, es, rb1), f64_scaled_to_f32(v, 0));
+                put_op<PREC>(B1 + buf * 64 * rb1, B1l + buf * 64 * rb1, tc::kmajor_off(n, k, es, rb1),
+                             f64_scaled_to_f32(v, 0));
             }
             if (SIDE == 0) {
 #pragma unroll
@@ -304,7 +345,8 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
                     const int mc = warp * 16 + c;
                     const int e = tile_exp_from_biased(__reduce_max_sync(0xffffffffu, f64_biased_exp(xv[c])));
                     if (lane == 0) ex1[buf * kStrip + mc] = e;
-                    P::put(A1 + buf * kStrip * rb1, tc::kmajor_off(mc, lane, es, rb1), f64_scaled_to_f32(xv[c], e));
+                    put_op<PREC>(A1 + buf * kStrip * rb1, A1l + buf * kStrip * rb1, tc::kmajor_off(mc, lane, es, rb1),
+                                 f64_scaled_to_f32(xv[c], e));
                 }
             } else {
                 __syncthreads();
@@ -312,14 +354,16 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
                 if (h == 0) ex1[buf * kStrip + m] = e;
 #pragma unroll
                 for (int i = 0; i < 16; ++i)
-                    P::put(A1 + buf * kStrip * rb1, tc::kmajor_off(m, h * 16 + i, es, rb1), f64_scaled_to_f32(xv[i], e));
+                    put_op<PREC>(A1 + buf * kStrip * rb1, A1l + buf * kStrip * rb1,
+                                 tc::kmajor_off(m, h * 16 + i, es, rb1), f64_scaled_to_f32(xv[i], e));
             }
             tc::fence_async_smem();
             tc::fence_before_sync();
             __syncthreads();
             tc::fence_after_sync();
             if (tid == 0) {
-                issue<PREC>(tbase + buf * 64, A1 + buf * kStrip * rb1, rb1, B1 + buf * 64 * rb1, rb1, rb1, id1, false);
+                issue<PREC>(tbase + buf * 64, A1 + buf * kStrip * rb1, A1l + buf * kStrip * rb1, rb1,
+                            B1 + buf * 64 * rb1, B1l + buf * 64 * rb1, rb1, rb1, id1, false);
                 tc::mma_commit(&sh->mbar[buf]);
                 sh->last_bar = buf;
                 sh->last_parity = (t >> 1) & 1;
@@ -420,9 +464,12 @@ tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__rest
     using P = Prec<PREC>;
     extern __shared__ __align__(1024) unsigned char sm[];
     const int es = P::es, rb3 = nbp * es;
+    constexpr int nsp = P::split ? 2 : 1;
     unsigned char *Aop = sm;                         // [128 x nbp]
     unsigned char *Bop = Aop + kStrip * rb3;         // [128 x nbp]
-    int *exs = reinterpret_cast<int *>(Bop + kStrip * rb3);   // 128 strip-line exponents
+    unsigned char *Aopl = Bop + kStrip * rb3;        // lo copies (compensated forms)
+    unsigned char *Bopl = Aopl + (nsp - 1) * kStrip * rb3;
+    int *exs = reinterpret_cast<int *>(Bopl + (nsp - 1) * kStrip * rb3);  // 128 strip-line exponents
     float *lmax = reinterpret_cast<float *>(exs + kStrip);    // 2 x 128
     TcShared *sh = reinterpret_cast<TcShared *>(lmax + 2 * kStrip);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -453,9 +500,10 @@ tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__rest
         if (hf == 0) exs[l] = e + (l < lw ? finexp[L0 + l] : 0);
         // QR: B operand rows = strip columns (N dim), K = reflectors; LQ: A operand rows = strip rows
         unsigned char *dst = SIDE == 0 ? Bop : Aop;
+        unsigned char *dstl = SIDE == 0 ? Bopl : Aopl;
         for (int k = hf; k < nbp; k += 2) {
             const float v = (l < lw && k < nb) ? fin[(size_t)k * Lext + L0 + l] : 0.f;
-            P::put(dst, tc::kmajor_off(l, k, es, rb3), ldexpf(v, -e));
+            put_op<PREC>(dst, dstl, tc::kmajor_off(l, k, es, rb3), ldexpf(v, -e));
         }
     }
     // V block of this tile: QR -> rows T0.. of V (A operand); LQ -> V(T0 + n, k) (B operand)
@@ -474,7 +522,8 @@ tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__rest
             else
                 v = g > k ? V[k + (long)g * ldv] : (g == k ? 1.0 : 0.0);
         }
-        P::put(SIDE == 0 ? Aop : Bop, tc::kmajor_off(r, k, es, rb3), f64_scaled_to_f32(v, 0));
+        put_op<PREC>(SIDE == 0 ? Aop : Bop, SIDE == 0 ? Aopl : Bopl, tc::kmajor_off(r, k, es, rb3),
+                     f64_scaled_to_f32(v, 0));
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -482,7 +531,7 @@ tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__rest
     tc::fence_after_sync();
     const uint32_t tbase = sh->tmem_base;
     if (tid == 0) {
-        issue<PREC>(tbase, Aop, rb3, Bop, rb3, rb3, tc::idesc(P::fmt, 128, 128), false);
+        issue<PREC>(tbase, Aop, Aopl, rb3, Bop, Bopl, rb3, rb3, tc::idesc(P::fmt, 128, 128), false);
         tc::mma_commit(&sh->mbar[0]);
         sh->last_bar = 0;
         sh->last_parity = 0;
@@ -521,20 +570,21 @@ tc_x_kernel(double *__restrict__ X, long ldx, int M, int N, const double *__rest
     if (warp == 0) tc::tmem_dealloc(tbase, 128);
 }
 
-size_t tc_w_smem(int es) {
+size_t tc_w_smem(int es, int nsp) {
     const size_t rb1 = (size_t)kKt * es;
-    return std::max((size_t)2 * kStrip * rb1 + 2 * 64 * rb1 + 2 * kStrip * 4 + 2 * kStrip * 8 + sizeof(TcShared) + 64,
+    return std::max((size_t)nsp * (2 * kStrip * rb1 + 2 * 64 * rb1) + 2 * kStrip * 4 + 2 * kStrip * 8 +
+                        sizeof(TcShared) + 64,
                     (size_t)64 * kStrip * 4 + kStrip * 4 + 64);
 }
-size_t tc_x_smem(int es, int nbp) {
-    return (size_t)2 * kStrip * nbp * es + kStrip * 4 + 2 * kStrip * 4 + sizeof(TcShared) + 64;
+size_t tc_x_smem(int es, int nbp, int nsp) {
+    return (size_t)nsp * 2 * kStrip * nbp * es + kStrip * 4 + 2 * kStrip * 4 + sizeof(TcShared) + 64;
 }
 
 template <int PREC, int SIDE>
 cudaError_t launch_tc(double *X, long ldx, int M, int N, const double *V, long ldv, int nb, const double *Tm,
                       const UpdScratch &sc, int *info, cudaStream_t st) {
     const int nbp = nb <= 32 ? 32 : 64;
-    const int es = Prec<PREC>::es;
+    const int es = Prec<PREC>::es, nsp = Prec<PREC>::split ? 2 : 1;
     static PerDeviceOnce a1, a3;
     allow_max_smem(tc_w_kernel<PREC, SIDE>, a1);
     allow_max_smem(tc_x_kernel<PREC, SIDE>, a3);
@@ -551,12 +601,12 @@ cudaError_t launch_tc(double *X, long ldx, int M, int N, const double *V, long l
     float *fin = part + (size_t)8 * 64 * L;
     int *pexp = reinterpret_cast<int *>(fin + (size_t)64 * L);
     int *finexp = pexp + (size_t)8 * L;
-    tc_w_kernel<PREC, SIDE><<<dim3(nblk, S), kTcThreads, tc_w_smem(es), st>>>(X, ldx, M, N, V, ldv, nb, nbp, Tm, Ls,
+    tc_w_kernel<PREC, SIDE><<<dim3(nblk, S), kTcThreads, tc_w_smem(es, nsp), st>>>(X, ldx, M, N, V, ldv, nb, nbp, Tm, Ls,
                                                                              part, pexp, fin, finexp, sc.tickets, info);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const int Text = SIDE == 0 ? M : N;
-    tc_x_kernel<PREC, SIDE><<<dim3(nblk, (Text + kStrip - 1) / kStrip), kTcThreads, tc_x_smem(es, nbp), st>>>(
+    tc_x_kernel<PREC, SIDE><<<dim3(nblk, (Text + kStrip - 1) / kStrip), kTcThreads, tc_x_smem(es, nbp, nsp), st>>>(
         X, ldx, M, N, V, ldv, nb, nbp, fin, finexp, info);
     return cudaGetLastError();
 }
@@ -582,6 +632,12 @@ cudaError_t trail_tc(int side, double *X, long ldx, int M, int N, const double *
     if (prec == NLA_UPD_BF16)
         return side == 0 ? launch_tc<NLA_UPD_BF16, 0>(X, ldx, M, N, V, ldv, nb, Tm, sc, info, st)
                          : launch_tc<NLA_UPD_BF16, 1>(X, ldx, M, N, V, ldv, nb, Tm, sc, info, st);
+    if (prec == NLA_UPD_TF32X3)
+        return side == 0 ? launch_tc<NLA_UPD_TF32X3, 0>(X, ldx, M, N, V, ldv, nb, Tm, sc, info, st)
+                         : launch_tc<NLA_UPD_TF32X3, 1>(X, ldx, M, N, V, ldv, nb, Tm, sc, info, st);
+    if (prec == NLA_UPD_BF16X3)
+        return side == 0 ? launch_tc<NLA_UPD_BF16X3, 0>(X, ldx, M, N, V, ldv, nb, Tm, sc, info, st)
+                         : launch_tc<NLA_UPD_BF16X3, 1>(X, ldx, M, N, V, ldv, nb, Tm, sc, info, st);
     return cudaErrorInvalidValue;
 }
 

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libnla.so")
 
 F64, F32 = 0, 1
-UPD_NATIVE, UPD_TF32, UPD_BF16 = 0, 1, 2
+UPD_NATIVE, UPD_TF32, UPD_BF16, UPD_TF32X3, UPD_BF16X3 = 0, 1, 2, 3, 4
 STATUS = {0: "NLA_OK", 1: "NLA_ERR_ARG", 2: "NLA_ERR_CUDA", 3: "NLA_ERR_CONFIG",
           4: "NLA_ERR_WORKSPACE", 5: "NLA_ERR_TIMEOUT", 6: "NLA_ERR_NOCONV", 7: "NLA_ERR_UNSUPPORTED"}
 

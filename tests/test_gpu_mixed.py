@@ -6,7 +6,8 @@ and the TF32/BF16 trailing update.
   bits, round half away from zero; BF16: keep 7, round half to even).
 * The scaling step's two conversions (FP64 * 2^-e -> FP32, FP32 * 2^e -> FP64)
   are checked element by element against numpy on edge values.
-* The pipeline is checked against prescribed singular values with a bound per
+* The pipeline (TF32, BF16 and the compensated TF32X3, BF16X3 forms) is
+  checked against prescribed singular values with a bound per
   (operand type, condition number) set a small factor above the error measured
   on GB300 (MIXED_BOUNDS), so a loss of accuracy of an order of magnitude
   fails; the first-order model 10 u sqrt(n / b) of the mixed form stays as the
@@ -145,12 +146,9 @@ def test_scale_conversions(nla):
 # Bound on max|sigma_hat - sigma| / sigma_1 per (operand type, kappa) at 700 x 600, band 32:
 # a small factor (about 3x) above the error measured on GB300, so that a tenfold loss of
 # accuracy fails; each sits under the first-order model 10 u sqrt(N / b) of the mixed form.
-MIXED_BOUNDS = {
-    (1, 1.0): 10 * 2.0 ** -11 * math.sqrt(700 / 32), (1, 1e4): 10 * 2.0 ** -11 * math.sqrt(700 / 32),
-    (1, 1e8): 10 * 2.0 ** -11 * math.sqrt(700 / 32),
-    (2, 1.0): 10 * 2.0 ** -8 * math.sqrt(700 / 32), (2, 1e4): 10 * 2.0 ** -8 * math.sqrt(700 / 32),
-    (2, 1e8): 10 * 2.0 ** -8 * math.sqrt(700 / 32),
-}
+# unit roundoff of each operand form: TF32, BF16 and the compensated TF32X3, BF16X3
+U_OF = {1: 2.0 ** -11, 2: 2.0 ** -8, 3: 2.0 ** -21, 4: 2.0 ** -16}
+MIXED_BOUNDS = {(p, k): 10 * U_OF[p] * math.sqrt(700 / 32) for p in U_OF for k in (1.0, 1e4, 1e8)}
 
 
 def mixed_run(nla, A, prec, b=32):
@@ -162,7 +160,7 @@ def mixed_run(nla, A, prec, b=32):
     return s
 
 
-@pytest.mark.parametrize("prec,u", [(1, 2.0 ** -11), (2, 2.0 ** -8)])
+@pytest.mark.parametrize("prec,u", sorted(U_OF.items()))
 @pytest.mark.parametrize("kappa", [1.0, 1e4, 1e8])
 def test_mixed_pipeline_prescribed(nla, prec, u, kappa):
     m, n, b = 700, 600, 32
@@ -174,7 +172,7 @@ def test_mixed_pipeline_prescribed(nla, prec, u, kappa):
     assert err <= MIXED_BOUNDS[(prec, kappa)], err
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3, 4])
 @pytest.mark.parametrize("shift", [200, -200])
 def test_mixed_scaling_equivariant(nla, prec, shift):
     # A * 2^shift lies entirely outside FP32's exponent range; with the power-of-two
@@ -189,7 +187,7 @@ def test_mixed_scaling_equivariant(nla, prec, shift):
     assert err_rel(np.ldexp(s1, -shift), oracle.svdvals(A)) <= MIXED_BOUNDS[(prec, 1e4)]
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3, 4])
 def test_mixed_graded_rows(nla, prec):
     # diag(2^k) Q with Q Haar and k spread over [-140, 140]: the rows span 2^280, beyond
     # FP32's and BF16's range; the singular values are the sorted 2^k
@@ -199,11 +197,10 @@ def test_mixed_graded_rows(nla, prec):
     A = np.ldexp(1.0, k)[:, None] * Q
     want = np.sort(np.ldexp(1.0, k))[::-1]
     got = mixed_run(nla, A, prec)
-    u = 2.0 ** -11 if prec == 1 else 2.0 ** -8
-    assert err_rel(got, want) <= 10 * u * math.sqrt(n / 32)
+    assert err_rel(got, want) <= 10 * U_OF[prec] * math.sqrt(n / 32)
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", [1, 2, 3, 4])
 @pytest.mark.parametrize("m,n,b", [(300, 200, 16), (257, 257, 64), (130, 129, 32), (64, 64, 32)])
 def test_mixed_stage1_keeps_sigma(nla, prec, m, n, b):
     # stage 1 with tensor-core updates: the band's singular values stay within the model of A's
@@ -218,5 +215,4 @@ def test_mixed_stage1_keeps_sigma(nla, prec, m, n, b):
     D = band_dense(ABt, b)
     i, j = np.indices(D.shape)
     assert np.all(D[(j - i < 0) | (j - i > b)] == 0)
-    u = 2.0 ** -11 if prec == 1 else 2.0 ** -8
-    assert err_rel(oracle.svdvals(D), oracle.svdvals(A)) <= 10 * u * math.sqrt(m / b)
+    assert err_rel(oracle.svdvals(D), oracle.svdvals(A)) <= 10 * U_OF[prec] * math.sqrt(m / b)
