@@ -68,6 +68,8 @@ typedef struct {
     int evaluated;         /* configurations timed (or read from the cache) */
     int valid;             /* configurations of the space valid for this problem */
     int failed;            /* configurations that failed to launch or verify */
+    nla_cfg best_lq;       /* KT_GESVD: the LQ side's configuration of the best point (best is
+                              the QR side's, with the band); zero for the kernel level */
 } kt_result;
 
 /* Number of points of the search space (2304) and the index-th point. */
@@ -97,9 +99,20 @@ int kt_cfg_valid(kt_kernel kernel, nla_dtype dtype, const nla_cfg *cfg);
 /* Tune.  strategy KT_EXHAUSTIVE times every valid point; KT_RANDOM times a
  * uniformly random fraction budget_frac of the valid points (SplitMix64 from
  * `seed`, partial Fisher-Yates); KT_MODEL_TOPK times the budget_frac fraction
- * ranked best by the MLP stored at model_path (kt_mlp_save).  cache_path (may
+ * ranked best by the MLP stored at model_path (kt_mlp_train).  cache_path (may
  * be NULL): CSV of measurements; existing rows for the same problem are reused
- * (an interrupted sweep resumes) and new rows appended. */
+ * (an interrupted sweep resumes) and new rows appended.
+ *
+ * KT_GESVD (whole SVD, timed end to end and verified against the default
+ * configuration's singular values): KT_EXHAUSTIVE picks the band width, each
+ * band running each side's best configuration found in the cache (kernel-level
+ * sweeps); KT_MODEL_TOPK and KT_RANDOM tune the pipeline jointly (the paper's
+ * full-pipeline optimisation, Section 5.2 and Section 6) over every (band, QR-
+ * side configuration, LQ-side configuration) triple: the model ranks a triple
+ * by the sum over all stage-1 steps of its two update launches' predicted
+ * runtimes at that step's trailing-block size; the random strategy samples the
+ * triples uniformly.  Their budget is budget_frac of the joint space, at most 64
+ * end-to-end runs. */
 nla_status kt_tune(const kt_problem *problem, kt_strategy strategy, double budget_frac,
                    const char *cache_path, const char *model_path, unsigned long long seed,
                    kt_result *out);

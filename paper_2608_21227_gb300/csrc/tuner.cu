@@ -7,6 +7,7 @@
 // `reps` timed runs, output verified against the default configuration, and
 // launch/verification failures recorded and skipped.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -426,38 +427,52 @@ double pipeline_tol(const kt_problem &p, int N) {
     return 2.0 * (p.dtype == NLA_F64 ? 1e-12 : 5e-6) * N;
 }
 
-nla_status tune_gesvd(const kt_problem &p, const char *cache_path, unsigned long long seed, kt_result *out) {
-    // pipeline level: band width, each band with each side's best kernel configuration
-    // from the cache (else the defaults), timed end to end and verified against the
-    // default configuration's singular values
-    std::map<Key, Meas> cache;
-    load_cache(cache_path, cache);
-    const int es = p.dtype == NLA_F64 ? 8 : 4;
-    const int M = std::max(p.m, p.n), N = std::min(p.m, p.n);
+// End-to-end timing of nla_gesvd_vals on one seeded U[-1, 1] problem: the input is
+// restored from a pristine copy before every run, one warm-up precedes `reps` timed
+// runs (median), and the singular values are either kept as the reference (the default
+// configuration) or checked against it.
+struct PipelineBench {
+    const kt_problem &p;
+    int es, M, N, reps;
+    size_t cnt, wbytes = 0;
     void *A = nullptr, *A0 = nullptr, *S = nullptr, *Sref = nullptr, *W = nullptr;
     int *info = nullptr;
     double *diff = nullptr;
-    size_t cnt = (size_t)M * N, wbytes = 0;
-    kt_result r;
-    memset(&r, 0, sizeof r);
-    r.best_ms = r.median_ms = r.default_ms = NAN;
-    std::vector<double> times;
-    cudaStream_t st;
-    cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    nla_status status = NLA_OK;
-    if (cudaMalloc(&A, cnt * es) || cudaMalloc(&A0, cnt * es) || cudaMalloc(&S, N * (size_t)es) ||
-        cudaMalloc(&Sref, N * (size_t)es) || cudaMalloc(&info, sizeof(int)) || cudaMalloc(&diff, 2 * sizeof(double))) {
-        cudaGetLastError();
-        status = terr(NLA_ERR_CUDA, "tuner: allocation failed");
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+
+    explicit PipelineBench(const kt_problem &prob)
+        : p(prob), es(prob.dtype == NLA_F64 ? 8 : 4), M(std::max(prob.m, prob.n)), N(std::min(prob.m, prob.n)),
+          reps(prob.reps > 0 ? prob.reps : 3), cnt((size_t)M * N) {}
+    ~PipelineBench() {
+        cudaFree(A);
+        cudaFree(A0);
+        cudaFree(S);
+        cudaFree(Sref);
+        cudaFree(W);
+        cudaFree(info);
+        cudaFree(diff);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (st) cudaStreamDestroy(st);
     }
-    const int reps = p.reps > 0 ? p.reps : 3;
-    TableSwap swap;
-    // one end-to-end configuration: median of `reps` timed runs after one warm-up (input
-    // restored before each), then the singular values checked (or kept as the reference)
-    auto run = [&](const nla_opts &o, bool reference, double &med) -> int {  // 0 ok, 1 launch, 2 verify
+    bool init(unsigned long long seed) {
+        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        if (cudaMalloc(&A, cnt * es) || cudaMalloc(&A0, cnt * es) || cudaMalloc(&S, N * (size_t)es) ||
+            cudaMalloc(&Sref, N * (size_t)es) || cudaMalloc(&info, sizeof(int)) || cudaMalloc(&diff, 2 * sizeof(double))) {
+            cudaGetLastError();
+            return false;
+        }
+        if (es == 8)
+            fill_uniform_kernel<double><<<1024, 256, 0, st>>>((double *)A0, (long)cnt, seed);
+        else
+            fill_uniform_kernel<float><<<1024, 256, 0, st>>>((float *)A0, (long)cnt, seed);
+        return cudaStreamSynchronize(st) == cudaSuccess;
+    }
+    // 0 ok, 1 launch failure, 2 verification failure
+    int run(const nla_opts &o, bool reference, double &med) {
         size_t need = 0;
         if (nla_gesvd_vals_workspace(M, N, p.dtype, &o, &need) != NLA_OK) return 1;
         if (need > wbytes) {
@@ -502,77 +517,211 @@ nla_status tune_gesvd(const kt_problem &p, const char *cache_path, unsigned long
         cudaMemcpyAsync(h, diff, sizeof h, cudaMemcpyDeviceToHost, st);
         cudaStreamSynchronize(st);
         return h[0] <= pipeline_tol(p, M) * std::max(h[1], 1e-300) ? 0 : 2;
-    };
-    if (status == NLA_OK) {
-        if (es == 8)
-            fill_uniform_kernel<double><<<1024, 256, 0, st>>>((double *)A0, (long)cnt, seed);
-        else
-            fill_uniform_kernel<float><<<1024, 256, 0, st>>>((float *)A0, (long)cnt, seed);
-        // the default configuration (every field explicit: no table), also the reference
+    }
+    // the whole SVD with band b, the QR-side update running cl and the LQ side cr at every
+    // step (installed as a one-size table while it runs)
+    int run_pair(TableSwap &swap, int b, const nla_cfg &cl, const nla_cfg &cr, double &med) {
+        std::vector<TableEntry> t(2);
+        t[0] = TableEntry{0, M, N, (int)p.dtype, (int)p.update, cl, 0.0};
+        t[1] = TableEntry{1, M, N, (int)p.dtype, (int)p.update, cr, 0.0};
+        swap.install(t);
+        nla_cfg band_only = {b, 0, 0, 0, 0};
+        nla_opts o = {p.update, &band_only, 0};
+        return run(o, false, med);
+    }
+    // the default configuration (every field explicit: no table), kept as the reference
+    bool run_default(double &med) {
         nla_cfg dflt = kDefault;
         nla_opts od = {p.update, &dflt, 0};
-        double dms = NAN;
-        if (run(od, true, dms) != 0) status = terr(NLA_ERR_CUDA, "tuner: the default configuration failed");
-        r.default_ms = dms;
+        return run(od, true, med) == 0;
     }
-    if (status == NLA_OK) {
-        for (int bi = 0; bi < 3; ++bi) {
-            const int b = kBands[bi];
-            if (p.band > 0 && b != p.band) continue;
-            if (b >= N) continue;
-            nla_cfg best[2];
-            for (int side = 0; side < 2; ++side) {
-                best[side] = kDefault;
-                best[side].band = b;
-                double bm = INFINITY;
-                for (auto &kv : cache) {
-                    const Key &k = kv.first;
-                    if (k.kernel != side || k.dtype != (int)p.dtype || k.update != (int)p.update || k.band != b ||
-                        kv.second.status != 0)
-                        continue;
-                    // nearest problem size in the cache with this band
-                    double d = std::fabs(std::log2((double)k.m / p.m)) + std::fabs(std::log2((double)k.n / p.n));
-                    double score = d * 1e6 + kv.second.ms;
-                    if (score < bm) {
-                        bm = score;
-                        best[side] = nla_cfg{b, k.tile, k.threads, k.cpb, k.unroll};
-                    }
+};
+
+nla_status tune_gesvd(const kt_problem &p, const char *cache_path, unsigned long long seed, kt_result *out) {
+    // pipeline level: band width, each band with each side's best kernel configuration
+    // from the cache (else the defaults), timed end to end and verified against the
+    // default configuration's singular values
+    std::map<Key, Meas> cache;
+    load_cache(cache_path, cache);
+    kt_result r;
+    memset(&r, 0, sizeof r);
+    r.best_ms = r.median_ms = r.default_ms = NAN;
+    std::vector<double> times;
+    TableSwap swap;
+    PipelineBench pb(p);
+    if (!pb.init(seed)) return terr(NLA_ERR_CUDA, "tuner: allocation failed");
+    double dms = NAN;
+    if (!pb.run_default(dms)) return terr(NLA_ERR_CUDA, "tuner: the default configuration failed");
+    r.default_ms = dms;
+    for (int bi = 0; bi < 3; ++bi) {
+        const int b = kBands[bi];
+        if (p.band > 0 && b != p.band) continue;
+        if (b >= pb.N) continue;
+        nla_cfg best[2];
+        for (int side = 0; side < 2; ++side) {
+            best[side] = kDefault;
+            best[side].band = b;
+            double bm = INFINITY;
+            for (auto &kv : cache) {
+                const Key &k = kv.first;
+                if (k.kernel != side || k.dtype != (int)p.dtype || k.update != (int)p.update || k.band != b ||
+                    kv.second.status != 0)
+                    continue;
+                // nearest problem size in the cache with this band
+                double d = std::fabs(std::log2((double)k.m / p.m)) + std::fabs(std::log2((double)k.n / p.n));
+                double score = d * 1e6 + kv.second.ms;
+                if (score < bm) {
+                    bm = score;
+                    best[side] = nla_cfg{b, k.tile, k.threads, k.cpb, k.unroll};
                 }
             }
-            // each side runs its own configuration: installed as a one-size table
-            std::vector<TableEntry> t(2);
-            for (int side = 0; side < 2; ++side) t[side] = TableEntry{side, M, N, (int)p.dtype, (int)p.update, best[side], 0.0};
-            swap.install(t);
-            nla_cfg band_only = {b, 0, 0, 0, 0};
-            nla_opts o = {p.update, &band_only, 0};
-            double med = NAN;
-            const int rs = run(o, false, med);
-            r.evaluated++;
-            if (rs != 0) {
-                r.failed++;
-                continue;
+        }
+        double med = NAN;
+        const int rs = pb.run_pair(swap, b, best[0], best[1], med);
+        r.evaluated++;
+        if (rs != 0) {
+            r.failed++;
+            continue;
+        }
+        times.push_back(med);
+        if (!(med >= r.best_ms)) {
+            r.best_ms = med;
+            r.best = best[0];
+            r.best_lq = best[1];
+        }
+    }
+    r.valid = (int)times.size() + r.failed;
+    r.median_ms = median_of(times);
+    if (times.empty()) return terr(NLA_ERR_CONFIG, "tuner: no band ran successfully");
+    *out = r;
+    return NLA_OK;
+}
+
+// Full-pipeline joint tuning: the space is every (band, QR-side configuration, LQ-side
+// configuration) triple valid for the problem, and each point is judged by the whole
+// SVD's runtime (the paper's "full pipeline optimization", Section 5.2 / Section 6).
+// KT_MODEL_TOPK ranks the joint space with the MLP: a point's predicted cost is the sum,
+// over every stage-1 step, of the predicted runtimes of its two update launches at that
+// step's trailing-block size; KT_RANDOM samples the joint space uniformly (SplitMix64).
+// The budget_frac fraction (at most kJointMax points) is timed end to end and verified.
+constexpr int kJointMax = 64;
+
+nla_status tune_joint(const kt_problem &p, kt_strategy strategy, double frac, const char *model_path,
+                      unsigned long long seed, kt_result *out) {
+    const int elem = p.dtype == NLA_F64 ? 8 : 4;
+    const int M = std::max(p.m, p.n), N = std::min(p.m, p.n);
+    struct BandSpace {
+        int b;
+        std::vector<nla_cfg> L, R;
+        std::vector<double> pl, pr;  // predicted stage-1 update time per configuration (ms)
+    };
+    std::vector<BandSpace> bands;
+    long total = 0;
+    for (int bi = 0; bi < 3; ++bi) {
+        const int b = kBands[bi];
+        if ((p.band > 0 && b != p.band) || b >= N) continue;
+        BandSpace bs;
+        bs.b = b;
+        for (int i = 0; i < kSpace; ++i) {
+            const nla_cfg c = space_point(i);
+            if (c.band != b) continue;
+            if (nla::upd_cfg_launchable(0, elem, b, upd_of(c))) bs.L.push_back(c);
+            if (nla::upd_cfg_launchable(1, elem, b, upd_of(c))) bs.R.push_back(c);
+        }
+        if (bs.L.empty() || bs.R.empty()) continue;
+        total += (long)bs.L.size() * (long)bs.R.size();
+        bands.push_back(std::move(bs));
+    }
+    if (bands.empty() || total <= 0) return terr(NLA_ERR_CONFIG, "tuner: empty joint space");
+    if (total > (long)1 << 30) return terr(NLA_ERR_UNSUPPORTED, "tuner: joint space too large");
+    long k = (long)std::ceil(std::max(0.0, std::min(1.0, frac)) * (double)total);
+    k = std::max(1L, std::min({k, total, (long)kJointMax}));
+    // candidates as (band index, left index, right index)
+    std::vector<std::array<int, 3>> cand;
+    auto decode = [&](long idx) {
+        for (int bi = 0; bi < (int)bands.size(); ++bi) {
+            const long sz = (long)bands[bi].L.size() * (long)bands[bi].R.size();
+            if (idx < sz) return std::array<int, 3>{bi, (int)(idx / (long)bands[bi].R.size()),
+                                                    (int)(idx % (long)bands[bi].R.size())};
+            idx -= sz;
+        }
+        return std::array<int, 3>{0, 0, 0};
+    };
+    if (strategy == KT_RANDOM) {
+        std::vector<int> idx((size_t)k);
+        kt_random_subset((int)total, (int)k, seed, idx.data());
+        for (long i = 0; i < k; ++i) cand.push_back(decode(idx[(size_t)i]));
+    } else {
+        if (!model_path) return terr(NLA_ERR_ARG, "KT_MODEL_TOPK needs model_path");
+        // predicted stage-1 update time of every configuration of each band and side
+        for (BandSpace &bs : bands) {
+            std::vector<std::pair<int, int>> steps[2];  // trailing-block sizes of the QR / LQ updates
+            for (int kb = 0; kb < N; kb += bs.b) {
+                const int nb = std::min(bs.b, N - kb), c0 = kb + nb;
+                if (c0 >= N) break;
+                steps[0].push_back({M - kb, N - c0});
+                if (M - c0 > 0) steps[1].push_back({M - c0, N - c0});
             }
-            times.push_back(med);
-            if (!(med >= r.best_ms)) {
-                r.best_ms = med;
-                r.best = best[0];
+            for (int side = 0; side < 2; ++side) {
+                const std::vector<nla_cfg> &cs = side == 0 ? bs.L : bs.R;
+                std::vector<double> &pred = side == 0 ? bs.pl : bs.pr;
+                const size_t rows = cs.size() * steps[side].size();
+                std::vector<float> X(rows * KT_MLP_FEATURES), y(rows);
+                size_t r = 0;
+                for (const nla_cfg &c : cs)
+                    for (const auto &mn : steps[side])
+                        kt_features(side == 0 ? KT_TRAIL_LEFT : KT_TRAIL_RIGHT, mn.first, mn.second, p.dtype, p.update,
+                                    &c, &X[(r++) * KT_MLP_FEATURES]);
+                nla_status s = nla::mlp_predict_host(model_path, X.data(), (int)rows, y.data());
+                if (s != NLA_OK) return s;
+                pred.assign(cs.size(), 0.0);
+                for (size_t i = 0; i < cs.size(); ++i)
+                    for (size_t j = 0; j < steps[side].size(); ++j) pred[i] += std::exp((double)y[i * steps[side].size() + j]);
             }
         }
-        r.valid = (int)times.size() + r.failed;
-        r.median_ms = median_of(times);
+        // the k joint points of smallest predicted cost (ties: lexicographic order)
+        std::vector<std::pair<double, long>> all;
+        all.reserve((size_t)total);
+        long base = 0;
+        for (const BandSpace &bs : bands) {
+            for (size_t i = 0; i < bs.L.size(); ++i)
+                for (size_t j = 0; j < bs.R.size(); ++j)
+                    all.push_back({bs.pl[i] + bs.pr[j], base + (long)(i * bs.R.size() + j)});
+            base += (long)bs.L.size() * (long)bs.R.size();
+        }
+        std::partial_sort(all.begin(), all.begin() + k, all.end());
+        for (long i = 0; i < k; ++i) cand.push_back(decode(all[(size_t)i].second));
     }
-    cudaFree(A);
-    cudaFree(A0);
-    cudaFree(S);
-    cudaFree(Sref);
-    cudaFree(W);
-    cudaFree(info);
-    cudaFree(diff);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaStreamDestroy(st);
-    if (status != NLA_OK) return status;
-    if (times.empty()) return terr(NLA_ERR_CONFIG, "tuner: no band ran successfully");
+    kt_result r;
+    memset(&r, 0, sizeof r);
+    r.best_ms = r.median_ms = r.default_ms = NAN;
+    r.valid = (int)std::min(total, (long)INT32_MAX);
+    std::vector<double> times;
+    TableSwap swap;
+    PipelineBench pb(p);
+    if (!pb.init(seed)) return terr(NLA_ERR_CUDA, "tuner: allocation failed");
+    double dms = NAN;
+    if (!pb.run_default(dms)) return terr(NLA_ERR_CUDA, "tuner: the default configuration failed");
+    r.default_ms = dms;
+    for (const auto &c : cand) {
+        const BandSpace &bs = bands[(size_t)c[0]];
+        const nla_cfg &cl = bs.L[(size_t)c[1]], &cr = bs.R[(size_t)c[2]];
+        double med = NAN;
+        const int rs = pb.run_pair(swap, bs.b, cl, cr, med);
+        r.evaluated++;
+        if (rs != 0) {
+            r.failed++;
+            continue;
+        }
+        times.push_back(med);
+        if (!(med >= r.best_ms)) {
+            r.best_ms = med;
+            r.best = cl;
+            r.best_lq = cr;
+        }
+    }
+    r.median_ms = median_of(times);
+    if (times.empty()) return terr(NLA_ERR_CONFIG, "tuner: no joint candidate ran successfully");
     *out = r;
     return NLA_OK;
 }
@@ -634,7 +783,9 @@ nla_status kt_tune(const kt_problem *p, kt_strategy strategy, double budget_frac
     if (p->m <= 0 || p->n <= 0) return terr(NLA_ERR_ARG, "empty problem");
     if (p->dtype != NLA_F64 && p->dtype != NLA_F32) return terr(NLA_ERR_ARG, "unknown dtype");
     if (strategy < KT_EXHAUSTIVE || strategy > KT_RANDOM) return terr(NLA_ERR_ARG, "unknown strategy");
-    if (p->kernel == KT_GESVD) return tune_gesvd(*p, cache_path, seed, out);
+    if (p->kernel == KT_GESVD)
+        return strategy == KT_EXHAUSTIVE ? tune_gesvd(*p, cache_path, seed, out)
+                                         : tune_joint(*p, strategy, budget_frac, model_path, seed, out);
     if (p->kernel != KT_TRAIL_LEFT && p->kernel != KT_TRAIL_RIGHT) return terr(NLA_ERR_ARG, "unknown kernel");
     if (p->update != NLA_UPD_NATIVE) return terr(NLA_ERR_ARG, "SIMT trailing-update tuning needs NLA_UPD_NATIVE");
     if (p->m < p->n) return terr(NLA_ERR_ARG, "trailing-update tuning needs m >= n");

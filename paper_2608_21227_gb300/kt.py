@@ -20,12 +20,12 @@ class Problem(ctypes.Structure):
 class Result(ctypes.Structure):
     _fields_ = [("best", _nla.Cfg), ("best_ms", ctypes.c_double), ("median_ms", ctypes.c_double),
                 ("default_ms", ctypes.c_double), ("evaluated", ctypes.c_int), ("valid", ctypes.c_int),
-                ("failed", ctypes.c_int)]
+                ("failed", ctypes.c_int), ("best_lq", _nla.Cfg)]
 
     def as_dict(self):
         return {"best": self.best.as_tuple(), "best_ms": self.best_ms, "median_ms": self.median_ms,
                 "default_ms": self.default_ms, "evaluated": self.evaluated, "valid": self.valid,
-                "failed": self.failed}
+                "failed": self.failed, "best_lq": self.best_lq.as_tuple()}
 
 
 _bound = False

@@ -1,16 +1,21 @@
 """What the learned cost model gains over the method without it.
 
-The tuner's own exhaustive sweeps (Eq. 1) produce the training data: FP64 QR- and
-LQ-side trailing-update launches at n = 512, 1024 and 2048, every band width and
-every valid configuration.  The MLP is trained on the GPU by the library's own
-kernels (kt_mlp_train) and then used through kt_tune(..., KT_MODEL_TOPK, 0.05):
-on a held-out size (n = 1536) it ranks the valid space and only the top 5 % is
-benchmarked.  The method without it is the same budget spent on a uniformly
-random 5 % sample (KT_RANDOM, ten seeds); exhaustive search is the judge.
+The tuner's own exhaustive sweeps (Eq. 1) produce the training data: QR- and
+LQ-side trailing-update launches at n = 512, 1024 and 2048, FP64 and FP32, every
+band width and every valid configuration.  The MLP is trained on the GPU by the
+library's own kernels (kt_mlp_train) and then used through kt_tune(...,
+KT_MODEL_TOPK, ...):
 
-Asserted, summed over both sides and all three band widths (so one noisy case
-cannot decide it): the model's picks are no slower than the random picks on
-average, and each pick is within 1.5x of the exhaustive optimum.
+* kernel level, FP64, held-out n = 1536: it ranks the valid space and only the
+  top 5 % is benchmarked.  The method without it is the same budget spent on a
+  uniformly random 5 % sample (KT_RANDOM, ten seeds); exhaustive search is the
+  judge.  Asserted, summed over both sides and all three band widths (so one
+  noisy case cannot decide it): the model's picks are no slower than the random
+  picks on average, and each pick is within 1.5x of the exhaustive optimum.
+* full pipeline, FP32, n = 1536 (the joint space of band x QR-side x LQ-side
+  configurations, each point timed as a whole SVD and verified): the model's
+  best of 16 end-to-end runs against the random sample's best of 16 (three
+  seeds) and the default configuration.
 """
 import csv
 
@@ -38,20 +43,27 @@ def read_rows(path):
         return [r for r in csv.DictReader(f) if int(r["status"]) == 0 and float(r["median_ms"]) > 0]
 
 
-def test_model_topk_beats_random_sample(kt, tmp_path):
-    cache = str(tmp_path / "sweep.csv")
-    for n in TRAIN_N:
-        for kern in (kt.KT_TRAIL_LEFT, kt.KT_TRAIL_RIGHT):
-            kt.tune(kern, n, n, 0, band=0, reps=3, cache=cache, seed=n)
+@pytest.fixture(scope="module")
+def trained(kt, tmp_path_factory):
+    d = tmp_path_factory.mktemp("costmodel")
+    cache = str(d / "sweep.csv")
+    for dt in (0, 1):
+        for n in TRAIN_N:
+            for kern in (kt.KT_TRAIL_LEFT, kt.KT_TRAIL_RIGHT):
+                kt.tune(kern, n, n, dt, band=0, reps=3, cache=cache, seed=n)
     rows = read_rows(cache)
     assert len(rows) > 1000
     X = np.stack([kt.features(int(r["kernel"]), int(r["m"]), int(r["n"]), int(r["dtype"]), int(r["update"]),
                               (int(r["band"]), int(r["tile"]), int(r["threads"]), int(r["cpb"]), int(r["unroll"])))
                   for r in rows])
     y = np.log(np.array([float(r["median_ms"]) for r in rows]))
-    model = str(tmp_path / "mlp.bin")
+    model = str(d / "mlp.bin")
     kt.mlp_train(X, y.astype(np.float32), epochs=150, batch=128, lr=2e-3, seed=1, model_path=model)
+    return model
 
+
+def test_model_topk_beats_random_sample(kt, trained, tmp_path):
+    model = trained
     held = str(tmp_path / "held.csv")
     model_ratio, random_ratio, report = [], [], []
     for kern in (kt.KT_TRAIL_LEFT, kt.KT_TRAIL_RIGHT):
@@ -70,3 +82,24 @@ def test_model_topk_beats_random_sample(kt, tmp_path):
     print("kernel band valid benchmarked model/opt random/opt:", report)
     assert max(model_ratio) <= 1.5, report
     assert sum(model_ratio) <= sum(random_ratio), report
+
+
+def test_joint_pipeline_tuning(kt, trained):
+    # the joint space at n = 1536, FP32: model-ranked top 16 vs random 16 (three seeds)
+    n, budget = HOLDOUT_N, 16
+    valid = {b: (sum(kt.cfg_valid(kt.KT_TRAIL_LEFT, 1, c) for c in kt.space() if c[0] == b),
+                 sum(kt.cfg_valid(kt.KT_TRAIL_RIGHT, 1, c) for c in kt.space() if c[0] == b)) for b in BANDS}
+    total = sum(l * r for l, r in valid.values())
+    frac = (budget - 0.5) / total  # ceil(frac * total) == budget
+    mo = kt.tune(kt.KT_GESVD, n, n, 1, reps=3, strategy=kt.KT_MODEL_TOPK, budget_frac=frac, model=trained, seed=5)
+    assert mo["valid"] == total and mo["evaluated"] == budget and mo["failed"] == 0
+    assert mo["best"][0] == mo["best_lq"][0] and mo["best"][0] in BANDS
+    assert kt.cfg_valid(kt.KT_TRAIL_LEFT, 1, mo["best"]) and kt.cfg_valid(kt.KT_TRAIL_RIGHT, 1, mo["best_lq"])
+    rnd = [kt.tune(kt.KT_GESVD, n, n, 1, reps=3, strategy=kt.KT_RANDOM, budget_frac=frac, seed=200 + s)
+           for s in range(3)]
+    assert all(r["failed"] == 0 and r["evaluated"] == budget for r in rnd)
+    rnd_mean = float(np.mean([r["best_ms"] for r in rnd]))
+    print(f"joint n={n}: model {mo['best_ms']:.3f} ms {mo['best']} / {mo['best_lq']}, random mean {rnd_mean:.3f} ms, "
+          f"default {mo['default_ms']:.3f} ms, joint space {total}")
+    assert mo["best_ms"] <= 1.05 * rnd_mean
+    assert mo["best_ms"] <= 1.02 * mo["default_ms"]
