@@ -44,6 +44,11 @@ extern "C" {
 
 typedef enum { KT_EXHAUSTIVE = 0, KT_MODEL_TOPK = 1, KT_RANDOM = 2 } kt_strategy;
 
+/* What Eq. 1 minimises: the runtime (milliseconds, CUDA events) or the energy one
+ * launch draws (millijoules, from the device's NVML energy counter; see the energy
+ * observer below). */
+typedef enum { KT_TIME = 0, KT_ENERGY = 1 } kt_objective;
+
 /* What is tuned: one trailing-update launch at panel step 0 (full size) of
  * the QR side or the LQ side, or the whole pipeline (band width only). */
 typedef enum { KT_TRAIL_LEFT = 0, KT_TRAIL_RIGHT = 1, KT_GESVD = 2 } kt_kernel;
@@ -55,6 +60,8 @@ typedef struct {
     nla_update update; /* must be NLA_UPD_NATIVE for the SIMT trailing-update kernels */
     int band;          /* band width to tune the kernel for; 0 = every band of the space */
     int reps;          /* timed runs per configuration (median taken); 0 = 5 */
+    int objective;     /* kt_objective; KT_ENERGY is supported for the kernel level (the
+                          *_ms fields of the result then hold millijoules per launch) */
 } kt_problem;
 
 typedef struct {
@@ -100,8 +107,8 @@ int kt_cfg_valid(kt_kernel kernel, nla_dtype dtype, const nla_cfg *cfg);
  * uniformly random fraction budget_frac of the valid points (SplitMix64 from
  * `seed`, partial Fisher-Yates); KT_MODEL_TOPK times the budget_frac fraction
  * ranked best by the MLP stored at model_path (kt_mlp_train).  cache_path (may
- * be NULL): CSV of measurements; existing rows for the same problem are reused
- * (an interrupted sweep resumes) and new rows appended.
+ * be NULL): CSV of measurements; existing rows for the same problem (and
+ * objective) are reused (an interrupted sweep resumes) and new rows appended.
  *
  * KT_GESVD (whole SVD, timed end to end and verified against the default
  * configuration's singular values): KT_EXHAUSTIVE picks the band width, each
@@ -128,6 +135,22 @@ nla_status kt_load_config(const char *path);
  * side 0 = QR-side update, 1 = LQ-side update, 2 = batched bucket m. */
 nla_status kt_write_table(const char *path, int side, int m, int n, nla_dtype dtype,
                           nla_update update, const nla_cfg *cfg, double ms);
+
+/* ---------------------------------------------------------------- energy observer */
+
+/* The tuner's energy observer (the paper's observers for an energy objective,
+ * Section 3.1, Section 6): reads, never changes, the GPU's total energy counter
+ * through NVML, opened at run time (libnvidia-ml.so.1, or the library named by
+ * the NLA_NVML_LIB environment variable, or by kt_energy_open).  The counter is
+ * in millijoules since the driver loaded; it advances in coarse steps, so the
+ * tuner measures energy over a window of at least 200 ms of repeated launches
+ * and divides by their count.  Returns NLA_ERR_UNSUPPORTED when NVML or the
+ * counter is unavailable. */
+nla_status kt_energy_open(const char *nvml_path);
+/* Counter of the current CUDA device (matched to NVML by PCI bus id). */
+nla_status kt_energy_read(unsigned long long *millijoules);
+/* Counter of NVML device `index`. */
+nla_status kt_energy_read_index(unsigned int index, unsigned long long *millijoules);
 
 /* ---------------------------------------------------------------- cost model */
 

@@ -69,7 +69,7 @@ def build(force: bool = False, jobs: int | None = None, extra=(), verbose: bool 
                     print(f"--- {os.path.basename(src)}\n{log}")
     if todo or not os.path.exists(LIB):
         tmp = LIB + f".{os.getpid()}.tmp"
-        cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC"]
+        cmd = [nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-Xcompiler", "-fPIC", "-ldl"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr[-4000:]}")

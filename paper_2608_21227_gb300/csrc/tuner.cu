@@ -107,14 +107,15 @@ __global__ void max_abs_diff_kernel(const T *A, const T *B, long count, double *
 
 // ------------------------------------------------------------------ cache
 struct Key {
-    int kernel, m, n, dtype, update, band, tile, threads, cpb, unroll;
+    int kernel, m, n, dtype, update, band, tile, threads, cpb, unroll, objective;
     bool operator<(const Key &o) const {
-        return std::tie(kernel, m, n, dtype, update, band, tile, threads, cpb, unroll) <
-               std::tie(o.kernel, o.m, o.n, o.dtype, o.update, o.band, o.tile, o.threads, o.cpb, o.unroll);
+        return std::tie(kernel, m, n, dtype, update, band, tile, threads, cpb, unroll, objective) <
+               std::tie(o.kernel, o.m, o.n, o.dtype, o.update, o.band, o.tile, o.threads, o.cpb, o.unroll,
+                        o.objective);
     }
 };
 struct Meas {
-    double ms;
+    double ms;   // the objective's value: milliseconds (KT_TIME) or millijoules per launch (KT_ENERGY)
     int status;  // 0 ok, 1 launch failure, 2 verification failure
 };
 
@@ -127,8 +128,9 @@ void load_cache(const char *path, std::map<Key, Meas> &c) {
         if (line[0] == '#' || line[0] == 'k') continue;  // comment / header
         Key k;
         Meas v;
-        if (sscanf(line, "%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%lf,%d", &k.kernel, &k.m, &k.n, &k.dtype, &k.update, &k.band,
-                   &k.tile, &k.threads, &k.cpb, &k.unroll, &v.ms, &v.status) == 12)
+        k.objective = KT_TIME;  // (files without the objective column hold runtimes)
+        if (sscanf(line, "%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%lf,%d,%d", &k.kernel, &k.m, &k.n, &k.dtype, &k.update, &k.band,
+                   &k.tile, &k.threads, &k.cpb, &k.unroll, &v.ms, &v.status, &k.objective) >= 12)
             c[k] = v;
     }
     fclose(f);
@@ -138,9 +140,9 @@ void append_cache(const char *path, const Key &k, const Meas &v) {
     if (!path) return;
     FILE *f = fopen(path, "a");
     if (!f) return;
-    if (ftell(f) == 0) fprintf(f, "kernel,m,n,dtype,update,band,tile,threads,cpb,unroll,median_ms,status\n");
-    fprintf(f, "%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%.6f,%d\n", k.kernel, k.m, k.n, k.dtype, k.update, k.band, k.tile,
-            k.threads, k.cpb, k.unroll, v.ms, v.status);
+    if (ftell(f) == 0) fprintf(f, "kernel,m,n,dtype,update,band,tile,threads,cpb,unroll,median_ms,status,objective\n");
+    fprintf(f, "%d,%d,%d,%d,%d,%d,%d,%d,%d,%d,%.6f,%d,%d\n", k.kernel, k.m, k.n, k.dtype, k.update, k.band, k.tile,
+            k.threads, k.cpb, k.unroll, v.ms, v.status, k.objective);
     fclose(f);
 }
 
@@ -171,7 +173,7 @@ bool is_default_kernel(const nla_cfg &c) {
 // ------------------------------------------------------------------ trailing-update tuning
 template <typename T>
 struct TrailBench {
-    int side, m, n, reps;
+    int side, m, n, reps, objective = KT_TIME;
     T *A = nullptr, *A0 = nullptr, *Xref = nullptr;
     T *tau = nullptr, *Tm = nullptr;
     unsigned int *bar = nullptr, *tickets = nullptr;
@@ -266,6 +268,28 @@ struct TrailBench {
             if (ms > 0.f) t.push_back(ms);
         }
         if (t.empty()) return {NAN, 1};
+        double value = median_of(t);
+        if (objective == KT_ENERGY) {
+            // energy per launch: back-to-back launches over at least 200 ms (the counter
+            // advances in coarse steps; each launch applies an orthogonal transformation,
+            // so the repeats keep X bounded), restored afterwards for the verification
+            const int R = std::max(reps, (int)std::ceil(200.0 / std::max(value, 1e-3)));
+            unsigned long long e0 = 0, e1 = 0;
+            cudaStreamSynchronize(st);
+            if (kt_energy_read(&e0) != NLA_OK) return {NAN, 1};
+            for (int r = 0; r < R; ++r)
+                if (launch(c) != cudaSuccess) {
+                    cudaGetLastError();
+                    return {NAN, 1};
+                }
+            if (cudaStreamSynchronize(st) != cudaSuccess || kt_energy_read(&e1) != NLA_OK) return {NAN, 1};
+            value = (double)(e1 - e0) / R;
+            restore();
+            if (launch(c) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+                cudaGetLastError();
+                return {NAN, 1};
+            }
+        }
         size_t cnt = (size_t)m * n;
         if (is_reference) {
             cudaMemcpyAsync(Xref, A, cnt * sizeof(T), cudaMemcpyDeviceToDevice, st);
@@ -277,9 +301,9 @@ struct TrailBench {
             cudaMemcpyAsync(h, diff, sizeof h, cudaMemcpyDeviceToHost, st);
             cudaStreamSynchronize(st);
             const double tol = sizeof(T) == 8 ? 1e-10 : 1e-3;
-            if (!(h[0] <= tol * std::max(h[1], 1e-300))) return {median_of(t), 2};
+            if (!(h[0] <= tol * std::max(h[1], 1e-300))) return {value, 2};
         }
-        return {median_of(t), 0};
+        return {value, 0};
     }
 };
 
@@ -305,6 +329,12 @@ nla_status tune_trail(const kt_problem &p, kt_strategy strategy, double frac, co
     tb.m = p.m;
     tb.n = p.n;
     tb.reps = p.reps > 0 ? p.reps : 5;
+    tb.objective = p.objective;
+    if (p.objective == KT_ENERGY) {
+        unsigned long long e = 0;
+        nla_status s = kt_energy_read(&e);
+        if (s != NLA_OK) return s;
+    }
     if (tb.init() != cudaSuccess) {
         cudaGetLastError();
         return terr(NLA_ERR_CUDA, "tuner: allocation failed");
@@ -367,7 +397,7 @@ nla_status tune_trail(const kt_problem &p, kt_strategy strategy, double frac, co
             if (is_default_kernel(ref) && (p.band > 0 || ref.band == kDefault.band)) r.default_ms = mref.ms;
         }
         Key k{(int)p.kernel, p.m, p.n, (int)p.dtype, (int)p.update, c.band, c.tile, c.threads, c.cols_per_block,
-              c.unroll};
+              c.unroll, p.objective};
         Meas v;
         auto it = cache.find(k);
         if (it != cache.end()) {
@@ -783,6 +813,9 @@ nla_status kt_tune(const kt_problem *p, kt_strategy strategy, double budget_frac
     if (p->m <= 0 || p->n <= 0) return terr(NLA_ERR_ARG, "empty problem");
     if (p->dtype != NLA_F64 && p->dtype != NLA_F32) return terr(NLA_ERR_ARG, "unknown dtype");
     if (strategy < KT_EXHAUSTIVE || strategy > KT_RANDOM) return terr(NLA_ERR_ARG, "unknown strategy");
+    if (p->objective != KT_TIME && p->objective != KT_ENERGY) return terr(NLA_ERR_ARG, "unknown objective");
+    if (p->objective == KT_ENERGY && p->kernel == KT_GESVD)
+        return terr(NLA_ERR_UNSUPPORTED, "the energy objective is supported for the kernel level");
     if (p->kernel == KT_GESVD)
         return strategy == KT_EXHAUSTIVE ? tune_gesvd(*p, cache_path, seed, out)
                                          : tune_joint(*p, strategy, budget_frac, model_path, seed, out);

@@ -9,12 +9,14 @@ from . import nla as _nla
 
 KT_EXHAUSTIVE, KT_MODEL_TOPK, KT_RANDOM = 0, 1, 2
 KT_TRAIL_LEFT, KT_TRAIL_RIGHT, KT_GESVD = 0, 1, 2
+KT_TIME, KT_ENERGY = 0, 1
 FEATURES = 15
 
 
 class Problem(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("m", ctypes.c_int), ("n", ctypes.c_int), ("dtype", ctypes.c_int),
-                ("update", ctypes.c_int), ("band", ctypes.c_int), ("reps", ctypes.c_int)]
+                ("update", ctypes.c_int), ("band", ctypes.c_int), ("reps", ctypes.c_int),
+                ("objective", ctypes.c_int)]
 
 
 class Result(ctypes.Structure):
@@ -54,8 +56,12 @@ def lib():
         vp = ctypes.c_void_p
         L.kt_mlp_forward_backward.argtypes = [vp, vp, vp, i, vp, vp, vp, sz, vp]
         L.kt_mlp_adam_step.argtypes = [vp, vp, vp, vp, sz, i, ctypes.c_float, vp]
+        L.kt_energy_open.argtypes = [c]
+        L.kt_energy_read.argtypes = [ctypes.POINTER(ctypes.c_ulonglong)]
+        L.kt_energy_read_index.argtypes = [ctypes.c_uint, ctypes.POINTER(ctypes.c_ulonglong)]
         for f in ("kt_space_get", "kt_random_subset", "kt_tune", "kt_load_config", "kt_write_table", "kt_features",
-                  "kt_mlp_train", "kt_mlp_predict", "kt_mlp_forward_backward", "kt_mlp_adam_step"):
+                  "kt_mlp_train", "kt_mlp_predict", "kt_mlp_forward_backward", "kt_mlp_adam_step",
+                  "kt_energy_open", "kt_energy_read", "kt_energy_read_index"):
             getattr(L, f).restype = i
         _bound = True
     return L
@@ -94,8 +100,8 @@ def features(kernel, m, n, dtype, update, cfg):
 
 
 def tune(kernel, m, n, dtype, update=0, band=0, reps=0, strategy=KT_EXHAUSTIVE, budget_frac=0.05, cache=None,
-         model=None, seed=0):
-    p = Problem(int(kernel), int(m), int(n), int(dtype), int(update), int(band), int(reps))
+         model=None, seed=0, objective=0):
+    p = Problem(int(kernel), int(m), int(n), int(dtype), int(update), int(band), int(reps), int(objective))
     r = Result()
     _nla._check(lib().kt_tune(ctypes.byref(p), int(strategy), float(budget_frac), _b(cache), _b(model), int(seed),
                               ctypes.byref(r)))
@@ -155,3 +161,17 @@ def mlp_adam_step(params, grads, m, v, t, lr, stream=None):
     vp = ctypes.c_void_p
     _nla._check(lib().kt_mlp_adam_step(vp(params.data_ptr()), vp(grads.data_ptr()), vp(m.data_ptr()),
                                        vp(v.data_ptr()), params.numel(), int(t), float(lr), _nla._stream_ptr(stream)))
+
+
+def energy_open(nvml_path=None):
+    _nla._check(lib().kt_energy_open(_b(nvml_path)))
+
+
+def energy_read(index=None):
+    """Energy counter (millijoules) of the current CUDA device, or of NVML device `index`."""
+    v = ctypes.c_ulonglong(0)
+    if index is None:
+        _nla._check(lib().kt_energy_read(ctypes.byref(v)))
+    else:
+        _nla._check(lib().kt_energy_read_index(int(index), ctypes.byref(v)))
+    return int(v.value)
