@@ -245,6 +245,17 @@ nla_status nla_tc_selftest(int prec, int K, int N, const float *dA, const float 
 nla_status nla_scale_selftest(int n, const double *dX, const int *dEx, float *dF, const float *dV,
                               const int *dEv, double *dD, nla_stream_t stream);
 
+/* Pipe microbenchmarks (no counterpart in the paper): the peaks the kernels'
+ * rooflines are measured against.  kind 0: FP32 FMA (blocks x 256 threads, 8
+ * independent chains of `iters` FMAs per thread: 2 * 8 * iters flops a thread);
+ * kind 1: the same with FP64 FMAs; kind 2: tensor cores, kind::tf32 (one block
+ * of 128 threads per entry of `blocks`, one thread issuing `iters` MMAs of
+ * 128 x 256 x 8: 524288 flops each; launch at most one block per SM).  dOut:
+ * a device buffer of blocks * 256 elements of the kind's type (never written in
+ * practice); dInfo: device int (-NLA_ERR_TIMEOUT if a wait gave up).  The caller
+ * times the launch on `stream` (CUDA events). */
+nla_status nla_pipe_selftest(int kind, int blocks, int iters, void *dOut, int *dInfo, nla_stream_t stream);
+
 /* Failure-detection self-test (no counterpart in the paper): one block waits,
  * with a budget of budget_us microseconds, on something that never happens --
  * mode 0: a global flag that nothing sets (the inter-block spin every

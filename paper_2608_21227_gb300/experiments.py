@@ -11,6 +11,8 @@ mixed:   A = U diag(sigma) V^T stored in FP64 with Haar-random U, V and sigma_i 
          singular values are within ~1e-14 sigma_1 of sigma), the error against the FP64
          path, the median relative error over sigma_i >= 1e-3 sigma_1, and the time (CUDA
          events) with the speedup over FP64-native.
+peaks:   FP32 FMA, FP64 FMA and tensor-core (kind::tf32) throughput from long chains of
+         independent operations (nla_pipe_selftest), CUDA events, SM clock sampled.
 latency: the 256 x 256 FP64 N(0,1) case (tile 32, band 32, default configuration): one
          call captured into a CUDA graph, median of 20 replays.
 case:    one workload run `--reps` times, for profilers that capture single launches:
@@ -194,6 +196,65 @@ def case(args):
                       "sigma_max": float(S[0].item())}))
 
 
+def peaks(args):
+    """FP32 FMA, FP64 FMA and tcgen05 kind::tf32 throughput of this GPU (nla_pipe_selftest),
+    timed with CUDA events while nvidia-smi samples the SM clock (read-only)."""
+    import ctypes
+    import subprocess
+    import threading
+
+    import torch
+
+    L = nla.lib()
+    L.nla_pipe_selftest.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p]
+    L.nla_pipe_selftest.restype = ctypes.c_int
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = torch.zeros(sms * 8 * 256, dtype=torch.float64, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    lines = []
+    proc = subprocess.Popen(["nvidia-smi", "-i", "0", "--query-gpu=clocks.sm,clocks.max.sm,power.draw",
+                             "--format=csv,noheader,nounits", "-lms", "100"], stdout=subprocess.PIPE,
+                            stderr=subprocess.DEVNULL, text=True)
+    reader = threading.Thread(target=lambda: [lines.append(x.strip()) for x in proc.stdout], daemon=True)
+    reader.start()
+    res = {}
+    # kind: (name, blocks, iters, flops per launch)
+    runs = [("fp32_fma", 0, sms * 8, 200000, lambda b, it: 2.0 * 8 * it * b * 256),
+            ("fp64_fma", 1, sms * 8, 20000, lambda b, it: 2.0 * 8 * it * b * 256),
+            ("tf32_tcgen05", 2, sms, 200000, lambda b, it: 2.0 * 128 * 256 * 8 * it * b)]
+    for name, kind, blocks, iters, fl in runs:
+        st = torch.cuda.current_stream().cuda_stream
+        for _ in range(2):  # warm-up
+            assert L.nla_pipe_selftest(kind, blocks, max(iters // 10, 1), ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(info.data_ptr()), ctypes.c_void_p(st)) == 0
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(args.reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            assert L.nla_pipe_selftest(kind, blocks, iters, ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(info.data_ptr()), ctypes.c_void_p(st)) == 0
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        assert int(info.item()) == 0
+        res[name] = {"tflops": round(fl(blocks, iters) / (best / 1e3) / 1e12, 2), "ms": round(best, 3),
+                     "blocks": blocks, "iters": iters}
+        print(json.dumps({name: res[name]}), flush=True)
+    proc.terminate()
+    reader.join(timeout=2)
+    mhz = [float(x.split(",")[0]) for x in lines if x and x.split(",")[0].strip().replace(".", "").isdigit()]
+    res["clocks"] = {"sm_mhz_median": float(np.median(mhz)) if mhz else None, "samples": len(mhz),
+                     "sm_max_mhz": float(lines[0].split(",")[1]) if lines else None}
+    res["sms"] = sms
+    if args.out:
+        with open(args.out, "w") as f:
+            json.dump(res, f, indent=1)
+    print(json.dumps(res))
+
+
 def main():
     ap = argparse.ArgumentParser()
     sub = ap.add_subparsers(dest="cmd", required=True)
@@ -213,9 +274,12 @@ def main():
     c.add_argument("--mlp", type=int, default=0)
     c.add_argument("--reps", type=int, default=2)
     c.add_argument("--tuned", action="store_true", help="install the tuned table first")
+    pk = sub.add_parser("peaks")
+    pk.add_argument("--reps", type=int, default=5)
+    pk.add_argument("--out")
     args = ap.parse_args()
     t0 = time.time()
-    {"mixed": mixed, "latency": latency, "case": case}[args.cmd](args)
+    {"mixed": mixed, "latency": latency, "case": case, "peaks": peaks}[args.cmd](args)
     print(json.dumps({"seconds": round(time.time() - t0, 1)}))
 
 
