@@ -157,25 +157,10 @@ def trail_bytes_per_step(M, N, b, side, elem=4):
     return tot
 
 
-def fused_update_bytes_per_step(M, N, b, elem=4):
-    """Algorithmic bytes of the fused FP32 update schedule in one step: per panel pair the QR
-    projection reads the trailing block, the QR update of the row block reads and writes b rows,
-    the fused pass (QR update of the rows below + LQ projection) reads and writes the rest once,
-    and the LQ update reads and writes it once more (V, W', Y' are small)."""
-    tot = 0.0
-    for kb in range(0, N, b):
-        nb = min(b, N - kb)
-        c0 = kb + nb
-        if c0 >= N:
-            break
-        tot += elem * (M - kb) * (N - c0) + 2.0 * elem * nb * (N - c0) + 4.0 * elem * (M - c0) * (N - c0)
-    return tot
-
-
 # kernels each traced region launches on the FP32 path (panel: one cluster or grid kernel;
-# trailing update: projection + update in one region, or -- fused schedule -- one kernel
-# per region; chase: sweeps + bidiagonal extraction; bisection: preparation + multisection)
-KERNELS_PER_REGION = {"panel_qr": 1, "panel_lq": 1, "trail_left": 2, "trail_right": 2, "trail_fused": 1,
+# trailing update: projection + update; chase: sweeps + bidiagonal extraction; bisection:
+# preparation + multisection)
+KERNELS_PER_REGION = {"panel_qr": 1, "panel_lq": 1, "trail_left": 2, "trail_right": 2,
                       "stage_copy": 1, "band_extract": 1, "band2bd": 2, "bisect": 2, "batched": 3}
 
 
@@ -445,11 +430,9 @@ def main():
     e2e_value = world * flops(n, n) / (max_over_ranks(e2e_ms, pg, dev) / 1e3) / 1e9
 
     # ---------------- roofline of the dominant kernel (live CUDA-event timing of its launches)
-    fused = "trail_fused" in trace
-    per_region = dict(KERNELS_PER_REGION, **({"trail_left": 1, "trail_right": 1} if fused else {}))
-    launches = sum(v[0] * per_region.get(k, 1) for k, v in trace.items())
+    launches = sum(v[0] * KERNELS_PER_REGION.get(k, 1) for k, v in trace.items())
     # the trailing update is one memory stream split over its regions: judged as a whole
-    upd_regions = [k for k in ("trail_left", "trail_fused", "trail_right") if k in trace]
+    upd_regions = [k for k in ("trail_left", "trail_right") if k in trace]
     upd_ms = sum(trace[k][1] for k in upd_regions)
     shares = {k: v[1] for k, v in trace.items() if k not in upd_regions}
     if upd_regions:
@@ -466,13 +449,8 @@ def main():
         b = nla.plan_cfg(n, n, nla.F32, side=0)[0]
         hbm = peaks.get("hbm_gbs", 6769.4)
         secs = upd_ms / 1e3
-        if fused:
-            byts = fused_update_bytes_per_step(n, n, b) * args.steps
-            note = ("fused schedule: QR projection read + row-block update + fused pass (QR update below the "
-                    "row block + LQ projection) + LQ update; trailing blocks below 129 MB run from L2")
-        else:
-            byts = (trail_bytes_per_step(n, n, b, 0) + trail_bytes_per_step(n, n, b, 1)) * args.steps
-            note = "3-pass bytes per side (read X twice, write once); trailing blocks below 129 MB run from L2"
+        byts = (trail_bytes_per_step(n, n, b, 0) + trail_bytes_per_step(n, n, b, 1)) * args.steps
+        note = "3-pass bytes per side (read X twice, write once); trailing blocks below 129 MB run from L2"
         achieved = byts / secs / 1e9
         roof = {"kernel": "trailing update (" + " + ".join(upd_regions) + ")", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),

@@ -208,9 +208,7 @@ nla_status nla_bdsvd_vals(int n, const double *dD, const double *dE, void *dS, n
  * stream; nla_trace_read synchronises those events and returns, per kernel
  * class, the number of launches and their summed device time.  Classes:
  * "panel_qr", "panel_lq", "trail_left", "trail_right", "stage_copy",
- * "band_extract", "band2bd", "bisect", "batched", "trail_fused" (the FP32 pass
- * that finishes the QR update below the row block and forms the LQ projection).
- * Tracing adds two event
+ * "band_extract", "band2bd", "bisect", "batched".  Tracing adds two event
  * records per launch; it is off by default. */
 typedef struct {
     const char *name;   /* static string owned by the library */

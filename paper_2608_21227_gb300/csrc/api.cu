@@ -134,75 +134,11 @@ nla_status check_upd(const Stage1Plan &p, int elem) {
     return NLA_OK;
 }
 
-// Auxiliary stream (high priority) and fork/join events for the look-ahead panels,
-// one set per device, created on first use.
-struct Aux {
-    cudaStream_t s = nullptr;
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    std::mutex use;  // held while a call enqueues work on s (events are re-recorded per step)
-};
-Aux *aux_for_device() {
-    static std::mutex mu;
-    static Aux per_dev[64];
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return nullptr;
-    std::lock_guard<std::mutex> lk(mu);
-    Aux &a = per_dev[dev];
-    if (!a.s) {
-        int lo = 0, hi = 0;
-        cudaDeviceGetStreamPriorityRange(&lo, &hi);
-        if (cudaStreamCreateWithPriority(&a.s, cudaStreamNonBlocking, hi) != cudaSuccess) {
-            a.s = nullptr;
-            cudaGetLastError();
-            return nullptr;
-        }
-        for (auto &e : a.ev) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
-    }
-    return &a;
-}
-
-// Algorithm 1 on the column-major M x N matrix X (M >= N), band width b.
-nla_status run_stage1_lookahead(float *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
-                                float *tauq_all, float *taup_all, int *dInfo, cudaStream_t st, Aux &ax);
-// Off by default: measured no gain at 8192 (the update kernels occupy every SM, so the
-// panel's cluster competes with them instead of filling idle SMs).  NLA_LOOKAHEAD=1 enables it.
-bool lookahead_enabled() {
-    static const bool on = [] {
-        const char *v = getenv("NLA_LOOKAHEAD");
-        return v && atoi(v) != 0;
-    }();
-    return on;
-}
-
-// FP32: the QR update of the rows below each row block fused with the LQ
-// projection (one pass over X instead of two).  Off by default (NLA_FUSED=1): the
-// fused pass does 2b FMAs per element and is bound by instruction issue, so at 8192
-// it took 60 ms per SVD where the two passes it replaces take 48 (206.2 vs 193.5 ms).
-bool fused_enabled() {
-    static const bool on = [] {
-        const char *v = getenv("NLA_FUSED");
-        return v && atoi(v) != 0;
-    }();
-    return on;
-}
-
-nla_status run_stage1_fused(float *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
-                            float *tauq_all, float *taup_all, int *dInfo, cudaStream_t st);
 void step_cfgs(const Stage1Plan &p, int Mt, int Nt, nla::UpdCfg &l, nla::UpdCfg &r);
 
 template <typename T>
 nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
                       T *tauq_all, T *taup_all, int *dInfo, cudaStream_t st) {
-    if constexpr (sizeof(T) == 4) {
-        if (p.update == NLA_UPD_NATIVE && (p.b == 16 || p.b == 32 || p.b == 64) && lookahead_enabled()) {
-            if (Aux *ax = aux_for_device()) {
-                std::lock_guard<std::mutex> lk(ax->use);
-                return run_stage1_lookahead(X, ldx, M, N, p, bufs, tauq_all, taup_all, dInfo, st, *ax);
-            }
-        }
-        if (p.update == NLA_UPD_NATIVE && (p.b == 16 || p.b == 32 || p.b == 64) && fused_enabled())
-            return run_stage1_fused(X, ldx, M, N, p, bufs, tauq_all, taup_all, dInfo, st);
-    }
     const int b = p.b;
     nla::PanelCtl ctl{bufs.bar, bufs.part, dInfo};
     const nla::UpdScratch usc{bufs.upd_work, bufs.tickets, dInfo};
@@ -249,152 +185,6 @@ nla_status run_stage1(T *X, long ldx, int M, int N, const Stage1Plan &p, const S
             NLA_LAUNCH(nla::kTrTrailRight, st, nla::trail_right<T>(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, cfr, usc, st),
                      "LQ trailing update");
         }
-    }
-    return NLA_OK;
-}
-
-// Algorithm 1 for FP32 with the TMA-streamed update, panels looked ahead: the
-// update of step k first finishes the b rows (QR side) / b columns (LQ side) the
-// next panel factors, and that panel then runs on the auxiliary stream while the
-// rest of the update streams on the caller's stream (disjoint parts of X).
-nla_status run_stage1_lookahead(float *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
-                                float *tauq_all, float *taup_all, int *dInfo, cudaStream_t st, Aux &ax) {
-    const int b = p.b;
-    nla::PanelCtl ctl{bufs.bar, bufs.part, dInfo};
-    const nla::UpdScratch usc{bufs.upd_work, bufs.tickets, dInfo};
-    float *Tq = reinterpret_cast<float *>(bufs.Tq), *Tp = reinterpret_cast<float *>(bufs.Tp);
-    auto tq_at = [&](int kb) { return tauq_all ? tauq_all + kb : reinterpret_cast<float *>(bufs.tauq); };
-    auto tp_at = [&](int kb) { return taup_all ? taup_all + kb : reinterpret_cast<float *>(bufs.taup); };
-    auto fork = [&](int i) -> nla_status {
-        NLA_CUDA(cudaEventRecord(ax.ev[i], st), "look-ahead fork");
-        NLA_CUDA(cudaStreamWaitEvent(ax.s, ax.ev[i], 0), "look-ahead fork");
-        return NLA_OK;
-    };
-    auto join = [&](int i) -> nla_status {
-        NLA_CUDA(cudaEventRecord(ax.ev[i], ax.s), "look-ahead join");
-        NLA_CUDA(cudaStreamWaitEvent(st, ax.ev[i], 0), "look-ahead join");
-        return NLA_OK;
-    };
-    bool panel_done = false;  // the QR panel of this step already ran (looked ahead)
-    for (int kb = 0; kb < N; kb += b) {
-        const int nb = std::min(b, N - kb);
-        float *panel = X + kb + (long)kb * ldx;
-        if (!panel_done)
-            NLA_LAUNCH(nla::kTrPanelQR, st, nla::panel_factor<float>(panel, 1, ldx, M - kb, nb, tq_at(kb), Tq, ctl, st),
-                       "QR panel");
-        panel_done = false;
-        const int c0 = kb + nb;
-        if (c0 >= N) break;
-        // ---- QR update; the LQ panel of row block kb overlaps its rows below the block
-        float *Xl = X + kb + (long)c0 * ldx;
-        float *rowp = X + kb + (long)c0 * ldx;  // element (kb, c0); LQ panel(r, c) = rowp[c + r*ldx]
-        const bool lq_split = nla::trail_tma_eligible(Xl, ldx, panel, ldx, nb, usc) && nb % 4 == 0;
-        if (lq_split) {
-            NLA_LAUNCH(nla::kTrTrailLeft, st,
-                       nla::trail_tma_project(0, Xl, ldx, M - kb, N - c0, panel, ldx, nb, Tq, p.left, usc, st),
-                       "QR trailing update");
-            NLA_LAUNCH(nla::kTrTrailLeft, st,
-                       nla::trail_tma_apply(0, Xl, ldx, M - kb, N - c0, panel, ldx, nb, 0, nb, p.left, usc, st),
-                       "QR trailing update");
-            nla_status f = fork(0);
-            if (f != NLA_OK) return f;
-            NLA_LAUNCH(nla::kTrPanelLQ, ax.s, nla::panel_factor<float>(rowp, ldx, 1, N - c0, nb, tp_at(kb), Tp, ctl, ax.s),
-                       "LQ panel");
-            NLA_LAUNCH(nla::kTrTrailLeft, st,
-                       nla::trail_tma_apply(0, Xl, ldx, M - kb, N - c0, panel, ldx, nb, nb, M - kb - nb, p.left, usc, st),
-                       "QR trailing update");
-            f = join(1);
-            if (f != NLA_OK) return f;
-        } else {
-            NLA_LAUNCH(nla::kTrTrailLeft, st,
-                       nla::trail_left<float>(Xl, ldx, M - kb, N - c0, panel, ldx, nb, Tq, p.left, usc, st),
-                       "QR trailing update");
-            NLA_LAUNCH(nla::kTrPanelLQ, st, nla::panel_factor<float>(rowp, ldx, 1, N - c0, nb, tp_at(kb), Tp, ctl, st),
-                       "LQ panel");
-        }
-        if (M - c0 <= 0) continue;
-        // ---- LQ update; the next QR panel overlaps its columns right of the next tile column
-        float *Xr = X + c0 + (long)c0 * ldx;
-        const int nb2 = std::min(b, N - c0);
-        const bool qr_split = nla::trail_tma_eligible(Xr, ldx, rowp, ldx, nb, usc) && nb2 % 4 == 0;
-        if (qr_split) {
-            NLA_LAUNCH(nla::kTrTrailRight, st,
-                       nla::trail_tma_project(1, Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.right, usc, st),
-                       "LQ trailing update");
-            NLA_LAUNCH(nla::kTrTrailRight, st,
-                       nla::trail_tma_apply(1, Xr, ldx, M - c0, N - c0, rowp, ldx, nb, 0, nb2, p.right, usc, st),
-                       "LQ trailing update");
-            nla_status f = fork(2);
-            if (f != NLA_OK) return f;
-            float *npanel = X + c0 + (long)c0 * ldx;
-            NLA_LAUNCH(nla::kTrPanelQR, ax.s,
-                       nla::panel_factor<float>(npanel, 1, ldx, M - c0, nb2, tq_at(c0), Tq, ctl, ax.s), "QR panel");
-            NLA_LAUNCH(nla::kTrTrailRight, st,
-                       nla::trail_tma_apply(1, Xr, ldx, M - c0, N - c0, rowp, ldx, nb, nb2, N - c0 - nb2, p.right, usc, st),
-                       "LQ trailing update");
-            f = join(3);
-            if (f != NLA_OK) return f;
-            panel_done = true;
-        } else {
-            NLA_LAUNCH(nla::kTrTrailRight, st,
-                       nla::trail_right<float>(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.right, usc, st),
-                       "LQ trailing update");
-        }
-    }
-    return NLA_OK;
-}
-
-// Algorithm 1 for FP32 with the TMA-streamed update and one fused pass per step:
-// QR panel; QR projection (W' = T^T V^T X); QR update of the b rows the LQ panel
-// factors; LQ panel; fused pass (QR update of the rows below + LQ projection
-// Y' = X U T); LQ update X -= Y' U^T.  Steps the TMA kernels cannot take (ragged
-// band, unaligned blocks) run the separate passes.
-nla_status run_stage1_fused(float *X, long ldx, int M, int N, const Stage1Plan &p, const Stage1Bufs &bufs,
-                            float *tauq_all, float *taup_all, int *dInfo, cudaStream_t st) {
-    const int b = p.b;
-    nla::PanelCtl ctl{bufs.bar, bufs.part, dInfo};
-    const nla::UpdScratch usc{bufs.upd_work, bufs.tickets, dInfo};
-    float *Tq = reinterpret_cast<float *>(bufs.Tq), *Tp = reinterpret_cast<float *>(bufs.Tp);
-    for (int kb = 0; kb < N; kb += b) {
-        const int nb = std::min(b, N - kb);
-        float *tq = tauq_all ? tauq_all + kb : reinterpret_cast<float *>(bufs.tauq);
-        float *tp = taup_all ? taup_all + kb : reinterpret_cast<float *>(bufs.taup);
-        float *panel = X + kb + (long)kb * ldx;
-        NLA_LAUNCH(nla::kTrPanelQR, st, nla::panel_factor<float>(panel, 1, ldx, M - kb, nb, tq, Tq, ctl, st), "QR panel");
-        const int c0 = kb + nb;
-        if (c0 >= N) break;
-        float *Xl = X + kb + (long)c0 * ldx;  // rows kb.., columns c0..
-        float *rowp = Xl;                      // LQ panel(r, c) = rowp[c + r*ldx]
-        float *Xr = X + c0 + (long)c0 * ldx;
-        const bool fuse = M - c0 > 0 && nb == b && nla::trail_tma_fused_ok(nb, p.right) &&
-                          nla::tma_cfg_valid(nb, p.left) && nla::trail_tma_eligible(Xl, ldx, panel, ldx, nb, usc) &&
-                          nla::trail_tma_eligible(Xr, ldx, rowp, ldx, nb, usc);
-        if (!fuse) {
-            NLA_LAUNCH(nla::kTrTrailLeft, st,
-                       nla::trail_left<float>(Xl, ldx, M - kb, N - c0, panel, ldx, nb, Tq, p.left, usc, st),
-                       "QR trailing update");
-            NLA_LAUNCH(nla::kTrPanelLQ, st, nla::panel_factor<float>(rowp, ldx, 1, N - c0, nb, tp, Tp, ctl, st),
-                       "LQ panel");
-            if (M - c0 > 0)
-                NLA_LAUNCH(nla::kTrTrailRight, st,
-                           nla::trail_right<float>(Xr, ldx, M - c0, N - c0, rowp, ldx, nb, Tp, p.right, usc, st),
-                           "LQ trailing update");
-            continue;
-        }
-        NLA_LAUNCH(nla::kTrTrailLeft, st,
-                   nla::trail_tma_project(0, Xl, ldx, M - kb, N - c0, panel, ldx, nb, Tq, p.left, usc, st),
-                   "QR projection");
-        NLA_LAUNCH(nla::kTrTrailLeft, st,
-                   nla::trail_tma_apply(0, Xl, ldx, M - kb, N - c0, panel, ldx, nb, 0, nb, p.left, usc, st),
-                   "QR update of the row block");
-        NLA_LAUNCH(nla::kTrPanelLQ, st, nla::panel_factor<float>(rowp, ldx, 1, N - c0, nb, tp, Tp, ctl, st), "LQ panel");
-        const float *ylq = nullptr;
-        NLA_LAUNCH(nla::kTrTrailFused, st,
-                   nla::trail_tma_fused(Xl, ldx, M - kb, N - c0, panel, ldx, nb, rowp, ldx, Tp, p.right, usc, st, &ylq),
-                   "QR update + LQ projection");
-        NLA_LAUNCH(nla::kTrTrailRight, st,
-                   nla::trail_tma_apply(1, Xr, ldx, M - c0, N - c0, rowp, ldx, nb, 0, N - c0, p.right, usc, st, ylq),
-                   "LQ trailing update");
     }
     return NLA_OK;
 }

@@ -68,24 +68,13 @@ cudaError_t trail_tma(int side, float *X, long ldx, int M, int N, const float *V
                       const UpdCfg &c, const UpdScratch &sc, cudaStream_t st);
 // The same in two parts: the projection (step 1 + T, into the scratch) and the
 // update of rows [off, off + len) (side 0) / columns [off, off + len) (side 1) of
-// the M x N block; off a multiple of 4.  Parts of one projection may run in any
-// order and on different streams.
+// the M x N block; off a multiple of 4.
 cudaError_t trail_tma_project(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb,
                               const float *Tm, const UpdCfg &c, const UpdScratch &sc, cudaStream_t st);
 // fin_in (side 1 only): Y' to apply instead of the one trail_tma_project left in the scratch.
 cudaError_t trail_tma_apply(int side, float *X, long ldx, int M, int N, const float *V, long ldv, int nb, int off,
                             int len, const UpdCfg &c, const UpdScratch &sc, cudaStream_t st,
                             const float *fin_in = nullptr);
-// One pass that finishes the QR update of Xl (Ml x Nl, V column-major at V, after
-// trail_tma_project(0, Xl, ...) and the update of its first nb rows) on rows nb ..
-// Ml-1 and, from the updated values, forms the LQ projection Y' = X U T_lq of those
-// rows (U stored as side 1's V at Vt, ldvt).  *y_out receives Y' for
-// trail_tma_apply(1, ..., fin_in = *y_out) on the same rows.  Needs a scratch of
-// (kMaxSplit + 2) x 64 x max(M, N) elements.
-bool trail_tma_fused_ok(int nb, const UpdCfg &c);
-cudaError_t trail_tma_fused(float *Xl, long ldx, int Ml, int Nl, const float *V, long ldv, int nb, const float *Vt,
-                            long ldvt, const float *Tlq, const UpdCfg &c, const UpdScratch &sc, cudaStream_t st,
-                            const float **y_out);
 
 // QR side: X (M x N at X, ldx) <- (I - V T V^T)^T X, V = unit lower M x nb at Vp (ldv).
 template <typename T>

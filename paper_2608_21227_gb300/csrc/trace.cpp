@@ -10,8 +10,7 @@
 namespace {
 
 const char *const kNames[nla::kTraceClasses] = {"panel_qr",     "panel_lq", "trail_left", "trail_right", "stage_copy",
-                                                "band_extract", "band2bd",  "bisect",     "batched",
-                                                "trail_fused"};
+                                                "band_extract", "band2bd",  "bisect",     "batched"};
 
 struct Rec {
     int cls;

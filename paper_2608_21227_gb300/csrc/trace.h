@@ -14,7 +14,6 @@ enum TraceClass {
     kTrBand2bd,
     kTrBisect,
     kTrBatched,
-    kTrTrailFused,
     kTraceClasses
 };
 

@@ -412,7 +412,7 @@ __global__ void right_x_kernel(T *__restrict__ X, long ldx, int M, int N, const 
 // -------------------------------------------------------------------- dispatch
 constexpr int kMaxSplit = 8;
 
-// partial slabs, the projection's W' / Y', and (fused FP32 pass) a second Y'
+// partial slabs, the projection's W' / Y', and room for the mixed path's line exponents
 size_t tiled_scratch_elems(int M, int N) { return (size_t)(kMaxSplit + 2) * 64 * (size_t)std::max(std::max(M, N), 1); }
 size_t tiled_tickets(int M, int N) { return (size_t)std::max(M, N) / 32 + 2; }
 

@@ -21,9 +21,6 @@
 //   qr_proj_tc    W = V^T X on the tensor cores (the default QR projection):
 //                 tcgen05 kind::tf32 MMAs on the TMA boxes, FP32 accuracy from
 //                 the three-term hi/lo split, accumulator in TMEM.
-//   qr_update_lq_proj  (opt-in) the QR update of the rows below the LQ panel's
-//                 row block and, from the updated values, the LQ projection, in
-//                 one pass over X.
 //
 // The projections are split over the long dimension; the last block of each
 // strip (atomic ticket, nobody waits) sums the partials in a fixed order and
@@ -894,206 +891,6 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
     }
 }
 
-// ------------------------------------------------------------------ qr_update_lq_proj
-// One pass over the rows below the row block that the LQ panel factors: the QR
-// update X -= V W'^T of those rows and, from the updated values, the LQ
-// projection Y = X U (U = the LQ reflectors, unit lower in (column, k)).  Block
-// (strip, split): 32*RL rows x the columns of split s, streamed in stages of tc
-// columns (X boxes, the stage's W'^T rows and U rows); updated stages go back by
-// TMA store; partial Y per split, the last block of a strip forms Y' = Y T
-// (T of the LQ panel) -> fin_out[k*M + i].  Rows of X start `moff` rows below
-// V's first row (V's unit diagonal lies above them when moff >= NB).
-template <int NB>
-__global__ void __launch_bounds__(kMaxThreads, 1)
-qr_update_lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ,
-                         const __grid_constant__ CUtensorMap tmU, int M, int N, const float *__restrict__ Pv, long ldp,
-                         int moff, const float *__restrict__ Tm, int tcols, int NC, int S, int Ns, float *part,
-                         float *fin_out, unsigned int *tickets, int *info) {
-    pdl_wait();
-    pdl_trigger();
-    constexpr int RL = 64 / NB, H = 32 * RL;
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[kMaxStages], done[kMaxStages];
-    __shared__ int sh_last, sh_abort;
-    unsigned char *base = align1k(smem_raw);
-    const int xbytes = tcols * 128, qbytes = tcols * NB * 4;
-    const int stage = RL * xbytes + 2 * qbytes;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i0 = blockIdx.x * H, hr = min(H, M - i0);
-    const int s = blockIdx.y, nsplit = gridDim.y;
-    const int cbeg = s * Ns, cend = min(N, cbeg + Ns);
-    const int nt = (cend - cbeg + tcols - 1) / tcols;
-    if (tid == 0) {
-        for (int i = 0; i < S; ++i) {
-            tc::mbar_init(&full[i], 1);
-            tc::mbar_init(&done[i], NC);
-        }
-        sh_abort = 0;
-        tma::fence_init();
-        tma::prefetch_map(&tmX);
-        tma::prefetch_map(&tmQ);
-        tma::prefetch_map(&tmU);
-    }
-    __syncthreads();
-
-    if (warp == 0) {
-        if (lane == 0) {
-            int issued = 0, stored = 0;
-            bool ok = true;
-            for (int t = 0; t < nt && ok; ++t) {
-                const int st = t % S;
-                unsigned char *sb = base + (size_t)st * stage;
-                if (t >= S) {
-                    // write back the tile that used this stage, then reuse it
-                    if (!tc::mbar_wait(&done[st], (uint32_t)(((t / S) - 1) & 1), info)) {
-                        sh_abort = 1;
-                        ok = false;
-                        break;
-                    }
-                    const int cbo = cbeg + (t - S) * tcols;
-                    for (int bx = 0; bx < RL; ++bx) tma::store_2d(&tmX, i0 + bx * kBoxRows, cbo, sb + bx * xbytes);
-                    tma::commit();
-                    stored = t - S + 1;
-                    tma::wait_read_all();
-                }
-                tma::expect_tx(&full[st], (uint32_t)stage);
-                const int cb = cbeg + t * tcols;
-                for (int bx = 0; bx < RL; ++bx) tma::load_2d(sb + bx * xbytes, &tmX, i0 + bx * kBoxRows, cb, &full[st]);
-                tma::load_2d(sb + RL * xbytes, &tmQ, 0, cb, &full[st]);
-                tma::load_2d(sb + RL * xbytes + qbytes, &tmU, 0, cb, &full[st]);
-                issued = t + 1;
-            }
-            for (int t = stored; ok && t < issued; ++t) {
-                const int st = t % S;
-                if (!tc::mbar_wait(&done[st], (uint32_t)((t / S) & 1), info)) {
-                    sh_abort = 1;
-                    ok = false;
-                    break;
-                }
-                const int cbo = cbeg + t * tcols;
-                for (int bx = 0; bx < RL; ++bx)
-                    tma::store_2d(&tmX, i0 + bx * kBoxRows, cbo, base + (size_t)st * stage + bx * xbytes);
-                tma::commit();
-            }
-            if (!ok) drain_loads(full, issued, S, info);
-            tma::wait_all();
-        }
-    } else {
-        const int cw = warp - 1;
-        // V(lane's rows, :) in registers
-        float p[RL][NB];
-#pragma unroll
-        for (int a = 0; a < RL; ++a) {
-            const int i = i0 + RL * lane + a;
-#pragma unroll
-            for (int k = 0; k < NB; ++k)
-                p[a][k] = i < M ? unit_lower(moff + i, k, moff + i > k ? __ldg(Pv + i + (long)k * ldp) : 0.f) : 0.f;
-        }
-        float acc[RL][NB];
-#pragma unroll
-        for (int a = 0; a < RL; ++a)
-#pragma unroll
-            for (int k = 0; k < NB; ++k) acc[a][k] = 0.f;
-        for (int t = 0; t < nt; ++t) {
-            const int st = t % S;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
-            unsigned char *sb = base + (size_t)st * stage;
-            const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
-            const float *us = reinterpret_cast<const float *>(sb + RL * xbytes + qbytes);
-            const int cb = cbeg + t * tcols;
-            for (int j = cw; j < tcols; j += NC) {
-                float *xp = xptr_rows<RL>(sb, tcols, j, lane);
-                float x[RL];
-                ld_rows<RL>(xp, x);
-                float d[RL][4];  // four independent partial sums per row: short FMA chains
-#pragma unroll
-                for (int a = 0; a < RL; ++a) d[a][0] = d[a][1] = d[a][2] = d[a][3] = 0.f;
-#pragma unroll
-                for (int k4 = 0; k4 < NB; k4 += 4) {
-                    const float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
-#pragma unroll
-                    for (int a = 0; a < RL; ++a) {
-                        d[a][0] = fmaf(p[a][k4], q.x, d[a][0]);
-                        d[a][1] = fmaf(p[a][k4 + 1], q.y, d[a][1]);
-                        d[a][2] = fmaf(p[a][k4 + 2], q.z, d[a][2]);
-                        d[a][3] = fmaf(p[a][k4 + 3], q.w, d[a][3]);
-                    }
-                }
-#pragma unroll
-                for (int a = 0; a < RL; ++a) x[a] -= (d[a][0] + d[a][1]) + (d[a][2] + d[a][3]);
-                st_rows<RL>(xp, x);
-                const int c = cb + j;  // column of X = row of U (unit diagonal at c == k)
-#pragma unroll
-                for (int k4 = 0; k4 < NB; k4 += 4) {
-                    float4 u = *reinterpret_cast<const float4 *>(us + j * NB + k4);
-                    if (cb < NB) {
-                        u.x = unit_lower(c, k4, u.x), u.y = unit_lower(c, k4 + 1, u.y);
-                        u.z = unit_lower(c, k4 + 2, u.z), u.w = unit_lower(c, k4 + 3, u.w);
-                    }
-#pragma unroll
-                    for (int a = 0; a < RL; ++a) {
-                        acc[a][k4] = fmaf(x[a], u.x, acc[a][k4]);
-                        acc[a][k4 + 1] = fmaf(x[a], u.y, acc[a][k4 + 1]);
-                        acc[a][k4 + 2] = fmaf(x[a], u.z, acc[a][k4 + 2]);
-                        acc[a][k4 + 3] = fmaf(x[a], u.w, acc[a][k4 + 3]);
-                    }
-                }
-            }
-            tc::fence_async_smem();  // this lane's shared-memory writes -> visible to the TMA store
-            __syncwarp();
-            if (lane == 0) tma::arrive(&done[st]);
-        }
-        // reduce the NC column groups in a fixed order into red[NB][H] (after the
-        // producer has drained every stage: red reuses stage memory)
-        float *red = reinterpret_cast<float *>(base + (size_t)S * stage);
-        consumers_sync(NC);
-        for (int g = 0; g < NC; ++g) {
-            if (cw == g) {
-#pragma unroll
-                for (int a = 0; a < RL; ++a)
-#pragma unroll
-                    for (int k = 0; k < NB; ++k) {
-                        float *pp = red + k * H + RL * lane + a;
-                        *pp = g == 0 ? acc[a][k] : *pp + acc[a][k];
-                    }
-            }
-            consumers_sync(NC);
-        }
-        for (int idx = tid - 32; idx < NB * H; idx += NC * 32) {
-            const int k = idx / H, i = idx % H;
-            if (i < hr) part[((size_t)s * NB + k) * M + i0 + i] = red[idx];
-        }
-    }
-    __threadfence();
-    __syncthreads();
-    if (sh_abort) return;
-    if (tid == 0) sh_last = atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(nsplit - 1);
-    __syncthreads();
-    if (!sh_last) return;
-    __threadfence();
-    float *Y = reinterpret_cast<float *>(base + (size_t)S * stage);
-    for (int idx = tid; idx < NB * H; idx += blockDim.x) {
-        const int k = idx / H, i = idx % H;
-        float sum = 0.f;
-        if (i < hr)
-#pragma unroll
-            for (int q = 0; q < kMaxSplitTma; ++q)  // (all partial loads in flight at once)
-                if (q < nsplit) sum += __ldcg(part + ((size_t)q * NB + k) * M + i0 + i);
-        Y[idx] = sum;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < NB * H; idx += blockDim.x) {
-        const int k = idx / H, i = idx % H;
-        if (i >= hr) continue;
-        float sum = 0.f;
-#pragma unroll
-        for (int j = 0; j < NB; ++j)
-            if (j <= k) sum = fmaf(Y[j * H + i], __ldg(Tm + j + (size_t)k * NB), sum);
-        fin_out[(size_t)k * M + i0 + i] = sum;
-    }
-    if (tid == 0) tickets[blockIdx.x] = 0u;
-}
-
 // ------------------------------------------------------------------ host launch
 int splits_for(int nstrip, int units, int waves) {
     const int target = waves * device_sm_count();
@@ -1274,37 +1071,6 @@ cudaError_t right_apply_nb(float *X, long ldx, int M, int N, const float *Vt, lo
                       fin, 0L, sh.tc, sh.nc, sh.stages, Ns, off, sc.info);
 }
 
-// QR update of the M x N block below the row block + LQ projection (Y' -> fout)
-template <int NB>
-size_t fused_smem(const TmaShape &sh, int S) {
-    constexpr int H = 32 * (64 / NB);
-    return (size_t)S * (stage_bytes_cols(NB, sh.tc) + (size_t)sh.tc * NB * 4) + (size_t)NB * H * 4 + 1024;
-}
-
-template <int NB>
-cudaError_t fused_nb(float *X, long ldx, int M, int N, const float *V, long ldv, int moff, const float *Vt, long ldvt,
-                     const float *Tm, const float *finq, float *fout, const TmaShape &sh, const UpdScratch &sc,
-                     cudaStream_t st) {
-    float *part = reinterpret_cast<float *>(sc.work);
-    CUtensorMap mX, mQ, mU;
-    if (!tma_encode_2d(&mX, X, 4, M, N, ldx * 4, kBoxRows, sh.tc, true) ||
-        !tma_encode_2d(&mQ, finq, 4, NB, N, NB * 4, NB, sh.tc, false) ||
-        !tma_encode_2d(&mU, Vt, 4, NB, N, ldvt * 4, NB, sh.tc, false))
-        return cudaErrorInvalidValue;
-    constexpr int H = 32 * (64 / NB);
-    int S = sh.stages;
-    while (S > 2 && fused_smem<NB>(sh, S) > kTmaSmemLimit) --S;
-    if (fused_smem<NB>(sh, S) > kTmaSmemLimit) return cudaErrorInvalidConfiguration;
-    static PerDeviceOnce attr;
-    allow_max_smem(qr_update_lq_proj_kernel<NB>, attr);
-    const int nstrip = (M + H - 1) / H;
-    int nsplit = splits_for(nstrip, (N + sh.tc - 1) / sh.tc, sh.waves);
-    const int Ns = ((N + nsplit - 1) / nsplit + sh.tc - 1) / sh.tc * sh.tc;
-    nsplit = (N + Ns - 1) / Ns;
-    return launch_pdl(qr_update_lq_proj_kernel<NB>, dim3(nstrip, nsplit), dim3(32 * (sh.nc + 1)), fused_smem<NB>(sh, S),
-                      st, mX, mQ, mU, M, N, V, ldv, moff, Tm, sh.tc, sh.nc, S, Ns, part, fout, sc.tickets, sc.info);
-}
-
 }  // namespace
 
 size_t tma_cfg_smem(int nb, const UpdCfg &c) {
@@ -1363,38 +1129,6 @@ cudaError_t trail_tma_apply(int side, float *X, long ldx, int M, int N, const fl
         case 16: return right_apply_nb<16>(X, ldx, M, N, V, ldv, off, len, sh, sc, st, fin_in);
         case 32: return right_apply_nb<32>(X, ldx, M, N, V, ldv, off, len, sh, sc, st, fin_in);
         default: return right_apply_nb<64>(X, ldx, M, N, V, ldv, off, len, sh, sc, st, fin_in);
-    }
-}
-
-bool trail_tma_fused_ok(int nb, const UpdCfg &c) {
-    if ((nb != 16 && nb != 32 && nb != 64) || !tma_cfg_valid(nb, c)) return false;
-    const TmaShape sh = shape_of(nb, c);
-    switch (nb) {
-        case 16: return fused_smem<16>(sh, 2) <= kTmaSmemLimit;
-        case 32: return fused_smem<32>(sh, 2) <= kTmaSmemLimit;
-        default: return fused_smem<64>(sh, 2) <= kTmaSmemLimit;
-    }
-}
-
-cudaError_t trail_tma_fused(float *Xl, long ldx, int Ml, int Nl, const float *V, long ldv, int nb, const float *Vt,
-                            long ldvt, const float *Tlq, const UpdCfg &c, const UpdScratch &sc, cudaStream_t st,
-                            const float **y_out) {
-    *y_out = nullptr;
-    const int M = Ml - nb;
-    if (M <= 0 || Nl <= 0) return cudaSuccess;
-    float *Xr = Xl + nb;
-    if (!trail_tma_eligible(Xr, ldx, V + nb, ldv, nb, sc) || !trail_tma_eligible(Vt, ldvt, Vt, ldvt, nb, sc) ||
-        !trail_tma_fused_ok(nb, c))
-        return cudaErrorInvalidConfiguration;
-    const TmaShape sh = shape_of(nb, c);
-    float *part = reinterpret_cast<float *>(sc.work);
-    const float *finq = part + (size_t)kMaxSplitTma * 64 * std::max(Ml, Nl);  // W' of the QR projection of Xl
-    float *fout = const_cast<float *>(finq) + (size_t)64 * std::max(Ml, Nl);
-    *y_out = fout;
-    switch (nb) {
-        case 16: return fused_nb<16>(Xr, ldx, M, Nl, V + nb, ldv, nb, Vt, ldvt, Tlq, finq, fout, sh, sc, st);
-        case 32: return fused_nb<32>(Xr, ldx, M, Nl, V + nb, ldv, nb, Vt, ldvt, Tlq, finq, fout, sh, sc, st);
-        default: return fused_nb<64>(Xr, ldx, M, Nl, V + nb, ldv, nb, Vt, ldvt, Tlq, finq, fout, sh, sc, st);
     }
 }
 

@@ -1,7 +1,6 @@
 """Alternative execution paths that environment switches select (read once per
-process, so each runs in a subprocess): the SIMT QR projection instead of the
-tensor-core one, the look-ahead stage-1 driver, the fused FP32 update pass
-(QR update below the row block + LQ projection), the one-sweep-per-block bulge chase, the grid-wide panel, the
+process, so each runs in a subprocess): the SIMT projections instead of the
+tensor-core ones, the one-sweep-per-block bulge chase, the grid-wide panel, the
 shared-memory cluster panel, programmatic dependent launch and other sweep-group sizes.  Each must give the same
 singular values as the FP64 oracle within the parity tolerance."""
 import json
@@ -37,13 +36,11 @@ print(json.dumps(out))
 
 VARIANTS = {
     "simt_projection": {"NLA_PROJ_TC": "0"},
-    "lookahead": {"NLA_LOOKAHEAD": "1"},
     "chase_one_sweep_per_block": {"NLA_CHASE_GROUP": "0"},
     "chase_group_4": {"NLA_CHASE_GROUP": "4"},
     "grid_panel": {"NLA_PANEL_CLUSTER": "0"},
     "shared_memory_cluster_panel": {"NLA_PANEL_REG": "0"},
     "programmatic_dependent_launch": {"NLA_PDL": "1"},
-    "fused_fp32_update": {"NLA_FUSED": "1"},
 }
 
 
