@@ -739,12 +739,14 @@ lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 }
 
 // ------------------------------------------------------------------ strip_update
-// Block (strip, cs): X(strip rows, columns of split cs) -= P(strip rows, :) Q(cols, :)^T.
+// Persistent: block b takes work items b, b + G, ... (item = strip of 32*RL rows x one
+// column chunk of Ns columns) and streams their tiles through one ring of S stages.
+// Item: X(strip rows, chunk columns) -= P(strip rows, :) Q(cols, :)^T.
 // SIDE 0 (QR): P = V (unit lower, column-major at Pv, ld ldp), Q = W'^T from
 // fin[c*NB + k].  SIDE 1 (LQ): P = Y' at Pv[k*M + i] (ldp unused), Q = V
 // stored by rows (unit lower in (c, k)).
 template <int NB, int SIDE>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __maxnreg__(136)
 strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int M, int N,
                     const float *__restrict__ Pv, long ldp, int tcols, int NC, int S, int Ns, int moff, int *info) {
     pdl_wait();
@@ -757,9 +759,7 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
     const int xbytes = tcols * 128, qbytes = tcols * NB * 4;
     const int stage = RL * xbytes + qbytes;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int i0 = blockIdx.x * H;
-    const int cbeg = blockIdx.y * Ns, cend = min(N, cbeg + Ns);
-    const int nt = (cend - cbeg + tcols - 1) / tcols;
+    const int nstrip = (M + H - 1) / H, ncs = (N + Ns - 1) / Ns, nitems = nstrip * ncs;
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
             tc::mbar_init(&full[i], 1);
@@ -774,30 +774,35 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0, stored = 0;
+            // ring entry t holds tile (row i0, column cb) until it is stored back
+            int ti0[kMaxStages], tcb[kMaxStages];
+            int g = 0, stored = 0;
             bool ok = true;
-            for (int t = 0; t < nt && ok; ++t) {
-                const int st = t % S;
-                unsigned char *sb = base + (size_t)st * stage;
-                if (t >= S) {
-                    // write back the tile that used this stage, then reuse it
-                    if (!tc::mbar_wait(&done[st], (uint32_t)(((t / S) - 1) & 1), info)) {
-                        sh_abort = 1;
-                        ok = false;
-                        break;
+            for (int it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
+                const int i0 = (it / ncs) * H, cbeg = (it % ncs) * Ns, cend = min(N, cbeg + Ns);
+                for (int cb = cbeg; cb < cend; cb += tcols, ++g) {
+                    const int st = g % S;
+                    unsigned char *sb = base + (size_t)st * stage;
+                    if (g >= S) {
+                        // write back the tile that used this stage, then reuse it
+                        if (!tc::mbar_wait(&done[st], (uint32_t)(((g / S) - 1) & 1), info)) {
+                            sh_abort = 1;
+                            ok = false;
+                            break;
+                        }
+                        for (int bx = 0; bx < RL; ++bx) tma::store_2d(&tmX, ti0[st] + bx * kBoxRows, tcb[st], sb + bx * xbytes);
+                        tma::commit();
+                        stored = g - S + 1;
+                        tma::wait_read_all();
                     }
-                    const int cbo = cbeg + (t - S) * tcols;
-                    for (int bx = 0; bx < RL; ++bx) tma::store_2d(&tmX, i0 + bx * kBoxRows, cbo, sb + bx * xbytes);
-                    tma::commit();
-                    stored = t - S + 1;
-                    tma::wait_read_all();
+                    tma::expect_tx(&full[st], (uint32_t)stage);
+                    for (int bx = 0; bx < RL; ++bx) tma::load_2d(sb + bx * xbytes, &tmX, i0 + bx * kBoxRows, cb, &full[st]);
+                    tma::load_2d(sb + RL * xbytes, &tmQ, 0, cb, &full[st]);
+                    ti0[st] = i0;
+                    tcb[st] = cb;
                 }
-                tma::expect_tx(&full[st], (uint32_t)stage);
-                const int cb = cbeg + t * tcols;
-                for (int bx = 0; bx < RL; ++bx) tma::load_2d(sb + bx * xbytes, &tmX, i0 + bx * kBoxRows, cb, &full[st]);
-                tma::load_2d(sb + RL * xbytes, &tmQ, 0, cb, &full[st]);
-                issued = t + 1;
             }
+            const int issued = g;
             for (int t = stored; ok && t < issued; ++t) {
                 const int st = t % S;
                 if (!tc::mbar_wait(&done[st], (uint32_t)((t / S) & 1), info)) {
@@ -805,9 +810,8 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
                     ok = false;
                     break;
                 }
-                const int cbo = cbeg + t * tcols;
                 for (int bx = 0; bx < RL; ++bx)
-                    tma::store_2d(&tmX, i0 + bx * kBoxRows, cbo, base + (size_t)st * stage + bx * xbytes);
+                    tma::store_2d(&tmX, ti0[st] + bx * kBoxRows, tcb[st], base + (size_t)st * stage + bx * xbytes);
                 tma::commit();
             }
             if (!ok) drain_loads(full, issued, S, info);
@@ -815,78 +819,86 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
         }
     } else {
         const int cw = warp - 1;
-        // P(lane's rows, :) in registers
-        float p[RL][NB];
+        int g = 0;
+        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+            const int i0 = (it / ncs) * H, cbeg = (it % ncs) * Ns, cend = min(N, cbeg + Ns);
+            // P(lane's rows, :) in registers
+            float p[RL][NB];
 #pragma unroll
-        for (int a = 0; a < RL; ++a) {
-            const int i = i0 + RL * lane + a;
+            for (int a = 0; a < RL; ++a) {
+                const int i = i0 + RL * lane + a;
 #pragma unroll
-            for (int k = 0; k < NB; ++k) {
-                float v = 0.f;
-                if (i < M) {
-                    if constexpr (SIDE == 0)
-                        v = unit_lower(moff + i, k, moff + i > k ? __ldg(Pv + i + (long)k * ldp) : 0.f);
-                    else
-                        v = __ldg(Pv + (size_t)k * M + i);
+                for (int k = 0; k < NB; ++k) {
+                    float v = 0.f;
+                    if (i < M) {
+                        if constexpr (SIDE == 0)
+                            v = unit_lower(moff + i, k, moff + i > k ? __ldg(Pv + i + (long)k * ldp) : 0.f);
+                        else
+                            v = __ldg(Pv + (size_t)k * M + i);
+                    }
+                    p[a][k] = v;
                 }
-                p[a][k] = v;
             }
-        }
-        for (int t = 0; t < nt; ++t) {
-            const int st = t % S;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
-            unsigned char *sb = base + (size_t)st * stage;
-            const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
-            const int cb = cbeg + t * tcols;
-            if (SIDE == 0 || moff + cb >= NB) {  // no column of this stage meets V's unit diagonal
+            bool ok = true;
+            for (int cb = cbeg; cb < cend; cb += tcols, ++g) {
+                const int st = g % S;
+                if (!tc::mbar_wait_warp(&full[st], (uint32_t)((g / S) & 1), info) || *(volatile int *)&sh_abort) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *sb = base + (size_t)st * stage;
+                const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
+                if (SIDE == 0 || moff + cb >= NB) {  // no column of this stage meets V's unit diagonal
 #pragma unroll 2
-                for (int j = cw; j < tcols; j += NC) {
-                    float *xp = xptr_rows<RL>(sb, tcols, j, lane);
-                    float x[RL];
-                    ld_rows<RL>(xp, x);
-                    float d[RL][4];  // four independent partial sums per row: short FMA chains
+                    for (int j = cw; j < tcols; j += NC) {
+                        float *xp = xptr_rows<RL>(sb, tcols, j, lane);
+                        float x[RL];
+                        ld_rows<RL>(xp, x);
+                        float d[RL][4];  // four independent partial sums per row: short FMA chains
 #pragma unroll
-                    for (int a = 0; a < RL; ++a) d[a][0] = d[a][1] = d[a][2] = d[a][3] = 0.f;
+                        for (int a = 0; a < RL; ++a) d[a][0] = d[a][1] = d[a][2] = d[a][3] = 0.f;
 #pragma unroll
-                    for (int k4 = 0; k4 < NB; k4 += 4) {
-                        const float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
+                        for (int k4 = 0; k4 < NB; k4 += 4) {
+                            const float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
 #pragma unroll
-                        for (int a = 0; a < RL; ++a) {
-                            d[a][0] = fmaf(p[a][k4], q.x, d[a][0]);
-                            d[a][1] = fmaf(p[a][k4 + 1], q.y, d[a][1]);
-                            d[a][2] = fmaf(p[a][k4 + 2], q.z, d[a][2]);
-                            d[a][3] = fmaf(p[a][k4 + 3], q.w, d[a][3]);
+                            for (int a = 0; a < RL; ++a) {
+                                d[a][0] = fmaf(p[a][k4], q.x, d[a][0]);
+                                d[a][1] = fmaf(p[a][k4 + 1], q.y, d[a][1]);
+                                d[a][2] = fmaf(p[a][k4 + 2], q.z, d[a][2]);
+                                d[a][3] = fmaf(p[a][k4 + 3], q.w, d[a][3]);
+                            }
                         }
+#pragma unroll
+                        for (int a = 0; a < RL; ++a) x[a] -= (d[a][0] + d[a][1]) + (d[a][2] + d[a][3]);
+                        st_rows<RL>(xp, x);
                     }
+                } else {
+                    for (int j = cw; j < tcols; j += NC) {
+                        float *xp = xptr_rows<RL>(sb, tcols, j, lane);
+                        float x[RL];
+                        ld_rows<RL>(xp, x);
+                        const int c = moff + cb + j;  // global column: V's unit diagonal
 #pragma unroll
-                    for (int a = 0; a < RL; ++a) x[a] -= (d[a][0] + d[a][1]) + (d[a][2] + d[a][3]);
-                    st_rows<RL>(xp, x);
-                }
-            } else {
-                for (int j = cw; j < tcols; j += NC) {
-                    float *xp = xptr_rows<RL>(sb, tcols, j, lane);
-                    float x[RL];
-                    ld_rows<RL>(xp, x);
-                    const int c = moff + cb + j;  // global column: V's unit diagonal
+                        for (int k4 = 0; k4 < NB; k4 += 4) {
+                            float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
+                            q.x = unit_lower(c, k4, q.x), q.y = unit_lower(c, k4 + 1, q.y);
+                            q.z = unit_lower(c, k4 + 2, q.z), q.w = unit_lower(c, k4 + 3, q.w);
 #pragma unroll
-                    for (int k4 = 0; k4 < NB; k4 += 4) {
-                        float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
-                        q.x = unit_lower(c, k4, q.x), q.y = unit_lower(c, k4 + 1, q.y);
-                        q.z = unit_lower(c, k4 + 2, q.z), q.w = unit_lower(c, k4 + 3, q.w);
-#pragma unroll
-                        for (int a = 0; a < RL; ++a) {
-                            x[a] = fmaf(-p[a][k4], q.x, x[a]);
-                            x[a] = fmaf(-p[a][k4 + 1], q.y, x[a]);
-                            x[a] = fmaf(-p[a][k4 + 2], q.z, x[a]);
-                            x[a] = fmaf(-p[a][k4 + 3], q.w, x[a]);
+                            for (int a = 0; a < RL; ++a) {
+                                x[a] = fmaf(-p[a][k4], q.x, x[a]);
+                                x[a] = fmaf(-p[a][k4 + 1], q.y, x[a]);
+                                x[a] = fmaf(-p[a][k4 + 2], q.z, x[a]);
+                                x[a] = fmaf(-p[a][k4 + 3], q.w, x[a]);
+                            }
                         }
+                        st_rows<RL>(xp, x);
                     }
-                    st_rows<RL>(xp, x);
                 }
+                tc::fence_async_smem();  // this lane's shared-memory writes -> visible to the TMA store
+                __syncwarp();
+                if (lane == 0) tma::arrive(&done[st]);
             }
-            tc::fence_async_smem();  // this lane's shared-memory writes -> visible to the TMA store
-            __syncwarp();
-            if (lane == 0) tma::arrive(&done[st]);
+            if (!ok) break;
         }
     }
 }
@@ -993,6 +1005,36 @@ cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long 
     return cudaGetLastError();
 }
 
+// Persistent grid of the strip update: as many blocks as the SMs hold (occupancy at
+// this shared-memory size), items = (strips of H rows) x (column chunks); the chunk
+// count is the one (at most `waves` chunks per block slot) whose items fill the block
+// slots best, ties to fewer chunks.
+template <typename K>
+void strip_grid(K kernel, int M, int N, int H, const TmaShape &sh, size_t smem, int &grid, int &Ns) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * (sh.nc + 1), smem) != cudaSuccess ||
+        per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    const int slots = per_sm * device_sm_count();
+    const int nstrip = (M + H - 1) / H, ntile = (N + sh.tc - 1) / sh.tc;
+    const int maxc = std::max(1, std::min(ntile, (sh.waves * slots + nstrip - 1) / nstrip));
+    int ncs = 1;
+    double best = -1.0;
+    for (int c = 1; c <= maxc; ++c) {
+        const long items = (long)nstrip * c;
+        const double eff = (double)items / ((double)((items + slots - 1) / slots) * slots);
+        if (eff > best + 1e-9) {
+            best = eff;
+            ncs = c;
+        }
+    }
+    Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
+    ncs = (N + Ns - 1) / Ns;
+    grid = std::min(nstrip * ncs, slots);
+}
+
 // pass 2 on rows [off, off + len) of the M x N trailing block: X -= V W'
 template <int NB>
 cudaError_t left_apply_nb(float *X, long ldx, int M, int N, const float *V, long ldv, int off, int len,
@@ -1008,14 +1050,10 @@ cudaError_t left_apply_nb(float *X, long ldx, int M, int N, const float *V, long
         return cudaErrorInvalidValue;
     static PerDeviceOnce attr;
     allow_max_smem(strip_update_kernel<NB, 0>, attr);
-    constexpr int H = 32 * (64 / NB);
-    const int stage = stage_bytes_cols(NB, sh.tc);
-    const int nstrip = (len + H - 1) / H;
-    int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (N + sh.tc - 1) / sh.tc));
-    const int Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
-    ncs = (N + Ns - 1) / Ns;
-    const size_t smem = (size_t)sh.stages * stage + 1024;
-    return launch_pdl(strip_update_kernel<NB, 0>, dim3(nstrip, ncs), dim3(32 * (sh.nc + 1)), smem, st, mX2, mQ, len, N,
+    const size_t smem = (size_t)sh.stages * stage_bytes_cols(NB, sh.tc) + 1024;
+    int grid = 0, Ns = 0;
+    strip_grid(strip_update_kernel<NB, 0>, len, N, 32 * (64 / NB), sh, smem, grid, Ns);
+    return launch_pdl(strip_update_kernel<NB, 0>, dim3(grid), dim3(32 * (sh.nc + 1)), smem, st, mX2, mQ, len, N,
                       Vo, ldv, sh.tc, sh.nc, sh.stages, Ns, off, sc.info);
 }
 
@@ -1058,16 +1096,12 @@ cudaError_t right_apply_nb(float *X, long ldx, int M, int N, const float *Vt, lo
     if (!tma_encode_2d(&mX, Xo, 4, M, len, ldx * 4, kBoxRows, sh.tc, true) ||
         !tma_encode_2d(&mQ, Vo, 4, NB, len, ldvt * 4, NB, sh.tc, false))
         return cudaErrorInvalidValue;
-    constexpr int H = 32 * (64 / NB);
-    const int stage = stage_bytes_cols(NB, sh.tc);
-    const int nstrip = (M + H - 1) / H;
-    const size_t smem = (size_t)sh.stages * stage + 1024;
+    const size_t smem = (size_t)sh.stages * stage_bytes_cols(NB, sh.tc) + 1024;
     static PerDeviceOnce attr;
     allow_max_smem(strip_update_kernel<NB, 1>, attr);
-    int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (len + sh.tc - 1) / sh.tc));
-    const int Ns = ((len + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
-    ncs = (len + Ns - 1) / Ns;
-    return launch_pdl(strip_update_kernel<NB, 1>, dim3(nstrip, ncs), dim3(32 * (sh.nc + 1)), smem, st, mX, mQ, M, len,
+    int grid = 0, Ns = 0;
+    strip_grid(strip_update_kernel<NB, 1>, M, len, 32 * (64 / NB), sh, smem, grid, Ns);
+    return launch_pdl(strip_update_kernel<NB, 1>, dim3(grid), dim3(32 * (sh.nc + 1)), smem, st, mX, mQ, M, len,
                       fin, 0L, sh.tc, sh.nc, sh.stages, Ns, off, sc.info);
 }
 
