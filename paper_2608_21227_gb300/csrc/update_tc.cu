@@ -377,15 +377,20 @@ tc_w_kernel(const double *__restrict__ X, long ldx, int M, int N, const double *
             // the tile's product is scaled by 2^-et per line; the running sum is kept
             // scaled by 2^-erun (erun = the largest et so far), so no factor leaves
             // FP32's range whatever the exponents of X
+            // (ok is warp-uniform: the TMEM loads below are warp-collective, so every lane
+            // executes them; a line whose tile is all zero adds its product with factor 0)
             const int et = ex1[pb * kStrip + 32 * q + lane];
-            if (ok && et != kNoExp) {
-                if (et > erun) {
-                    const float r = exp2_nonpos(erun - et);
+            if (ok) {
+                float sc = 0.f;
+                if (et != kNoExp) {
+                    if (et > erun) {
+                        const float r = exp2_nonpos(erun - et);
 #pragma unroll
-                    for (int i = 0; i < 32; ++i) acc[i] *= r;
-                    erun = et;
+                        for (int i = 0; i < 32; ++i) acc[i] *= r;
+                        erun = et;
+                    }
+                    sc = exp2_nonpos(et - erun);
                 }
-                const float sc = exp2_nonpos(et - erun);
                 for (int c = 0; c < half; c += 16) {
                     float v[16];
                     tc::tmem_ld16(tbase + pb * 64 + hh * half + c + ((uint32_t)(32 * q) << 16), v);
