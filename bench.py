@@ -257,7 +257,7 @@ def paper_workload(dev, stream):
             "table2_launch": t2}
 
 
-def extras(n, dev, stream, tuned_ms):
+def extras(n, dev, stream, tuned_ms, batched):
     """Forms the method is judged by besides the headline: tuned vs default, the plain FP64 path,
     TF32/BF16 trailing updates, and the batched workload against a looped FP64 path."""
     import torch
@@ -278,7 +278,8 @@ def extras(n, dev, stream, tuned_ms):
     del A
     S64 = torch.empty(n, dtype=torch.float64, device=dev)
     res = {}
-    for name, upd in (("fp64", nla.UPD_NATIVE), ("tf32", nla.UPD_TF32), ("bf16", nla.UPD_BF16)):
+    for name, upd in (("fp64", nla.UPD_NATIVE), ("tf32", nla.UPD_TF32), ("bf16", nla.UPD_BF16),
+                      ("tf32x3", nla.UPD_TF32X3)):
         cfg = DEFAULT_CFG if upd == nla.UPD_NATIVE else None
         w = nla.workspace(nla.gesvd_vals_workspace(n, n, nla.F64, update=upd, cfg=cfg, preserve_a=True), dev)
         ms = time_steps(lambda: nla.gesvd_vals(A64, update=upd, cfg=cfg, preserve_a=True, work=w, S=S64, info=info,
@@ -286,40 +287,64 @@ def extras(n, dev, stream, tuned_ms):
         res[name] = {"ms_per_step": round(ms, 2), "gflops": round(flops(n, n) / (ms / 1e3) / 1e9, 2),
                      "sigma_1": float(S64[0].item())}
         del w
-    for k in ("tf32", "bf16"):
+    for k in ("tf32", "bf16", "tf32x3"):
         res[k]["speedup_vs_fp64"] = round(res["fp64"]["ms_per_step"] / res[k]["ms_per_step"], 2)
+        res[k]["sigma_1_rel_diff_vs_fp64"] = abs(res[k]["sigma_1"] - res["fp64"]["sigma_1"]) / res["fp64"]["sigma_1"]
     out["fp64_and_mixed"] = {"workload": f"{n}x{n} U[-1,1] stored FP64", **res}
     del A64
-    # batched: 10,000 FP32 matrices, n ~ U{8..256}, m/n ~ U[1,4], N(0,1) (generated on the device)
-    ms_, ns_ = inputs.batch_shapes(10000, seed=3)
+    out["batched"] = batched
+    return out
+
+
+def batched_leg(dev, stream, rank, world, pg):
+    """The batched workload (10,000 FP32 matrices, n ~ U{8..256}, m/n ~ U[1,4], N(0,1), made on
+    the device from one seeded generator, so every rank holds the same batch).  With several
+    ranks each takes its cost-balanced share (dist.shard_batch, no collective) and makes one
+    batched call on it; the batch's time is the slowest rank's.  Rank 0 also times the plain
+    FP64 path looped over a sample of the same matrices."""
+    import torch
+
+    from paper_2608_21227_gb300 import inputs, kt, nla
+    from paper_2608_21227_gb300.dist import max_over_ranks, shard_batch
+
+    count = 10000
+    ms_, ns_ = inputs.batch_shapes(count, seed=3)
     g = torch.Generator(device=dev)
     g.manual_seed(3)
     mats = [torch.randn(int(nn), int(mm), generator=g, device=dev, dtype=torch.float32) for mm, nn in zip(ms_, ns_)]
-    bt = nla.Batch(mats)
-    b_ms = time_steps(lambda: nla.gesvd_vals_batched(bt, stream=stream), 5, stream, warmup=2)
+    mine = shard_batch(ms_, ns_, world)[rank] if world > 1 else list(range(count))
+    bt = nla.Batch([mats[i] for i in mine])
+    for _ in range(2):
+        nla.gesvd_vals_batched(bt, stream=stream)
+    torch.cuda.synchronize(dev)
+    if pg is not None:
+        pg.barrier()
+    b_ms = time_steps(lambda: nla.gesvd_vals_batched(bt, stream=stream), 5, stream, warmup=0)
+    b_ms = max_over_ranks(b_ms, pg, dev)
     ok = bool((bt.info == 0).all().item())
-    # the plain FP64 path looped over a sample of the same matrices (upcast), same GPU
-    k = 100
-    wl = nla.workspace(nla.gesvd_vals_workspace(1024, 256, nla.F64, cfg=DEFAULT_CFG, preserve_a=True) * 2, dev)
-    sample = [m.double() for m in mats[:k]]
-    Sl = torch.empty(256, dtype=torch.float64, device=dev)
-    from paper_2608_21227_gb300 import kt
-
-    kt.load_config(None)  # the plain, untuned FP64 path: default configuration for every shape
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for a in sample:
-        nla.gesvd_vals(a, preserve_a=True, work=wl, S=Sl[: min(a.shape)], info=info, stream=stream)
-    torch.cuda.synchronize()
-    loop_per = (time.perf_counter() - t0) / k
-    if os.path.exists(TABLE):
-        kt.load_config(TABLE)
-    out["batched"] = {"workload": "10000 FP32 matrices, n~U{8..256}, m/n~U[1,4], N(0,1)", "ms_per_batch": round(b_ms, 3),
-                      "matrices_per_s": round(10000 / (b_ms / 1e3), 1), "all_info_zero": ok,
-                      "fp64_loop_matrices_per_s": round(1.0 / loop_per, 1),
-                      "speedup_vs_fp64_loop": round((10000 / (b_ms / 1e3)) * loop_per, 1),
-                      "fp64_loop_sample": f"first {k} matrices, upcast, one nla_gesvd_vals call each, default configuration"}
-    return out
+    res = {"workload": f"{count} FP32 matrices, n~U{{8..256}}, m/n~U[1,4], N(0,1)", "ms_per_batch": round(b_ms, 3),
+           "matrices_per_s": round(count / (b_ms / 1e3), 1), "all_info_zero": ok,
+           "ranks": world, "sharding": "cost-balanced (dist.shard_batch), slowest rank's time" if world > 1 else None}
+    if rank == 0:
+        # the plain FP64 path looped over a sample of the same matrices (upcast), same GPU
+        k = 100
+        wl = nla.workspace(nla.gesvd_vals_workspace(1024, 256, nla.F64, cfg=DEFAULT_CFG, preserve_a=True) * 2, dev)
+        sample = [m.double() for m in mats[:k]]
+        Sl = torch.empty(256, dtype=torch.float64, device=dev)
+        info = torch.zeros(1, dtype=torch.int32, device=dev)
+        kt.load_config(None)  # the plain, untuned FP64 path: default configuration for every shape
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for a in sample:
+            nla.gesvd_vals(a, preserve_a=True, work=wl, S=Sl[: min(a.shape)], info=info, stream=stream)
+        torch.cuda.synchronize(dev)
+        loop_per = (time.perf_counter() - t0) / k
+        if os.path.exists(TABLE):
+            kt.load_config(TABLE)
+        res.update({"fp64_loop_matrices_per_s": round(1.0 / loop_per, 1),
+                    "speedup_vs_fp64_loop": round((count / (b_ms / 1e3)) * loop_per, 1),
+                    "fp64_loop_sample": f"first {k} matrices, upcast, one nla_gesvd_vals call each, default configuration"})
+    return res
 
 
 def main():
@@ -484,8 +509,9 @@ def main():
         "clocks": clk,
     }
     line["sigma_err"] = sigma_error(n, dev, stream, work, info)
+    batched = batched_leg(dev, stream, rank, world, pg) if not args.no_extras else None
     if rank == 0 and not args.no_extras:
-        line["extra"] = extras(n, dev, stream, ms)
+        line["extra"] = extras(n, dev, stream, ms, batched)
         line["extra"]["paper_workload"] = paper_workload(dev, stream)
     if rank == 0 and not args.no_cpu_baseline:
         gf, dt, cores = oracle_sample(SAMPLE_N, 1)

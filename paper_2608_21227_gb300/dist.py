@@ -2,7 +2,7 @@
 
 A single matrix does not shard: the panel -> update chain of Algorithm 1 is sequential
 step by step, so N GPUs run N independent problems (weak scaling) and nothing on the
-data path is exchanged.  Two pieces are shared by the ranks:
+data path is exchanged.  Three pieces are shared by the ranks:
 
 - shard_batch: a cost-balanced, deterministic split of a batch of matrices across ranks
   (longest-processing-time-first greedy on the flop count 4mn^2 - 4n^3/3 of each matrix).
@@ -10,6 +10,9 @@ data path is exchanged.  Two pieces are shared by the ranks:
   collective; each rank then makes one nla_gesvd_vals_batched call on its share.
 - max_over_ranks: a job's time is its slowest rank's; the benchmark reduces its per-rank
   timings with it (all_reduce MAX over the process group).
+- gather_by_index: after the ranks have solved their shares, every rank's (index,
+  result) pairs gathered back into batch order -- host objects only (all_gather_object),
+  off the timed path; a batch needs no exchange to be solved.
 """
 from __future__ import annotations
 
@@ -52,3 +55,26 @@ def max_over_ranks(value: float, pg=None, device=None) -> float:
     t = torch.tensor([float(value)], dtype=torch.float64, device=device)
     pg.all_reduce(t, op=pg.ReduceOp.MAX)
     return float(t.item())
+
+
+def gather_by_index(mine, results, count: int, pg=None):
+    """The batch's results in index order from every rank's share.
+
+    `mine` are this rank's batch indices and `results` its results for them (any
+    picklable objects, e.g. numpy arrays of singular values).  With no process group
+    the share must be the whole batch.  Raises if an index is missing or repeated."""
+    pairs = list(zip(mine, results))
+    if pg is not None and pg.is_available() and pg.is_initialized() and pg.get_world_size() > 1:
+        gathered = [None] * pg.get_world_size()
+        pg.all_gather_object(gathered, pairs)
+        pairs = [p for part in gathered for p in part]
+    out = [None] * count
+    seen = [False] * count
+    for i, r in pairs:
+        if not 0 <= i < count or seen[i]:
+            raise ValueError(f"batch index {i} out of range or assigned twice")
+        seen[i] = True
+        out[i] = r
+    if not all(seen):
+        raise ValueError("some batch indices were assigned to no rank")
+    return out
