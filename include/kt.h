@@ -125,7 +125,9 @@ nla_status kt_tune(const kt_problem *problem, kt_strategy strategy, double budge
                    kt_result *out);
 
 /* Install a table of best configurations written by kt_write_table (or by
- * hand); nla_gesvd_vals consults it whenever opts->cfg is NULL, matching
+ * hand) -- the tuner's results put to use (Section 5.2: the tuned kernel
+ * configurations and the pipeline-level band width); nla_gesvd_vals consults
+ * it whenever opts->cfg is NULL, matching
  * dtype, update precision and side and taking the entry nearest in log size;
  * side-2 entries set the batched kernel's threads per matrix (cfg.band) for
  * size bucket m (0..4).  path NULL clears the table. */

@@ -107,7 +107,9 @@ typedef struct {
 nla_status nla_gesvd_vals_workspace(int m, int n, nla_dtype dtype, const nla_opts *opts,
                                     size_t *bytes);
 
-/* Singular values of the column-major m x n matrix dA (dtype elements, lda >= m).
+/* Singular values of the column-major m x n matrix dA (dtype elements, lda >= m)
+ * by the whole two-stage method (Section 5.1.1, Fig. 3; Algorithm 1 for stage 1,
+ * Algorithm 2 for its trailing updates).
  * dS receives min(m, n) values in descending order, in dtype.  dA is
  * overwritten unless opts->preserve_a (or m < n, where A^T is formed in the
  * workspace and dA is left intact).  dWork: >= nla_gesvd_vals_workspace bytes,
@@ -166,9 +168,11 @@ nla_status nla_gebrd_band(int m, int n, int band, nla_dtype dtype, void *dA, int
 nla_status nla_band_extract(int n, int band, nla_dtype dtype, const void *dA, int lda,
                             void *dAB, int ldab, nla_stream_t stream);
 
-/* Stage 2: reduce the upper band matrix in dAB (layout of nla_band_extract,
- * overwritten) to upper bidiagonal form by Householder bulge chasing; dD (n)
- * and dE (n-1) receive the FP64 diagonal and superdiagonal. */
+/* Stage 2 (Section 5.1.1, Fig. 3: band to bidiagonal): reduce the upper band
+ * matrix in dAB (layout of nla_band_extract, overwritten) to upper bidiagonal
+ * form by Householder bulge chasing; dD (n) and dE (n-1) receive the FP64
+ * diagonal and superdiagonal.  dWork: >= nla_band2bd_workspace bytes (the
+ * sweeps' progress counters; the library allocates nothing on this path). */
 nla_status nla_band2bd_workspace(int n, int band, nla_dtype dtype, size_t *bytes);
 nla_status nla_band2bd(int n, int band, nla_dtype dtype, void *dAB, int ldab, double *dD,
                        double *dE, void *dWork, size_t work_bytes, int *dInfo,
@@ -191,7 +195,8 @@ nla_status nla_band2bd(int n, int band, nla_dtype dtype, void *dAB, int ldab, do
 nla_status nla_band2bd_noalloc(int n, int band, nla_dtype dtype, void *dAB, int ldab, double *dD,
                                double *dE, int *dInfo, nla_stream_t stream);
 
-/* Stage 3: singular values of the upper bidiagonal (dD, dE) by bisection on
+/* Stage 3 (Section 5.1.1: bidiagonal to diagonal form, i.e. the singular
+ * values): singular values of the upper bidiagonal (dD, dE) by bisection on
  * Sturm counts of the Golub-Kahan tridiagonal (coarse steps with FP32 counts,
  * final steps with FP64 counts); dS receives n values descending, converted to
  * dtype, accurate to the output type's resolution of the bidiagonal's
