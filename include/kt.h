@@ -119,7 +119,9 @@ int kt_cfg_valid(kt_kernel kernel, nla_dtype dtype, const nla_cfg *cfg);
  * by the sum over all stage-1 steps of its two update launches' predicted
  * runtimes at that step's trailing-block size; the random strategy samples the
  * triples uniformly.  Their budget is budget_frac of the joint space, at most 64
- * end-to-end runs. */
+ * end-to-end runs; with the model, each band's default-kernel point is among
+ * them and calibrates what the band costs besides its updates (panels, chase,
+ * bisection), which the model does not predict. */
 nla_status kt_tune(const kt_problem *problem, kt_strategy strategy, double budget_frac,
                    const char *cache_path, const char *model_path, unsigned long long seed,
                    kt_result *out);

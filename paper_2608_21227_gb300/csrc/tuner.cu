@@ -709,18 +709,6 @@ nla_status tune_joint(const kt_problem &p, kt_strategy strategy, double frac, co
                     for (size_t j = 0; j < steps[side].size(); ++j) pred[i] += std::exp((double)y[i * steps[side].size() + j]);
             }
         }
-        // the k joint points of smallest predicted cost (ties: lexicographic order)
-        std::vector<std::pair<double, long>> all;
-        all.reserve((size_t)total);
-        long base = 0;
-        for (const BandSpace &bs : bands) {
-            for (size_t i = 0; i < bs.L.size(); ++i)
-                for (size_t j = 0; j < bs.R.size(); ++j)
-                    all.push_back({bs.pl[i] + bs.pr[j], base + (long)(i * bs.R.size() + j)});
-            base += (long)bs.L.size() * (long)bs.R.size();
-        }
-        std::partial_sort(all.begin(), all.begin() + k, all.end());
-        for (long i = 0; i < k; ++i) cand.push_back(decode(all[(size_t)i].second));
     }
     kt_result r;
     memset(&r, 0, sizeof r);
@@ -733,7 +721,7 @@ nla_status tune_joint(const kt_problem &p, kt_strategy strategy, double frac, co
     double dms = NAN;
     if (!pb.run_default(dms)) return terr(NLA_ERR_CUDA, "tuner: the default configuration failed");
     r.default_ms = dms;
-    for (const auto &c : cand) {
+    auto measure = [&](const std::array<int, 3> &c) -> double {
         const BandSpace &bs = bands[(size_t)c[0]];
         const nla_cfg &cl = bs.L[(size_t)c[1]], &cr = bs.R[(size_t)c[2]];
         double med = NAN;
@@ -741,7 +729,7 @@ nla_status tune_joint(const kt_problem &p, kt_strategy strategy, double frac, co
         r.evaluated++;
         if (rs != 0) {
             r.failed++;
-            continue;
+            return (double)NAN;
         }
         times.push_back(med);
         if (!(med >= r.best_ms)) {
@@ -749,7 +737,48 @@ nla_status tune_joint(const kt_problem &p, kt_strategy strategy, double frac, co
             r.best = cl;
             r.best_lq = cr;
         }
+        return med;
+    };
+    if (strategy != KT_RANDOM) {
+        // The model predicts the update launches only; what a band adds besides them (its
+        // panels, chase and bisection) is measured: each band's default-kernel point is
+        // timed first (part of the budget) and the difference to its predicted update
+        // cost is the band's constant.  The rest of the budget goes to the points of
+        // smallest predicted total (ties: lexicographic order).
+        std::vector<double> cband(bands.size(), 0.0);
+        std::vector<long> taken;
+        long base = 0;
+        for (size_t bi = 0; bi < bands.size() && (long)taken.size() < k; ++bi) {
+            const BandSpace &bs = bands[bi];
+            auto pick = [&](const std::vector<nla_cfg> &cs) {
+                for (size_t i = 0; i < cs.size(); ++i)
+                    if (is_default_kernel(cs[i])) return i;
+                return (size_t)0;
+            };
+            const size_t dl = pick(bs.L), dr = pick(bs.R);
+            const double t = measure({(int)bi, (int)dl, (int)dr});
+            if (t == t) cband[bi] = std::max(0.0, t - (bs.pl[dl] + bs.pr[dr]));
+            taken.push_back(base + (long)(dl * bs.R.size() + dr));
+            base += (long)bs.L.size() * (long)bs.R.size();
+        }
+        std::vector<std::pair<double, long>> all;
+        all.reserve((size_t)total);
+        base = 0;
+        for (size_t bi = 0; bi < bands.size(); ++bi) {
+            const BandSpace &bs = bands[bi];
+            for (size_t i = 0; i < bs.L.size(); ++i)
+                for (size_t j = 0; j < bs.R.size(); ++j) {
+                    const long idx = base + (long)(i * bs.R.size() + j);
+                    if (std::find(taken.begin(), taken.end(), idx) == taken.end())
+                        all.push_back({cband[bi] + bs.pl[i] + bs.pr[j], idx});
+                }
+            base += (long)bs.L.size() * (long)bs.R.size();
+        }
+        const long rest = std::max(0L, std::min(k - (long)taken.size(), (long)all.size()));
+        std::partial_sort(all.begin(), all.begin() + rest, all.end());
+        for (long i = 0; i < rest; ++i) cand.push_back(decode(all[(size_t)i].second));
     }
+    for (const auto &c : cand) measure(c);
     r.median_ms = median_of(times);
     if (times.empty()) return terr(NLA_ERR_CONFIG, "tuner: no joint candidate ran successfully");
     *out = r;
