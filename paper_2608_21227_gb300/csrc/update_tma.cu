@@ -33,6 +33,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 
 #include "common.cuh"
@@ -315,7 +316,7 @@ qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 // partials in split order and applies T (Algorithm 2, step 2).  Every wait is bounded.
 constexpr int kTcWarps = 6;
 constexpr int kLanding = 12;  // most landing stages
-constexpr int kOpStages = 2;
+constexpr int kMaxOp = 6;     // most operand stages
 
 NLA_DEV float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 NLA_DEV float4 tf32_lo4(float4 v) {
@@ -329,14 +330,14 @@ __host__ __device__ constexpr int proj_op_bytes(int side, int nb) { return (side
 template <int NB, int SIDE>
 __global__ void __launch_bounds__(32 * kTcWarps, 1)
 proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int M, int N,
-               const float *__restrict__ Tm, int SL, int nsplit, int Ks, float *part, float *fin,
+               const float *__restrict__ Tm, int SL, int SO, int nsplit, int Ks, float *part, float *fin,
                unsigned int *tickets, int *info) {
     pdl_wait();
     pdl_trigger();
     constexpr uint32_t kCols = 2 * NB < 32 ? 32 : 2 * NB;  // TMEM columns (power of two >= 32)
     constexpr int LB = proj_land_bytes(NB), OB = proj_op_bytes(SIDE, NB);
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[kLanding], lempty[kLanding], conv[kOpStages], oempty[kOpStages], accfull,
+    __shared__ __align__(8) uint64_t full[kLanding], lempty[kLanding], conv[kMaxOp], oempty[kMaxOp], accfull,
         accdone;
     __shared__ uint32_t tmem_base;
     __shared__ int sh_abort;
@@ -351,7 +352,7 @@ proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&lempty[i], 1);
         }
-        for (int i = 0; i < kOpStages; ++i) {
+        for (int i = 0; i < SO; ++i) {
             tc::mbar_init(&conv[i], 4);
             tc::mbar_init(&oempty[i], 1);
         }
@@ -413,9 +414,9 @@ proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             for (int it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
                 const int nt = ktiles(it);
                 for (int t = 0; t < nt; ++t, ++g) {
-                    const int st = g % SL, ot = g % kOpStages;
+                    const int st = g % SL, ot = g % SO;
                     if (*(volatile int *)&sh_abort ||
-                        !tc::mbar_wait(&conv[ot], (uint32_t)((g / kOpStages) & 1), info)) {
+                        !tc::mbar_wait(&conv[ot], (uint32_t)((g / SO) & 1), info)) {
                         sh_abort = 1;
                         ok = false;
                         break;
@@ -451,9 +452,9 @@ proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             const int kb = sp * Ks, nt = ktiles(it);
             bool ok = true;
             for (int t = 0; t < nt; ++t, ++g) {
-                const int st = g % SL, ot = g % kOpStages;
+                const int st = g % SL, ot = g % SO;
                 if (!tc::mbar_wait_warp(&full[st], (uint32_t)((g / SL) & 1), info) ||
-                    (g >= kOpStages && !tc::mbar_wait_warp(&oempty[ot], (uint32_t)(((g / kOpStages) - 1) & 1), info)) ||
+                    (g >= SO && !tc::mbar_wait_warp(&oempty[ot], (uint32_t)(((g / SO) - 1) & 1), info)) ||
                     abort_seen(&sh_abort)) {
                     ok = false;
                     break;
@@ -751,7 +752,7 @@ lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 // fin[c*NB + k].  SIDE 1 (LQ): P = Y' at Pv[k*M + i] (ldp unused), Q = V
 // stored by rows (unit lower in (c, k)).
 template <int NB, int SIDE>
-__global__ void __maxnreg__(136)
+__global__ void __maxnreg__(128)
 strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int M, int N,
                     const float *__restrict__ Pv, long ldp, int tcols, int NC, int S, int Ns, int moff, int *info) {
     pdl_wait();
@@ -948,10 +949,20 @@ cudaError_t proj_tc_launch(const CUtensorMap &mX, const CUtensorMap &mV, int M, 
     static PerDeviceOnce attr;
     allow_max_smem(proj_tc_kernel<NB, SIDE>, attr);
     constexpr int LB = proj_land_bytes(NB), OB = proj_op_bytes(SIDE, NB);
-    const int SL = std::max(2, std::min(kLanding, (int)((kTmaSmemLimit - 1024 - (size_t)kOpStages * OB) / LB)));
+    // ring depths (landing, operand) and blocks per SM; NLA_PROJ_RING="SL,SO,B" overrides
+    static const int3 ring = [] {
+        int3 r = make_int3(0, 0, 0);
+        if (const char *v = getenv("NLA_PROJ_RING")) sscanf(v, "%d,%d,%d", &r.x, &r.y, &r.z);
+        return r;
+    }();
+    const int per_sm = ring.z > 0 ? std::min(ring.z, 4) : 1;
+    const size_t budget = kTmaSmemLimit / per_sm - 1024;
+    const int SO = std::max(2, std::min(kMaxOp, ring.y > 0 ? ring.y : 2));
+    const int SL = std::max(2, std::min(kLanding, ring.x > 0 ? ring.x : (int)((budget - (size_t)SO * OB) / LB)));
+    const size_t smem = (size_t)SL * LB + (size_t)SO * OB + 1024;
     const int Lext = SIDE == 0 ? N : M, Kext = SIDE == 0 ? M : N;
     const int nstrip = (Lext + 127) / 128, ktiles = (Kext + 31) / 32;
-    const int G = device_sm_count();
+    const int G = device_sm_count() * per_sm;
     int nsplit = 1;
     double best = -1.0;
     for (int s = 1; s <= kMaxSplitTma && s <= ktiles; ++s) {
@@ -965,8 +976,7 @@ cudaError_t proj_tc_launch(const CUtensorMap &mX, const CUtensorMap &mV, int M, 
     const int Ks = ((Kext + nsplit - 1) / nsplit + 31) / 32 * 32;
     nsplit = (Kext + Ks - 1) / Ks;
     const int grid = std::min(nstrip * nsplit, G);
-    const size_t smem = (size_t)SL * LB + (size_t)kOpStages * OB + 1024;
-    return launch_pdl(proj_tc_kernel<NB, SIDE>, dim3(grid), dim3(32 * kTcWarps), smem, st, mX, mV, M, N, Tm, SL,
+    return launch_pdl(proj_tc_kernel<NB, SIDE>, dim3(grid), dim3(32 * kTcWarps), smem, st, mX, mV, M, N, Tm, SL, SO,
                       nsplit, Ks, part, fin, sc.tickets, sc.info);
 }
 
@@ -1035,9 +1045,14 @@ void strip_grid(K kernel, int M, int N, int H, const TmaShape &sh, size_t smem, 
             ncs = c;
         }
     }
+    static const bool all_items = [] {  // NLA_STRIP_GRID=1: one block per item instead of persistent blocks
+        const char *v = getenv("NLA_STRIP_GRID");
+        return v && atoi(v) != 0;
+    }();
+    if (all_items) ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, ntile));
     Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
     ncs = (N + Ns - 1) / Ns;
-    grid = std::min(nstrip * ncs, slots);
+    grid = all_items ? nstrip * ncs : std::min(nstrip * ncs, slots);
 }
 
 // pass 2 on rows [off, off + len) of the M x N trailing block: X -= V W'
