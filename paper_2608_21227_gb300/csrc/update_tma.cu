@@ -291,72 +291,48 @@ qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     if (tid == 0) tickets[blockIdx.x] = 0u;
 }
 
-// ------------------------------------------------------------------ projections on the tensor cores
-// QR side: W^T (128 strip columns x NB) = X_strip^T V; LQ side: Y (128 strip rows x NB)
-// = X_strip V.  Both accumulate in TMEM with tcgen05 kind::tf32 MMAs (M = 128, K = 8 per
-// instruction) and reach FP32 accuracy by the three-term split x = hi + lo (hi = x with
-// the low 13 mantissa bits cleared, what the tensor core reads of an FP32 word; lo = x -
-// hi, exact): x . v ~ hi_x (hi_v + lo_v) + lo_x hi_v -- the dropped lo_x lo_v term and the
-// truncation of lo are below 2^-21 relative.  The first product runs as one MMA with
-// N = 2 NB against the stacked operand [V_hi; V_lo] (its two halves of D are summed at
-// the end), so a K step is two MMAs.
-//
-// Persistent blocks, one per SM: block b takes work items b, b + G, ... (item = strip x
-// split of the reduction dimension) and streams their 32-deep K tiles through two rings:
-//   landing ring (SL stages, deep): TMA boxes of X and V exactly as they arrive, so many
-//                 bytes are in flight per SM whatever the converter and MMA latency;
-//   operand ring (2 stages): what the MMAs read besides the landing tile -- the lo copy of
-//                 X (QR side: the landing box is already the K-major operand, hi = the raw
-//                 word) or hi and lo copies of X transposed to K-major (LQ side), and the
-//                 stacked [V_hi; V_lo] with V's unit diagonal applied.
-// Roles: warp 0 issues the TMA loads; warp 1 owns TMEM and one lane issues the MMAs (each
-// tile's commits free its landing stage and its operand stage); warps 2..5 convert, then
-// per item read the accumulator back (each warp its TMEM lane quadrant), write the split's
-// partial and take a per-warp ticket: the last of the strip's 4 x nsplit arrivals sums the
-// partials in split order and applies T (Algorithm 2, step 2).  Every wait is bounded.
+// ------------------------------------------------------------------ qr_proj on the tensor cores
+// W^T (128 strip columns x NB) = X_strip^T V accumulated in TMEM by tcgen05.mma
+// (kind::tf32, M = 128, N = NB, K = 8 per instruction) over 32-row stages of X.
+// FP32 accuracy from TF32 operands by the three-term split x = hi + lo,
+// hi = x with the low 13 mantissa bits cleared (what the tensor core reads of an
+// FP32 word), lo = x - hi (exact): x . v ~ hi_x hi_v + hi_x lo_v + lo_x hi_v, the
+// dropped lo_x lo_v term and the truncation of lo are below 2^-21 relative.
+// Roles: warp 0 issues the TMA loads of X and V (128-byte-swizzled boxes, which
+// are the canonical K-major operand layout); warps 2..5 write the lo copies and
+// mask V's unit diagonal; warp 1 owns TMEM and one lane issues the MMAs, each
+// stage's commit freeing it for the producer; warps 2..5 read the accumulator
+// back (each warp its TMEM lane quadrant).
 constexpr int kTcWarps = 6;
-constexpr int kLanding = 12;  // most landing stages
-constexpr int kMaxOp = 6;     // most operand stages
 
 NLA_DEV float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
-NLA_DEV float4 tf32_lo4(float4 v) {
-    return make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
-}
 
-// Shared-memory plan of the tensor-core projections (bytes).
-__host__ __device__ constexpr int proj_land_bytes(int nb) { return 16384 + nb * 128; }
-__host__ __device__ constexpr int proj_op_bytes(int side, int nb) { return (side == 0 ? 16384 : 32768) + 2 * nb * 128; }
-
-template <int NB, int SIDE>
+template <int NB>
 __global__ void __launch_bounds__(32 * kTcWarps, 1)
-proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int M, int N,
-               const float *__restrict__ Tm, int SL, int SO, int nsplit, int Ks, float *part, float *fin,
-               unsigned int *tickets, int *info) {
+qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmV, int M, int N,
+                  const float *__restrict__ Tm, int S, int Ms, float *part, float *fin, unsigned int *tickets,
+                  int *info) {
     pdl_wait();
     pdl_trigger();
-    constexpr uint32_t kCols = 2 * NB < 32 ? 32 : 2 * NB;  // TMEM columns (power of two >= 32)
-    constexpr int LB = proj_land_bytes(NB), OB = proj_op_bytes(SIDE, NB);
+    constexpr uint32_t kCols = NB < 32 ? 32 : NB;  // TMEM columns (power of two >= 32)
     extern __shared__ unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t full[kLanding], lempty[kLanding], conv[kMaxOp], oempty[kMaxOp], accfull,
-        accdone;
+    __shared__ __align__(8) uint64_t full[kMaxStages], conv[kMaxStages], empty[kMaxStages], accdone;
     __shared__ uint32_t tmem_base;
-    __shared__ int sh_abort;
+    __shared__ int sh_last, sh_abort;
     unsigned char *base = align1k(smem_raw);
-    unsigned char *ops = base + (size_t)SL * LB;
+    const int xbytes = 32 * 128 * 4, vbytes = NB * 128;  // one 32-row box of X (128 columns) and of V
+    const int stage = 2 * xbytes + 2 * vbytes;          // hi and lo copies
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // strip lines: QR -> columns of X, LQ -> rows; reduction dimension: the other one
-    const int Lext = SIDE == 0 ? N : M, Kext = SIDE == 0 ? M : N;
-    const int nstrip = (Lext + 127) / 128, nitems = nstrip * nsplit;
+    const int c0 = blockIdx.x * 128, wc = min(128, N - c0);
+    const int sp = blockIdx.y, nsplit = gridDim.y;
+    const int rbeg = sp * Ms, rend = min(M, rbeg + Ms);
+    const int nt = (rend - rbeg + kBoxRows - 1) / kBoxRows;
     if (tid == 0) {
-        for (int i = 0; i < SL; ++i) {
+        for (int i = 0; i < S; ++i) {
             tc::mbar_init(&full[i], 1);
-            tc::mbar_init(&lempty[i], 1);
-        }
-        for (int i = 0; i < SO; ++i) {
             tc::mbar_init(&conv[i], 4);
-            tc::mbar_init(&oempty[i], 1);
+            tc::mbar_init(&empty[i], 1);
         }
-        tc::mbar_init(&accfull, 1);
         tc::mbar_init(&accdone, 1);
         sh_abort = 0;
         tma::fence_init();
@@ -371,222 +347,138 @@ proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tbase = tmem_base;
-    auto land = [&](int st) { return base + (size_t)st * LB; };
-    auto opst = [&](int ot) { return ops + (size_t)ot * OB; };
-    auto ktiles = [&](int it) {
-        const int kb = (it % nsplit) * Ks;
-        return (min(Kext, kb + Ks) - kb + 31) / 32;
-    };
+    auto xhi = [&](int st) { return base + (size_t)st * stage; };
+    auto xlo = [&](int st) { return base + (size_t)st * stage + xbytes; };
+    auto vhi = [&](int st) { return base + (size_t)st * stage + 2 * xbytes; };
+    auto vlo = [&](int st) { return base + (size_t)st * stage + 2 * xbytes + vbytes; };
 
     if (warp == 0) {
         if (lane == 0) {
-            int g = 0;
-            bool ok = true;
-            for (int it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
-                const int l0 = (it / nsplit) * 128, kb = (it % nsplit) * Ks, nt = ktiles(it);
-                for (int t = 0; t < nt; ++t, ++g) {
-                    const int st = g % SL;
-                    if (g >= SL && !tc::mbar_wait(&lempty[st], (uint32_t)(((g / SL) - 1) & 1), info)) {
-                        sh_abort = 1;
-                        ok = false;
-                        break;
-                    }
-                    unsigned char *sb = land(st);
-                    tma::expect_tx(&full[st], (uint32_t)LB);
-                    const int k0 = kb + 32 * t;
-                    if (SIDE == 0) {
-                        tma::load_2d(sb, &tmX, k0, l0, &full[st]);            // 32 rows x 128 columns
-                        tma::load_2d(sb + 16384, &tmV, k0, 0, &full[st]);     // V rows k0.., NB columns
-                    } else {
-                        for (int bx = 0; bx < 4; ++bx)                         // 128 rows x 32 columns
-                            tma::load_2d(sb + bx * 4096, &tmX, l0 + 32 * bx, k0, &full[st]);
-                        tma::load_2d(sb + 16384, &tmV, 0, k0, &full[st]);     // V^T: NB x 32 columns
-                    }
+            int issued = 0;
+            for (int t = 0; t < nt; ++t) {
+                const int st = t % S;
+                if (t >= S && !tc::mbar_wait(&empty[st], (uint32_t)(((t / S) - 1) & 1), info)) {
+                    sh_abort = 1;
+                    break;
                 }
+                tma::expect_tx(&full[st], (uint32_t)(xbytes + vbytes));
+                const int r0 = rbeg + t * kBoxRows;
+                tma::load_2d(xhi(st), &tmX, r0, c0, &full[st]);
+                tma::load_2d(vhi(st), &tmV, r0, 0, &full[st]);
+                issued = t + 1;
             }
-            drain_loads(full, g, SL, info);
+            drain_loads(full, issued, S, info);
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t id2 = tc::idesc(2, 128, 2 * NB), id1 = tc::idesc(2, 128, NB);
-            int g = 0;
-            bool ok = true;
-            for (int it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
-                const int nt = ktiles(it);
-                for (int t = 0; t < nt; ++t, ++g) {
-                    const int st = g % SL, ot = g % SO;
-                    if (*(volatile int *)&sh_abort ||
-                        !tc::mbar_wait(&conv[ot], (uint32_t)((g / SO) & 1), info)) {
-                        sh_abort = 1;
-                        ok = false;
-                        break;
-                    }
-                    tc::fence_after_sync();
-                    const uint32_t o = tc::smem_u32(opst(ot));
-                    // A_hi: the landing box (QR) or the transposed hi copy (LQ); A_lo; [V_hi; V_lo]
-                    const uint32_t ah = SIDE == 0 ? tc::smem_u32(land(st)) : o;
-                    const uint32_t al = SIDE == 0 ? o : o + 16384;
-                    const uint32_t bv = o + (SIDE == 0 ? 16384 : 32768);
-#pragma unroll
-                    for (int kk = 0; kk < 4; ++kk) {  // 8 TF32 = 32 bytes of K per instruction
-                        const uint32_t off = kk * 32;
-                        tc::mma_tf32(tbase, tc::sdesc_sw128(ah + off), tc::sdesc_sw128(bv + off), id2,
-                                     (t > 0 || kk > 0) ? 1u : 0u);
-                        tc::mma_tf32(tbase, tc::sdesc_sw128(al + off), tc::sdesc_sw128(bv + off), id1, 1u);
-                    }
-                    tc::mma_commit(&lempty[st]);  // free once these MMAs have read them
-                    tc::mma_commit(&oempty[ot]);
+            const uint32_t id = tc::idesc(2, 128, NB);
+            for (int t = 0; t < nt; ++t) {
+                const int st = t % S;
+                if (*(volatile int *)&sh_abort || !tc::mbar_wait(&conv[st], (uint32_t)((t / S) & 1), info)) {
+                    sh_abort = 1;
+                    break;
                 }
-                if (ok) tc::mma_commit(&accfull);  // this item's accumulator is complete
+                tc::fence_after_sync();
+                const uint32_t ah = tc::smem_u32(xhi(st)), al = tc::smem_u32(xlo(st));
+                const uint32_t bh = tc::smem_u32(vhi(st)), bl = tc::smem_u32(vlo(st));
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk) {  // 8 TF32 = 32 bytes of K per instruction
+                    const uint32_t off = kk * 32;
+                    tc::mma_tf32(tbase, tc::sdesc_sw128(ah + off), tc::sdesc_sw128(bh + off), id,
+                                 (t > 0 || kk > 0) ? 1u : 0u);
+                    tc::mma_tf32(tbase, tc::sdesc_sw128(ah + off), tc::sdesc_sw128(bl + off), id, 1u);
+                    tc::mma_tf32(tbase, tc::sdesc_sw128(al + off), tc::sdesc_sw128(bh + off), id, 1u);
+                }
+                tc::mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
             }
             tc::mma_commit(&accdone);  // every issued MMA has completed
         }
         __syncwarp();
     } else {
+        // ---- warps 2..5: lo copies (and V's unit diagonal), then the epilogue
         const int ct = tid - 64;  // 0..127
-        const int q = warp & 3;   // TMEM lanes 32q .. 32q + 31 (the warp's quadrant)
-        int g = 0, li = 0;
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x, ++li) {
-            const int strip = it / nsplit, sp = it % nsplit;
-            const int l0 = strip * 128, lw = min(128, Lext - l0);
-            const int kb = sp * Ks, nt = ktiles(it);
-            bool ok = true;
-            for (int t = 0; t < nt; ++t, ++g) {
-                const int st = g % SL, ot = g % SO;
-                if (!tc::mbar_wait_warp(&full[st], (uint32_t)((g / SL) & 1), info) ||
-                    (g >= SO && !tc::mbar_wait_warp(&oempty[ot], (uint32_t)(((g / SO) - 1) & 1), info)) ||
-                    abort_seen(&sh_abort)) {
-                    ok = false;
-                    break;
+        for (int t = 0; t < nt; ++t) {
+            const int st = t % S;
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || abort_seen(&sh_abort)) {
+                sh_abort = 1;
+                break;
+            }
+            const int r0 = rbeg + t * kBoxRows;  // trailing-matrix row of the stage's first row
+            float *vh = reinterpret_cast<float *>(vhi(st));
+            if (r0 < NB) {
+                // V(r, k) with r <= k: 1 on the diagonal, 0 above (entry (r, k) of the box:
+                // row k, 16-byte chunk (r/4) ^ (k & 7), word r % 4)
+                for (int e = ct; e < NB * kBoxRows; e += 128) {
+                    const int k = e / kBoxRows, rr = e % kBoxRows, r = r0 + rr;
+                    if (r <= k) vh[k * 32 + ((((rr >> 2) ^ (k & 7))) << 2) + (rr & 3)] = r == k ? 1.f : 0.f;
                 }
-                const int k0 = kb + 32 * t;  // reduction index of the tile's first entry
-                unsigned char *sb = land(st), *ob = opst(ot);
-                if (SIDE == 0) {
-                    // lo copy of the X box (same K-major swizzled layout)
-                    const float4 *xs = reinterpret_cast<const float4 *>(sb);
-                    float4 *xl = reinterpret_cast<float4 *>(ob);
+                asm volatile("bar.sync 2, 128;" ::: "memory");
+            }
+            const float4 *xs = reinterpret_cast<const float4 *>(xhi(st));
+            float4 *xl = reinterpret_cast<float4 *>(xlo(st));
 #pragma unroll 4
-                    for (int e = ct; e < 1024; e += 128) xl[e] = tf32_lo4(xs[e]);
-                    // V: entry (r, k) of the box is row k, 16-byte chunk (r/4) ^ (k & 7), word r % 4;
-                    // unit diagonal applied (r == k: 1, r < k: 0), hi copy and lo stacked
-                    const float4 *vs = reinterpret_cast<const float4 *>(sb + 16384);
-                    float4 *vh = reinterpret_cast<float4 *>(ob + 16384);
-                    float4 *vl = reinterpret_cast<float4 *>(ob + 16384 + NB * 128);
-                    for (int e = ct; e < NB * 8; e += 128) {
-                        float4 v = vs[e];
-                        if (k0 < NB) {
-                            const int k = e >> 3, rr = 4 * ((e & 7) ^ (k & 7)), r = k0 + rr;
-                            v.x = unit_lower(r, k, v.x), v.y = unit_lower(r + 1, k, v.y);
-                            v.z = unit_lower(r + 2, k, v.z), v.w = unit_lower(r + 3, k, v.w);
-                        }
-                        vh[e] = v;
-                        vl[e] = tf32_lo4(v);
-                    }
-                } else {
-                    // X (column-major boxes of 32 rows) -> K-major rows of 32 columns: row r,
-                    // 16-byte chunk c4 ^ (r & 7) holds columns 4 c4 .. 4 c4 + 3
-                    const int r = ct, box = r >> 5, rib = r & 31;
-                    const unsigned char *xb = sb + box * 4096;
-                    unsigned char *ah = ob + r * 128, *al = ob + 16384 + r * 128;
-#pragma unroll
-                    for (int c4 = 0; c4 < 8; ++c4) {
-                        float x4[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int j = 4 * c4 + i;
-                            x4[i] = *reinterpret_cast<const float *>(xb + j * 128 + ((((rib >> 2) ^ (j & 7))) << 4) +
-                                                                     (rib & 3) * 4);
-                        }
-                        const float4 v = make_float4(x4[0], x4[1], x4[2], x4[3]);
-                        const int ch = (c4 ^ (r & 7)) << 4;
-                        *reinterpret_cast<float4 *>(ah + ch) = v;
-                        *reinterpret_cast<float4 *>(al + ch) = tf32_lo4(v);
-                    }
-                    // V^T box (column c: NB consecutive reflector entries) -> rows k of 32
-                    // columns, unit diagonal applied (global column c: c == k -> 1, c < k -> 0)
-                    const float *vs = reinterpret_cast<const float *>(sb + 16384);
-                    unsigned char *vh = ob + 32768, *vl = ob + 32768 + NB * 128;
-                    for (int e = ct; e < NB * 8; e += 128) {
-                        const int k = e >> 3, c4 = e & 7;
-                        float x4[4];
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const int j = 4 * c4 + i;
-                            const float v = vs[j * NB + k];
-                            x4[i] = k0 < NB ? unit_lower(k0 + j, k, v) : v;
-                        }
-                        const float4 v = make_float4(x4[0], x4[1], x4[2], x4[3]);
-                        const int ch = k * 128 + ((c4 ^ (k & 7)) << 4);
-                        *reinterpret_cast<float4 *>(vh + ch) = v;
-                        *reinterpret_cast<float4 *>(vl + ch) = tf32_lo4(v);
-                    }
-                }
-                tc::fence_async_smem();  // the copies -> visible to the tensor core
-                __syncwarp();
-                if (lane == 0) tma::arrive(&conv[ot]);
+            for (int e = ct; e < xbytes / 16; e += 128) {
+                const float4 v = xs[e];
+                xl[e] = make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
             }
-            if (!ok) {
-                if (lane == 0) sh_abort = 1;
-                break;
+            const float4 *vs = reinterpret_cast<const float4 *>(vh);
+            float4 *vl = reinterpret_cast<float4 *>(vlo(st));
+            for (int e = ct; e < vbytes / 16; e += 128) {
+                const float4 v = vs[e];
+                vl[e] = make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
             }
-            // ---- epilogue of the item: this warp's 32 strip lines of the partial
-            if (!tc::mbar_wait_warp(&accfull, (uint32_t)(li & 1), info)) {
-                if (lane == 0) sh_abort = 1;
-                break;
-            }
-            tc::fence_after_sync();
-            const int line = 32 * q + lane;
+            tc::fence_async_smem();  // the lo copies -> visible to the tensor core
+            __syncwarp();
+            if (lane == 0) tma::arrive(&conv[st]);
+        }
+        // epilogue: W^T rows of this warp's TMEM lane quadrant
+        const bool ok = tc::mbar_wait_warp(&accdone, 0, info);
+        tc::fence_after_sync();
+        const int q = warp & 3;  // TMEM lanes 32q .. 32q + 31
+        const int col = 32 * q + lane;
+        if (ok && !abort_seen(&sh_abort)) {
 #pragma unroll
             for (int c = 0; c < NB; c += 16) {
-                float w1[16], w2[16];
-                tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c, w1);
-                tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)(NB + c), w2);
+                float w[16];
+                tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c, w);
                 tc::tmem_wait_ld();
-                if (line < lw) {
+                if (col < wc) {
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) part[((size_t)sp * NB + c + k) * Lext + l0 + line] = w1[k] + w2[k];
+                    for (int k = 0; k < 16; ++k) part[((size_t)sp * NB + c + k) * N + c0 + col] = w[k];
                 }
             }
-            tc::fence_before_sync();  // (the next item's MMAs start only after this warp's next arrive)
-            // per-warp ticket: the last of the strip's 4 x nsplit arrivals finishes the strip
-            __threadfence();
-            __syncwarp();
-            unsigned last = 0;
-            if (lane == 0) last = atomicAdd(&tickets[strip], 1u) == (unsigned)(4 * nsplit - 1);
-            last = __shfl_sync(0xffffffffu, last, 0);
-            if (!last) continue;
-            __threadfence();
-            for (int l = lane; l < lw; l += 32) {
-                float w[NB];
-#pragma unroll
-                for (int k = 0; k < NB; ++k) w[k] = 0.f;
-#pragma unroll 1
-                for (int qq = 0; qq < nsplit; ++qq) {  // fixed split order; a split's NB loads in flight together
-                    const float *pp = part + (size_t)qq * NB * Lext + l0 + l;
-#pragma unroll
-                    for (int k = 0; k < NB; ++k) w[k] += __ldcg(pp + (size_t)k * Lext);
-                }
-                // QR: W'(:, c) = T^T W(:, c) -> fin[c * NB + k];  LQ: Y'(i, :) = Y(i, :) T -> fin[k * M + i]
-#pragma unroll 1
-                for (int k = 0; k < NB; ++k) {
-                    float s = 0.f;
-#pragma unroll
-                    for (int j = 0; j < NB; ++j)
-                        if (j <= k) s = fmaf(__ldg(Tm + j + (size_t)k * NB), w[j], s);
-                    if (SIDE == 0)
-                        fin[(size_t)(l0 + l) * NB + k] = s;
-                    else
-                        fin[(size_t)k * M + l0 + l] = s;
-                }
-            }
-            if (lane == 0) tickets[strip] = 0u;
         }
     }
-    // every issued MMA completes before TMEM is released
-    if (warp == 1) tc::mbar_wait_warp(&accdone, 0, info);
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 1) tc::tmem_dealloc(tbase, kCols);
+    __threadfence();
+    __syncthreads();
+    if (sh_abort) return;
+    if (tid == 0) sh_last = atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(nsplit - 1);
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    float *W = reinterpret_cast<float *>(base);
+    for (int idx = tid; idx < NB * 128; idx += blockDim.x) {
+        const int k = idx >> 7, c = idx & 127;
+        float sum = 0.f;
+        if (c < wc)
+#pragma unroll
+            for (int qq = 0; qq < kMaxSplitTma; ++qq)  // (all partial loads in flight at once)
+                if (qq < nsplit) sum += __ldcg(part + ((size_t)qq * NB + k) * N + c0 + c);
+        W[idx] = sum;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NB * wc; idx += blockDim.x) {
+        const int k = idx % NB, c = idx / NB;
+        float sum = 0.f;
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (j <= k) sum = fmaf(__ldg(Tm + j + (size_t)k * NB), W[j * 128 + c], sum);
+        fin[(size_t)(c0 + c) * NB + k] = sum;
+    }
+    if (tid == 0) tickets[blockIdx.x] = 0u;
 }
 
 // ------------------------------------------------------------------ lq_proj
@@ -745,14 +637,12 @@ lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 }
 
 // ------------------------------------------------------------------ strip_update
-// Persistent: block b takes work items b, b + G, ... (item = strip of 32*RL rows x one
-// column chunk of Ns columns) and streams their tiles through one ring of S stages.
-// Item: X(strip rows, chunk columns) -= P(strip rows, :) Q(cols, :)^T.
+// Block (strip, cs): X(strip rows, columns of split cs) -= P(strip rows, :) Q(cols, :)^T.
 // SIDE 0 (QR): P = V (unit lower, column-major at Pv, ld ldp), Q = W'^T from
 // fin[c*NB + k].  SIDE 1 (LQ): P = Y' at Pv[k*M + i] (ldp unused), Q = V
 // stored by rows (unit lower in (c, k)).
 template <int NB, int SIDE>
-__global__ void __maxnreg__(128)
+__global__ void __launch_bounds__(kMaxThreads, 1)
 strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int M, int N,
                     const float *__restrict__ Pv, long ldp, int tcols, int NC, int S, int Ns, int moff, int *info) {
     pdl_wait();
@@ -765,7 +655,9 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
     const int xbytes = tcols * 128, qbytes = tcols * NB * 4;
     const int stage = RL * xbytes + qbytes;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int nstrip = (M + H - 1) / H, ncs = (N + Ns - 1) / Ns, nitems = nstrip * ncs;
+    const int i0 = blockIdx.x * H;
+    const int cbeg = blockIdx.y * Ns, cend = min(N, cbeg + Ns);
+    const int nt = (cend - cbeg + tcols - 1) / tcols;
     if (tid == 0) {
         for (int i = 0; i < S; ++i) {
             tc::mbar_init(&full[i], 1);
@@ -780,35 +672,30 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
 
     if (warp == 0) {
         if (lane == 0) {
-            // ring entry t holds tile (row i0, column cb) until it is stored back
-            int ti0[kMaxStages], tcb[kMaxStages];
-            int g = 0, stored = 0;
+            int issued = 0, stored = 0;
             bool ok = true;
-            for (int it = blockIdx.x; ok && it < nitems; it += gridDim.x) {
-                const int i0 = (it / ncs) * H, cbeg = (it % ncs) * Ns, cend = min(N, cbeg + Ns);
-                for (int cb = cbeg; cb < cend; cb += tcols, ++g) {
-                    const int st = g % S;
-                    unsigned char *sb = base + (size_t)st * stage;
-                    if (g >= S) {
-                        // write back the tile that used this stage, then reuse it
-                        if (!tc::mbar_wait(&done[st], (uint32_t)(((g / S) - 1) & 1), info)) {
-                            sh_abort = 1;
-                            ok = false;
-                            break;
-                        }
-                        for (int bx = 0; bx < RL; ++bx) tma::store_2d(&tmX, ti0[st] + bx * kBoxRows, tcb[st], sb + bx * xbytes);
-                        tma::commit();
-                        stored = g - S + 1;
-                        tma::wait_read_all();
+            for (int t = 0; t < nt && ok; ++t) {
+                const int st = t % S;
+                unsigned char *sb = base + (size_t)st * stage;
+                if (t >= S) {
+                    // write back the tile that used this stage, then reuse it
+                    if (!tc::mbar_wait(&done[st], (uint32_t)(((t / S) - 1) & 1), info)) {
+                        sh_abort = 1;
+                        ok = false;
+                        break;
                     }
-                    tma::expect_tx(&full[st], (uint32_t)stage);
-                    for (int bx = 0; bx < RL; ++bx) tma::load_2d(sb + bx * xbytes, &tmX, i0 + bx * kBoxRows, cb, &full[st]);
-                    tma::load_2d(sb + RL * xbytes, &tmQ, 0, cb, &full[st]);
-                    ti0[st] = i0;
-                    tcb[st] = cb;
+                    const int cbo = cbeg + (t - S) * tcols;
+                    for (int bx = 0; bx < RL; ++bx) tma::store_2d(&tmX, i0 + bx * kBoxRows, cbo, sb + bx * xbytes);
+                    tma::commit();
+                    stored = t - S + 1;
+                    tma::wait_read_all();
                 }
+                tma::expect_tx(&full[st], (uint32_t)stage);
+                const int cb = cbeg + t * tcols;
+                for (int bx = 0; bx < RL; ++bx) tma::load_2d(sb + bx * xbytes, &tmX, i0 + bx * kBoxRows, cb, &full[st]);
+                tma::load_2d(sb + RL * xbytes, &tmQ, 0, cb, &full[st]);
+                issued = t + 1;
             }
-            const int issued = g;
             for (int t = stored; ok && t < issued; ++t) {
                 const int st = t % S;
                 if (!tc::mbar_wait(&done[st], (uint32_t)((t / S) & 1), info)) {
@@ -816,8 +703,9 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
                     ok = false;
                     break;
                 }
+                const int cbo = cbeg + t * tcols;
                 for (int bx = 0; bx < RL; ++bx)
-                    tma::store_2d(&tmX, ti0[st] + bx * kBoxRows, tcb[st], base + (size_t)st * stage + bx * xbytes);
+                    tma::store_2d(&tmX, i0 + bx * kBoxRows, cbo, base + (size_t)st * stage + bx * xbytes);
                 tma::commit();
             }
             if (!ok) drain_loads(full, issued, S, info);
@@ -825,86 +713,78 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
         }
     } else {
         const int cw = warp - 1;
-        int g = 0;
-        for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-            const int i0 = (it / ncs) * H, cbeg = (it % ncs) * Ns, cend = min(N, cbeg + Ns);
-            // P(lane's rows, :) in registers
-            float p[RL][NB];
+        // P(lane's rows, :) in registers
+        float p[RL][NB];
 #pragma unroll
-            for (int a = 0; a < RL; ++a) {
-                const int i = i0 + RL * lane + a;
+        for (int a = 0; a < RL; ++a) {
+            const int i = i0 + RL * lane + a;
 #pragma unroll
-                for (int k = 0; k < NB; ++k) {
-                    float v = 0.f;
-                    if (i < M) {
-                        if constexpr (SIDE == 0)
-                            v = unit_lower(moff + i, k, moff + i > k ? __ldg(Pv + i + (long)k * ldp) : 0.f);
-                        else
-                            v = __ldg(Pv + (size_t)k * M + i);
-                    }
-                    p[a][k] = v;
+            for (int k = 0; k < NB; ++k) {
+                float v = 0.f;
+                if (i < M) {
+                    if constexpr (SIDE == 0)
+                        v = unit_lower(moff + i, k, moff + i > k ? __ldg(Pv + i + (long)k * ldp) : 0.f);
+                    else
+                        v = __ldg(Pv + (size_t)k * M + i);
                 }
+                p[a][k] = v;
             }
-            bool ok = true;
-            for (int cb = cbeg; cb < cend; cb += tcols, ++g) {
-                const int st = g % S;
-                if (!tc::mbar_wait_warp(&full[st], (uint32_t)((g / S) & 1), info) || abort_seen(&sh_abort)) {
-                    ok = false;
-                    break;
-                }
-                unsigned char *sb = base + (size_t)st * stage;
-                const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
-                if (SIDE == 0 || moff + cb >= NB) {  // no column of this stage meets V's unit diagonal
+        }
+        for (int t = 0; t < nt; ++t) {
+            const int st = t % S;
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || abort_seen(&sh_abort)) break;
+            unsigned char *sb = base + (size_t)st * stage;
+            const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
+            const int cb = cbeg + t * tcols;
+            if (SIDE == 0 || moff + cb >= NB) {  // no column of this stage meets V's unit diagonal
 #pragma unroll 2
-                    for (int j = cw; j < tcols; j += NC) {
-                        float *xp = xptr_rows<RL>(sb, tcols, j, lane);
-                        float x[RL];
-                        ld_rows<RL>(xp, x);
-                        float d[RL][4];  // four independent partial sums per row: short FMA chains
+                for (int j = cw; j < tcols; j += NC) {
+                    float *xp = xptr_rows<RL>(sb, tcols, j, lane);
+                    float x[RL];
+                    ld_rows<RL>(xp, x);
+                    float d[RL][4];  // four independent partial sums per row: short FMA chains
 #pragma unroll
-                        for (int a = 0; a < RL; ++a) d[a][0] = d[a][1] = d[a][2] = d[a][3] = 0.f;
+                    for (int a = 0; a < RL; ++a) d[a][0] = d[a][1] = d[a][2] = d[a][3] = 0.f;
 #pragma unroll
-                        for (int k4 = 0; k4 < NB; k4 += 4) {
-                            const float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
+                    for (int k4 = 0; k4 < NB; k4 += 4) {
+                        const float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
 #pragma unroll
-                            for (int a = 0; a < RL; ++a) {
-                                d[a][0] = fmaf(p[a][k4], q.x, d[a][0]);
-                                d[a][1] = fmaf(p[a][k4 + 1], q.y, d[a][1]);
-                                d[a][2] = fmaf(p[a][k4 + 2], q.z, d[a][2]);
-                                d[a][3] = fmaf(p[a][k4 + 3], q.w, d[a][3]);
-                            }
+                        for (int a = 0; a < RL; ++a) {
+                            d[a][0] = fmaf(p[a][k4], q.x, d[a][0]);
+                            d[a][1] = fmaf(p[a][k4 + 1], q.y, d[a][1]);
+                            d[a][2] = fmaf(p[a][k4 + 2], q.z, d[a][2]);
+                            d[a][3] = fmaf(p[a][k4 + 3], q.w, d[a][3]);
                         }
-#pragma unroll
-                        for (int a = 0; a < RL; ++a) x[a] -= (d[a][0] + d[a][1]) + (d[a][2] + d[a][3]);
-                        st_rows<RL>(xp, x);
                     }
-                } else {
-                    for (int j = cw; j < tcols; j += NC) {
-                        float *xp = xptr_rows<RL>(sb, tcols, j, lane);
-                        float x[RL];
-                        ld_rows<RL>(xp, x);
-                        const int c = moff + cb + j;  // global column: V's unit diagonal
 #pragma unroll
-                        for (int k4 = 0; k4 < NB; k4 += 4) {
-                            float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
-                            q.x = unit_lower(c, k4, q.x), q.y = unit_lower(c, k4 + 1, q.y);
-                            q.z = unit_lower(c, k4 + 2, q.z), q.w = unit_lower(c, k4 + 3, q.w);
-#pragma unroll
-                            for (int a = 0; a < RL; ++a) {
-                                x[a] = fmaf(-p[a][k4], q.x, x[a]);
-                                x[a] = fmaf(-p[a][k4 + 1], q.y, x[a]);
-                                x[a] = fmaf(-p[a][k4 + 2], q.z, x[a]);
-                                x[a] = fmaf(-p[a][k4 + 3], q.w, x[a]);
-                            }
-                        }
-                        st_rows<RL>(xp, x);
-                    }
+                    for (int a = 0; a < RL; ++a) x[a] -= (d[a][0] + d[a][1]) + (d[a][2] + d[a][3]);
+                    st_rows<RL>(xp, x);
                 }
-                tc::fence_async_smem();  // this lane's shared-memory writes -> visible to the TMA store
-                __syncwarp();
-                if (lane == 0) tma::arrive(&done[st]);
+            } else {
+                for (int j = cw; j < tcols; j += NC) {
+                    float *xp = xptr_rows<RL>(sb, tcols, j, lane);
+                    float x[RL];
+                    ld_rows<RL>(xp, x);
+                    const int c = moff + cb + j;  // global column: V's unit diagonal
+#pragma unroll
+                    for (int k4 = 0; k4 < NB; k4 += 4) {
+                        float4 q = *reinterpret_cast<const float4 *>(qs + j * NB + k4);
+                        q.x = unit_lower(c, k4, q.x), q.y = unit_lower(c, k4 + 1, q.y);
+                        q.z = unit_lower(c, k4 + 2, q.z), q.w = unit_lower(c, k4 + 3, q.w);
+#pragma unroll
+                        for (int a = 0; a < RL; ++a) {
+                            x[a] = fmaf(-p[a][k4], q.x, x[a]);
+                            x[a] = fmaf(-p[a][k4 + 1], q.y, x[a]);
+                            x[a] = fmaf(-p[a][k4 + 2], q.z, x[a]);
+                            x[a] = fmaf(-p[a][k4 + 3], q.w, x[a]);
+                        }
+                    }
+                    st_rows<RL>(xp, x);
+                }
             }
-            if (!ok) break;
+            tc::fence_async_smem();  // this lane's shared-memory writes -> visible to the TMA store
+            __syncwarp();
+            if (lane == 0) tma::arrive(&done[st]);
         }
     }
 }
@@ -941,53 +821,6 @@ TmaShape shape_of(int nb, const UpdCfg &c) {
     return sh;
 }
 
-// Persistent launch of a tensor-core projection: one block per SM, the split count of
-// the reduction dimension (<= 8) chosen so the items fill the grid's block slots best.
-template <int NB, int SIDE>
-cudaError_t proj_tc_launch(const CUtensorMap &mX, const CUtensorMap &mV, int M, int N, const float *Tm, float *part,
-                           float *fin, const UpdScratch &sc, cudaStream_t st) {
-    static PerDeviceOnce attr;
-    allow_max_smem(proj_tc_kernel<NB, SIDE>, attr);
-    constexpr int LB = proj_land_bytes(NB), OB = proj_op_bytes(SIDE, NB);
-    // ring depths (landing, operand) and blocks per SM; NLA_PROJ_RING="SL,SO,B" overrides
-    static const int3 ring = [] {
-        int3 r = make_int3(0, 0, 0);
-        if (const char *v = getenv("NLA_PROJ_RING")) sscanf(v, "%d,%d,%d", &r.x, &r.y, &r.z);
-        return r;
-    }();
-    const int per_sm = ring.z > 0 ? std::min(ring.z, 4) : 1;
-    const size_t budget = kTmaSmemLimit / per_sm - 1024;
-    const int SO = std::max(2, std::min(kMaxOp, ring.y > 0 ? ring.y : 2));
-    const int SL = std::max(2, std::min(kLanding, ring.x > 0 ? ring.x : (int)((budget - (size_t)SO * OB) / LB)));
-    const size_t smem = (size_t)SL * LB + (size_t)SO * OB + 1024;
-    const int Lext = SIDE == 0 ? N : M, Kext = SIDE == 0 ? M : N;
-    const int nstrip = (Lext + 127) / 128, ktiles = (Kext + 31) / 32;
-    const int G = device_sm_count() * per_sm;
-    int nsplit = 1;
-    double best = -1.0;
-    for (int s = 1; s <= kMaxSplitTma && s <= ktiles; ++s) {
-        const long items = (long)nstrip * s;
-        const double eff = (double)items / ((double)((items + G - 1) / G) * G);  // busy fraction of block slots
-        if (eff > best + 1e-9) {
-            best = eff;
-            nsplit = s;
-        }
-    }
-    const int Ks = ((Kext + nsplit - 1) / nsplit + 31) / 32 * 32;
-    nsplit = (Kext + Ks - 1) / Ks;
-    const int grid = std::min(nstrip * nsplit, G);
-    return launch_pdl(proj_tc_kernel<NB, SIDE>, dim3(grid), dim3(32 * kTcWarps), smem, st, mX, mV, M, N, Tm, SL, SO,
-                      nsplit, Ks, part, fin, sc.tickets, sc.info);
-}
-
-bool proj_tc_enabled() {
-    static const bool on = [] {  // NLA_PROJ_TC=0: the SIMT projections instead of the tensor-core ones
-        const char *v = getenv("NLA_PROJ_TC");
-        return !v || atoi(v) != 0;
-    }();
-    return on;
-}
-
 template <int NB>
 cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long ldv, const float *Tm,
                          const TmaShape &sh, const UpdScratch &sc, cudaStream_t st) {
@@ -998,10 +831,28 @@ cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long 
         !tma_encode_2d(&mV, V, 4, M, NB, ldv * 4, kBoxRows, NB, false))
         return cudaErrorInvalidValue;
     // pass 1 (+ step 2): W' = T^T V^T X -- on the tensor cores (3xTF32) unless disabled
-    const bool use_tc = proj_tc_enabled();
+    static const bool use_tc = [] {
+        const char *v = getenv("NLA_PROJ_TC");
+        return !v || atoi(v) != 0;
+    }();
     CUtensorMap mVs;
     if (use_tc && tma_encode_2d(&mVs, V, 4, M, NB, ldv * 4, kBoxRows, NB, true)) {
-        cudaError_t e = proj_tc_launch<NB, 0>(mX, mVs, M, N, Tm, part, fin, sc, st);
+        static PerDeviceOnce attr;
+        allow_max_smem(qr_proj_tc_kernel<NB>, attr);
+        const int stage = 2 * (32 * 128 * 4) + 2 * NB * 128;
+        static const int sforce = [] {  // NLA_TC_STAGES: pipeline depth of the tensor-core projection
+            const char *v = getenv("NLA_TC_STAGES");
+            return v ? atoi(v) : 0;
+        }();
+        // 3 stages measured best at 8192 (deeper rings cost blocks per SM)
+        const int S = std::max(2, std::min({sforce > 0 ? sforce : 3, kMaxStages, (200 * 1024) / stage}));
+        const int nstrip = (N + 127) / 128;
+        int nsplit = splits_for(nstrip, (M + kBoxRows - 1) / kBoxRows, sh.waves);
+        const int Ms = ((M + nsplit - 1) / nsplit + kBoxRows - 1) / kBoxRows * kBoxRows;
+        nsplit = (M + Ms - 1) / Ms;
+        const size_t smem = (size_t)S * stage + 1024;
+        cudaError_t e = launch_pdl(qr_proj_tc_kernel<NB>, dim3(nstrip, nsplit), dim3(32 * kTcWarps), smem, st, mX, mVs,
+                                   M, N, Tm, S, Ms, part, fin, sc.tickets, sc.info);
         if (e != cudaSuccess) return e;
     } else {
         static PerDeviceOnce attr;
@@ -1020,41 +871,6 @@ cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long 
     return cudaGetLastError();
 }
 
-// Persistent grid of the strip update: as many blocks as the SMs hold (occupancy at
-// this shared-memory size), items = (strips of H rows) x (column chunks); the chunk
-// count is the one (at most `waves` chunks per block slot) whose items fill the block
-// slots best, ties to fewer chunks.
-template <typename K>
-void strip_grid(K kernel, int M, int N, int H, const TmaShape &sh, size_t smem, int &grid, int &Ns) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * (sh.nc + 1), smem) != cudaSuccess ||
-        per_sm < 1) {
-        cudaGetLastError();
-        per_sm = 1;
-    }
-    const int slots = per_sm * device_sm_count();
-    const int nstrip = (M + H - 1) / H, ntile = (N + sh.tc - 1) / sh.tc;
-    const int maxc = std::max(1, std::min(ntile, (sh.waves * slots + nstrip - 1) / nstrip));
-    int ncs = 1;
-    double best = -1.0;
-    for (int c = 1; c <= maxc; ++c) {
-        const long items = (long)nstrip * c;
-        const double eff = (double)items / ((double)((items + slots - 1) / slots) * slots);
-        if (eff > best + 1e-9) {
-            best = eff;
-            ncs = c;
-        }
-    }
-    static const bool all_items = [] {  // NLA_STRIP_GRID=1: one block per item instead of persistent blocks
-        const char *v = getenv("NLA_STRIP_GRID");
-        return v && atoi(v) != 0;
-    }();
-    if (all_items) ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, ntile));
-    Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
-    ncs = (N + Ns - 1) / Ns;
-    grid = all_items ? nstrip * ncs : std::min(nstrip * ncs, slots);
-}
-
 // pass 2 on rows [off, off + len) of the M x N trailing block: X -= V W'
 template <int NB>
 cudaError_t left_apply_nb(float *X, long ldx, int M, int N, const float *V, long ldv, int off, int len,
@@ -1070,10 +886,14 @@ cudaError_t left_apply_nb(float *X, long ldx, int M, int N, const float *V, long
         return cudaErrorInvalidValue;
     static PerDeviceOnce attr;
     allow_max_smem(strip_update_kernel<NB, 0>, attr);
-    const size_t smem = (size_t)sh.stages * stage_bytes_cols(NB, sh.tc) + 1024;
-    int grid = 0, Ns = 0;
-    strip_grid(strip_update_kernel<NB, 0>, len, N, 32 * (64 / NB), sh, smem, grid, Ns);
-    return launch_pdl(strip_update_kernel<NB, 0>, dim3(grid), dim3(32 * (sh.nc + 1)), smem, st, mX2, mQ, len, N,
+    constexpr int H = 32 * (64 / NB);
+    const int stage = stage_bytes_cols(NB, sh.tc);
+    const int nstrip = (len + H - 1) / H;
+    int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (N + sh.tc - 1) / sh.tc));
+    const int Ns = ((N + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
+    ncs = (N + Ns - 1) / Ns;
+    const size_t smem = (size_t)sh.stages * stage + 1024;
+    return launch_pdl(strip_update_kernel<NB, 0>, dim3(nstrip, ncs), dim3(32 * (sh.nc + 1)), smem, st, mX2, mQ, len, N,
                       Vo, ldv, sh.tc, sh.nc, sh.stages, Ns, off, sc.info);
 }
 
@@ -1083,10 +903,6 @@ cudaError_t right_proj_nb(float *X, long ldx, int M, int N, const float *Vt, lon
     float *part = reinterpret_cast<float *>(sc.work);
     float *fin = part + (size_t)kMaxSplitTma * 64 * std::max(M, N);
     CUtensorMap mX, mQ;
-    // pass 1 (+ step 2): Y' = X V T -- on the tensor cores (3xTF32) unless disabled
-    if (proj_tc_enabled() && tma_encode_2d(&mX, X, 4, M, N, ldx * 4, kBoxRows, 32, true) &&
-        tma_encode_2d(&mQ, Vt, 4, NB, N, ldvt * 4, NB, 32, false))
-        return proj_tc_launch<NB, 1>(mX, mQ, M, N, Tm, part, fin, sc, st);
     if (!tma_encode_2d(&mX, X, 4, M, N, ldx * 4, kBoxRows, sh.tc, true) ||
         !tma_encode_2d(&mQ, Vt, 4, NB, N, ldvt * 4, NB, sh.tc, false))
         return cudaErrorInvalidValue;
@@ -1094,6 +910,7 @@ cudaError_t right_proj_nb(float *X, long ldx, int M, int N, const float *Vt, lon
     const int stage = stage_bytes_cols(NB, sh.tc);
     const int nstrip = (M + H - 1) / H;
     const size_t smem = (size_t)sh.stages * stage + 1024;
+    // pass 1 (+ step 2): Y' = X V T
     static PerDeviceOnce attr;
     allow_max_smem(lq_proj_kernel<NB>, attr);
     int nsplit = splits_for(nstrip, (N + sh.tc - 1) / sh.tc, sh.waves);
@@ -1116,12 +933,16 @@ cudaError_t right_apply_nb(float *X, long ldx, int M, int N, const float *Vt, lo
     if (!tma_encode_2d(&mX, Xo, 4, M, len, ldx * 4, kBoxRows, sh.tc, true) ||
         !tma_encode_2d(&mQ, Vo, 4, NB, len, ldvt * 4, NB, sh.tc, false))
         return cudaErrorInvalidValue;
-    const size_t smem = (size_t)sh.stages * stage_bytes_cols(NB, sh.tc) + 1024;
+    constexpr int H = 32 * (64 / NB);
+    const int stage = stage_bytes_cols(NB, sh.tc);
+    const int nstrip = (M + H - 1) / H;
+    const size_t smem = (size_t)sh.stages * stage + 1024;
     static PerDeviceOnce attr;
     allow_max_smem(strip_update_kernel<NB, 1>, attr);
-    int grid = 0, Ns = 0;
-    strip_grid(strip_update_kernel<NB, 1>, M, len, 32 * (64 / NB), sh, smem, grid, Ns);
-    return launch_pdl(strip_update_kernel<NB, 1>, dim3(grid), dim3(32 * (sh.nc + 1)), smem, st, mX, mQ, M, len,
+    int ncs = std::max(1, std::min((sh.waves * device_sm_count() + nstrip - 1) / nstrip, (len + sh.tc - 1) / sh.tc));
+    const int Ns = ((len + ncs - 1) / ncs + sh.tc - 1) / sh.tc * sh.tc;
+    ncs = (len + Ns - 1) / Ns;
+    return launch_pdl(strip_update_kernel<NB, 1>, dim3(nstrip, ncs), dim3(32 * (sh.nc + 1)), smem, st, mX, mQ, M, len,
                       fin, 0L, sh.tc, sh.nc, sh.stages, Ns, off, sc.info);
 }
 

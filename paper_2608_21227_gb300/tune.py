@@ -2,6 +2,8 @@
 
     python -m paper_2608_21227_gb300.tune sweep  --sizes 1024 2048 4096 8192 --dtypes f32 f64 \
         --cache tuned/sweep.csv --table tuned/gb300.kt --summary tuned/sweep.json
+    python -m paper_2608_21227_gb300.tune sweep  --sizes 768 1536 --shapes 4096x1024 --no-pipeline \
+        --cache tuned/sweep.csv                       (more training rows for the cost model)
     python -m paper_2608_21227_gb300.tune batched --table tuned/gb300.kt --summary tuned/batched.json
     python -m paper_2608_21227_gb300.tune mlp --cache tuned/sweep.csv --holdout 3072 6144 12288 \
         --model tuned/mlp.bin --summary tuned/mlp.json
@@ -36,32 +38,43 @@ SIDES = {0: kt.KT_TRAIL_LEFT, 1: kt.KT_TRAIL_RIGHT}
 DEFAULT = (32, 64, 128, 2, 1)
 
 
+def parse_shapes(args):
+    shapes = [(n, n) for n in args.sizes]
+    for s in args.shapes:
+        m, n = (int(x) for x in s.lower().split("x"))
+        shapes.append((max(m, n), min(m, n)))
+    return shapes
+
+
 def sweep(args):
     summary = []
     os.makedirs(os.path.dirname(os.path.abspath(args.cache)), exist_ok=True)
     for dname in args.dtypes:
         dt = DT[dname]
-        for n in args.sizes:
+        for m, n in parse_shapes(args):
             per_band = {}
             for side, kern in SIDES.items():
                 for band in args.bands:
                     t0 = time.time()
-                    r = kt.tune(kern, n, n, dt, band=band, reps=args.reps, cache=args.cache, seed=n)
-                    r.update({"n": n, "dtype": dname, "side": side, "band": band, "seconds": time.time() - t0,
-                              "opt_over_median": r["median_ms"] / r["best_ms"],
+                    r = kt.tune(kern, m, n, dt, band=band, reps=args.reps, cache=args.cache, seed=n)
+                    r.update({"m": m, "n": n, "dtype": dname, "side": side, "band": band,
+                              "seconds": time.time() - t0, "opt_over_median": r["median_ms"] / r["best_ms"],
                               "default_over_opt": (r["default_ms"] / r["best_ms"]) if r["default_ms"] == r["default_ms"] else None})
                     summary.append(r)
                     per_band.setdefault(band, {})[side] = r
                     print(json.dumps(r), flush=True)
-            pipe = kt.tune(kt.KT_GESVD, n, n, dt, reps=2, cache=args.cache, seed=n)
+            if args.no_pipeline:
+                continue
+            pipe = kt.tune(kt.KT_GESVD, m, n, dt, reps=2, cache=args.cache, seed=n)
             band = pipe["best"][0]
-            rec = {"n": n, "dtype": dname, "pipeline": pipe}
+            rec = {"m": m, "n": n, "dtype": dname, "pipeline": pipe,
+                   "tuned_over_default": pipe["default_ms"] / pipe["best_ms"]}
             summary.append(rec)
             print(json.dumps(rec), flush=True)
             if args.table:
                 for side in (0, 1):
                     best = per_band[band][side]
-                    kt.write_table(args.table, side, n, n, dt, 0, best["best"], best["best_ms"])
+                    kt.write_table(args.table, side, m, n, dt, 0, best["best"], best["best_ms"])
     # mixed-precision forms: only the band width is a free parameter (pipeline level)
     for n in args.mixed_sizes:
         for upd in (nla.UPD_TF32, nla.UPD_BF16):
@@ -129,7 +142,7 @@ def read_cache(path):
     with open(path) as f:
         for r in csv.DictReader(f):
             r = {k: (float(v) if k == "median_ms" else int(v)) for k, v in r.items()}
-            if r["status"] == 0 and r["kernel"] in (0, 1) and r["median_ms"] > 0:
+            if r["status"] == 0 and r["kernel"] in (0, 1) and r["median_ms"] > 0 and r.get("objective", 0) == 0:
                 rows.append(r)
     return rows
 
@@ -177,6 +190,8 @@ def main():
     sub = ap.add_subparsers(dest="cmd", required=True)
     s = sub.add_parser("sweep")
     s.add_argument("--sizes", type=int, nargs="*", default=[1024, 2048, 4096, 8192])
+    s.add_argument("--shapes", nargs="*", default=[], help="rectangular problems MxN (m >= n)")
+    s.add_argument("--no-pipeline", action="store_true", help="kernel-level sweeps only (training data)")
     s.add_argument("--dtypes", nargs="+", default=["f32", "f64"])
     s.add_argument("--bands", type=int, nargs="+", default=[16, 32, 64])
     s.add_argument("--reps", type=int, default=5)
