@@ -168,12 +168,13 @@ __device__ int count_below_f(int n, const float *d, const float *e, float x, flo
     return neg - n;
 }
 
-// One matrix by one group: W (M x N, column-major, ld M) already loaded, M >= N.
+// One matrix by one group: W (M x N, column-major, leading dimension ldw) already
+// loaded, M >= N.
 __device__ void group_svd(float *W, int M, int N, float *d, float *e, float *vbuf, float *red, float *S, int gid,
-                          int g, int gt) {
+                          int g, int gt, int ldw) {
     for (int j = 0; j < N; ++j) {
         // ---- left reflector on column j, rows j..M-1
-        float *col = W + (size_t)j * M;
+        float *col = W + (size_t)j * ldw;
         float part = 0.f;
         for (int i = j + 1 + gt; i < M; i += g) part += col[i] * col[i];
         const float xn2 = gsum(part, red, gid, g, gt);
@@ -185,7 +186,7 @@ __device__ void group_svd(float *W, int M, int N, float *d, float *e, float *vbu
             // columns c > j: warp-per-column dot products, then the update
             const int wid = gt >> 5, lane = gt & 31, nw = g >> 5;
             for (int c = j + 1 + wid; c < N; c += nw) {
-                float *cc = W + (size_t)c * M;
+                float *cc = W + (size_t)c * ldw;
                 float s = lane == 0 ? cc[j] : 0.f;
                 for (int i = j + 1 + lane; i < M; i += 32) s += col[i] * cc[i];
                 s = nla::warp_sum(s) * tau;
@@ -200,20 +201,20 @@ __device__ void group_svd(float *W, int M, int N, float *d, float *e, float *vbu
         const int L = N - j - 1;
         float p2 = 0.f;
         for (int c = j + 2 + gt; c < N; c += g) {
-            float v = W[j + (size_t)c * M];
+            float v = W[j + (size_t)c * ldw];
             p2 += v * v;
         }
         const float yn2 = gsum(p2, red, gid, g, gt);
-        reflector(W[j + (size_t)(j + 1) * M], yn2, tau, beta, sc);
+        reflector(W[j + (size_t)(j + 1) * ldw], yn2, tau, beta, sc);
         if (gt == 0) e[j] = beta;
         if (tau != 0.f && L > 1) {
-            for (int c = gt; c < L; c += g) vbuf[c] = c == 0 ? 1.f : W[j + (size_t)(j + 1 + c) * M] * sc;
+            for (int c = gt; c < L; c += g) vbuf[c] = c == 0 ? 1.f : W[j + (size_t)(j + 1 + c) * ldw] * sc;
             gsync(gid, g);
             for (int i = j + 1 + gt; i < M; i += g) {  // one thread per row
                 float s = 0.f;
-                for (int c = 0; c < L; ++c) s += W[i + (size_t)(j + 1 + c) * M] * vbuf[c];
+                for (int c = 0; c < L; ++c) s += W[i + (size_t)(j + 1 + c) * ldw] * vbuf[c];
                 s *= tau;
-                for (int c = 0; c < L; ++c) W[i + (size_t)(j + 1 + c) * M] -= s * vbuf[c];
+                for (int c = 0; c < L; ++c) W[i + (size_t)(j + 1 + c) * ldw] -= s * vbuf[c];
             }
         }
         gsync(gid, g);
@@ -307,7 +308,7 @@ batched_svd_kernel(int batch, const int *__restrict__ dM, const int *__restrict_
                     W[idx] = tr ? A[c + (size_t)r * lda] : A[r + (size_t)c * lda];
                 }
                 gsync(gid, g);
-                if (N > 0) group_svd(W, M, N, d, e, vb, red, Sout, gid, g, gt);
+                if (N > 0) group_svd(W, M, N, d, e, vb, red, Sout, gid, g, gt, M);
                 if (gt == 0) dInfo[i] = 0;
             } else if (gt == 0) {
                 dInfo[i] = -NLA_ERR_UNSUPPORTED;
@@ -317,20 +318,195 @@ batched_svd_kernel(int batch, const int *__restrict__ dM, const int *__restrict_
     }
 }
 
+// ---------------------------------------------------------------- blocked QR (large matrices)
+// W (M x N, column-major, leading dimension ldw a multiple of 4, M >= N) is reduced to
+// R = Q^T W by blocked Householder QR with panels of PW columns: each panel (rows k0..M-1)
+// is factored in shared memory (column-major, leading dimension ldp), its compact-WY
+// factor T formed from V^T V (T(j, j) = tau_j, T(0:j, j) = -tau_j T(0:j, 0:j) V(:, 0:j)^T v_j),
+// and the trailing columns updated as X -= V (T^T (V^T X)) in two streaming passes
+// (X read once, then read and written once), so the trailing block is read 3 times per
+// PW columns instead of twice per column.  On return the top N x N block of W holds R
+// (zeros below its diagonal).  The singular values of R are those of W: R = Q^T W with Q
+// orthogonal (the same argument as Section 5.1.1's).
+template <int PW, int G>
+__device__ void group_qr_blocked(float *W, int ldw, int M, int N, float *Pm, int ldp, float *Wt, float *Tt, float *tau,
+                                 float *red, int gt) {
+    const int lane = gt & 31, wid = gt >> 5, nw = G / 32;
+    for (int k0 = 0; k0 < N; k0 += PW) {
+        const int nb = min(PW, N - k0), r = M - k0, C = N - k0 - nb;
+        // ---- load the panel (rows k0.., columns k0..k0+nb-1); zero rows up to ldp
+        for (int idx = gt; idx < PW * ldp; idx += G) {
+            const int k = idx / ldp, i = idx % ldp;
+            Pm[idx] = (k < nb && i < r) ? W[(k0 + i) + (size_t)(k0 + k) * ldw] : 0.f;
+        }
+        gsync(0, G);
+        // ---- factor the panel: reflector j on rows j..r-1, applied to the panel's columns > j
+        for (int j = 0; j < nb; ++j) {
+            float *col = Pm + (size_t)j * ldp;
+            float part = 0.f;
+            for (int i = j + 1 + gt; i < r; i += G) part += col[i] * col[i];
+            const float xn2 = gsum(part, red, 0, G, gt);
+            float t, beta, sc;
+            reflector(col[j], xn2, t, beta, sc);
+            if (gt == 0) tau[j] = t;
+            if (t != 0.f) {
+                for (int i = j + 1 + gt; i < r; i += G) col[i] *= sc;  // v, v_j = 1 implicit
+                gsync(0, G);
+                for (int c = j + 1 + wid; c < nb; c += nw) {
+                    float *cc = Pm + (size_t)c * ldp;
+                    float s = lane == 0 ? cc[j] : 0.f;
+                    for (int i = j + 1 + lane; i < r; i += 32) s += col[i] * cc[i];
+                    s = nla::warp_sum(s) * t;
+                    if (lane == 0) cc[j] -= s;
+                    for (int i = j + 1 + lane; i < r; i += 32) cc[i] -= s * col[i];
+                }
+            }
+            gsync(0, G);
+            if (gt == 0) col[j] = beta;
+            gsync(0, G);
+        }
+        // ---- R rows of the panel back to W (zeros below the diagonal within the top N rows),
+        // then V's unit diagonal and zeros above it in the panel
+        for (int idx = gt; idx < nb * nb; idx += G) {
+            const int i = idx % nb, k = idx / nb;
+            W[(k0 + i) + (size_t)(k0 + k) * ldw] = i <= k ? Pm[i + (size_t)k * ldp] : 0.f;
+        }
+        for (int idx = gt; idx < nb * (N - k0 - nb); idx += G) {  // rows k0+nb..N-1 of the panel columns
+            const int i = nb + idx % (N - k0 - nb), k = idx / (N - k0 - nb);
+            W[(k0 + i) + (size_t)(k0 + k) * ldw] = 0.f;
+        }
+        gsync(0, G);
+        for (int idx = gt; idx < nb * nb; idx += G) {
+            const int i = idx % nb, k = idx / nb;
+            if (i <= k) Pm[i + (size_t)k * ldp] = i == k ? 1.f : 0.f;
+        }
+        gsync(0, G);
+        if (C <= 0) continue;
+        // ---- T from V^T V (warp per entry of the strict upper triangle), then the recurrence
+        for (int e = wid; e < nb * nb; e += nw) {
+            const int a = e % nb, b = e / nb;
+            if (a >= b) continue;
+            const float *va = Pm + (size_t)a * ldp, *vb = Pm + (size_t)b * ldp;
+            float s = 0.f;
+            for (int i = lane; i < r; i += 32) s += va[i] * vb[i];
+            s = nla::warp_sum(s);
+            if (lane == 0) Tt[a + b * PW] = s;  // (V^T V)(a, b), overwritten by T below
+        }
+        gsync(0, G);
+        if (wid == 0) {
+            // column b of T: T(0:b, b) = -tau_b T(0:b, 0:b) (V^T V)(0:b, b), computed top-down in
+            // registers (lane a holds entry a); T(b, b) = tau_b
+            for (int b = 0; b < nb; ++b) {
+                const float g_ab = lane < b ? Tt[lane + b * PW] : 0.f;
+                float v = 0.f;
+                for (int a = 0; a < b; ++a) {  // v_lane = sum_a T(lane, a) g(a, b), T upper triangular
+                    const float ga = __shfl_sync(0xffffffffu, g_ab, a);
+                    if (lane <= a) v += Tt[lane + a * PW] * ga;
+                }
+                __syncwarp();
+                if (lane < b) Tt[lane + b * PW] = -tau[b] * v;
+                if (lane == b) Tt[b + b * PW] = tau[b];
+                __syncwarp();
+            }
+        }
+        gsync(0, G);
+        // ---- pass 1: Wt(:, c) = V^T X(:, c) (warp per column; each lane 4 consecutive rows)
+        const float *X0 = W + k0;  // X(i, c) = X0[i + (c0 + c) * ldw], c0 = k0 + nb
+        const int c0 = k0 + nb;
+        for (int c = wid; c < C; c += nw) {
+            const float *xc = X0 + (size_t)(c0 + c) * ldw;
+            float acc[PW];
+#pragma unroll
+            for (int k = 0; k < PW; ++k) acc[k] = 0.f;
+            for (int i0 = 4 * lane; i0 < r; i0 += 128) {
+                float4 x4;
+                if (i0 + 3 < r) {
+                    x4 = *reinterpret_cast<const float4 *>(xc + i0);
+                } else {
+                    x4.x = xc[i0];
+                    x4.y = i0 + 1 < r ? xc[i0 + 1] : 0.f;
+                    x4.z = i0 + 2 < r ? xc[i0 + 2] : 0.f;
+                    x4.w = 0.f;
+                }
+#pragma unroll
+                for (int k = 0; k < PW; ++k) {
+                    const float4 v4 = *reinterpret_cast<const float4 *>(Pm + (size_t)k * ldp + i0);
+                    acc[k] += v4.x * x4.x + v4.y * x4.y + v4.z * x4.z + v4.w * x4.w;
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < PW; ++k) {
+                const float s = nla::warp_sum(acc[k]);
+                if (lane == k) Wt[k * 256 + c] = s;
+            }
+        }
+        gsync(0, G);
+        // ---- W' = T^T Wt (in place, column by column: W'(k, c) = sum_{j <= k} T(j, k) Wt(j, c))
+        for (int c = gt; c < C; c += G) {
+            float w[PW];
+#pragma unroll
+            for (int k = 0; k < PW; ++k) w[k] = k < nb ? Wt[k * 256 + c] : 0.f;
+#pragma unroll
+            for (int k = PW - 1; k >= 0; --k) {
+                float v = 0.f;
+#pragma unroll
+                for (int j = 0; j <= k; ++j) v += Tt[j + k * PW] * w[j];
+                if (k < nb) Wt[k * 256 + c] = v;
+            }
+        }
+        gsync(0, G);
+        // ---- pass 2: X(:, c) -= V W'(:, c)
+        for (int c = wid; c < C; c += nw) {
+            float *xc = W + k0 + (size_t)(c0 + c) * ldw;
+            float wk[PW];
+#pragma unroll
+            for (int k = 0; k < PW; ++k) wk[k] = k < nb ? Wt[k * 256 + c] : 0.f;
+            for (int i0 = 4 * lane; i0 < r; i0 += 128) {
+                float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < PW; ++k) {
+                    const float4 v4 = *reinterpret_cast<const float4 *>(Pm + (size_t)k * ldp + i0);
+                    d.x += v4.x * wk[k], d.y += v4.y * wk[k], d.z += v4.z * wk[k], d.w += v4.w * wk[k];
+                }
+                if (i0 + 3 < r) {
+                    float4 x4 = *reinterpret_cast<float4 *>(xc + i0);
+                    x4.x -= d.x, x4.y -= d.y, x4.z -= d.z, x4.w -= d.w;
+                    *reinterpret_cast<float4 *>(xc + i0) = x4;
+                } else {
+                    xc[i0] -= d.x;
+                    if (i0 + 1 < r) xc[i0 + 1] -= d.y;
+                    if (i0 + 2 < r) xc[i0 + 2] -= d.z;
+                }
+            }
+        }
+        gsync(0, G);
+    }
+}
+
 // threads per block of the large-matrix kernel: 1024 per SM in blocks of G
 // (global scratch slots: one per block)
 constexpr int kLargeThreadsPerSm = 1024;
 constexpr int kLargeSlotsPerSm = kLargeThreadsPerSm / 128;
 
 // The matrices too large for shared memory (the sorted order's first counter[2]):
-// one per block of 256 threads, working in the block's global scratch slot (L2),
-// with several blocks per SM (no matrix shared memory) so that more of these
-// latency-bound reductions run at once.
+// one per block of G threads, working in the block's global scratch slot (leading
+// dimension rounded up to 4).  When its panel fits the block's shared memory
+// (ldp_max), a matrix is first reduced to its N x N triangular factor R by blocked
+// Householder QR (three streaming passes per 16 columns instead of two per column)
+// and R's singular values are found by the one-stage bidiagonalisation + bisection;
+// otherwise the one-stage reduction runs on the whole matrix.
+constexpr int kQrPanel = 16;
+
+__host__ __device__ constexpr size_t large_smem_floats(int ldp) {
+    return (size_t)kQrPanel * ldp + (size_t)kQrPanel * 256 + kQrPanel * kQrPanel + kQrPanel;
+}
+
 template <int G>
-__global__ void __launch_bounds__(G, kLargeThreadsPerSm / G)
+__global__ void __launch_bounds__(G)
 batched_large_kernel(const int *__restrict__ dM, const int *__restrict__ dN, const int *__restrict__ dLda,
                      float *const *dA, float *const *dS, const int *__restrict__ order, unsigned int *counter,
-                     float *scratch, size_t scratch_elems, int *dInfo) {
+                     float *scratch, size_t scratch_elems, int ldp_max, int *dInfo) {
+    extern __shared__ __align__(16) float qsm[];
     __shared__ float aux[800];
     __shared__ int sh_item;
     const int tid = threadIdx.x;
@@ -345,14 +521,24 @@ batched_large_kernel(const int *__restrict__ dM, const int *__restrict__ dN, con
         const float *A = dA[i];
         const int M = max(m, n), N = min(m, n);
         const bool tr = m < n;
+        const int ldw = (M + 3) & ~3;
         float *W = scratch + (size_t)blockIdx.x * scratch_elems;
-        if ((size_t)M * N <= scratch_elems && N <= 256) {
+        if ((size_t)ldw * N <= scratch_elems && N <= 256) {
             for (int idx = tid; idx < M * N; idx += G) {
                 const int r = idx % M, c = idx / M;  // W(r, c)
-                W[idx] = tr ? A[c + (size_t)r * lda] : A[r + (size_t)c * lda];
+                W[r + (size_t)c * ldw] = tr ? A[c + (size_t)r * lda] : A[r + (size_t)c * lda];
             }
             gsync(0, G);
-            if (N > 0) group_svd(W, M, N, aux, aux + 256, aux + 512, aux + 768, dS[i], 0, G, tid);
+            if (N > 0) {
+                if (ldw <= ldp_max && M > N) {
+                    float *Pm = qsm, *Wt = Pm + (size_t)kQrPanel * ldw, *Tt = Wt + kQrPanel * 256,
+                          *tau = Tt + kQrPanel * kQrPanel;
+                    group_qr_blocked<kQrPanel, G>(W, ldw, M, N, Pm, ldw, Wt, Tt, tau, aux + 768, tid);
+                    group_svd(W, N, N, aux, aux + 256, aux + 512, aux + 768, dS[i], 0, G, tid, ldw);
+                } else {
+                    group_svd(W, M, N, aux, aux + 256, aux + 512, aux + 768, dS[i], 0, G, tid, ldw);
+                }
+            }
             if (tid == 0) dInfo[i] = 0;
         } else if (tid == 0) {
             dInfo[i] = -NLA_ERR_UNSUPPORTED;
@@ -381,7 +567,7 @@ nla_status nla_gesvd_vals_batched_workspace(int batch, nla_dtype dtype, int max_
     if (!bytes || batch < 0 || max_m < 0 || max_n < 0) return berr(NLA_ERR_ARG, "bad arguments");
     if (dtype != NLA_F32) return berr(NLA_ERR_UNSUPPORTED, "the batched kernel supports FP32 only");
     const size_t blocks = (size_t)nla::device_sm_count() * std::max(2, kLargeSlotsPerSm);
-    const size_t slot = (size_t)std::max(max_m, 1) * std::max(max_n, 1);
+    const size_t slot = (size_t)((std::max(max_m, 1) + 3) & ~3) * std::max(max_n, 1);
     size_t b = 256;                                    // counter
     b += ((size_t)std::max(batch, 1) * 4 + 255) / 256 * 256;  // order
     b += blocks * slot * 4;                            // scratch slots
@@ -408,7 +594,7 @@ nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *dM, con
     unsigned int *counter = reinterpret_cast<unsigned int *>(w);
     int *order = reinterpret_cast<int *>(w + 256);
     float *scratch = reinterpret_cast<float *>(w + 256 + ((size_t)batch * 4 + 255) / 256 * 256);
-    const size_t slot = (size_t)std::max(max_m, 1) * std::max(max_n, 1);
+    const size_t slot = (size_t)((std::max(max_m, 1) + 3) & ~3) * std::max(max_n, 1);
     BatchCfg cfg = default_cfg();
     for (int b = 0; b < kBuckets; ++b)
         if (nla::g_batched_group[b] >= kMinGroup[b] && nla::g_batched_group[b] <= kBThreads &&
@@ -432,15 +618,31 @@ nla_status nla_gesvd_vals_batched(int batch, nla_dtype dtype, const int *dM, con
                 const int t = v ? atoi(v) : kLargeThreadsPerSm;
                 return std::max(256, std::min(t, kLargeThreadsPerSm));
             }();
-            // threads per large matrix: the tuned group of the largest bucket (128 or 256)
+            // threads per large matrix: the tuned group of the largest bucket (128 or 256); the
+            // blocked QR's panel is sized for the batch's largest row count when it fits
+            const int ldp = (std::max(max_m, max_n) + 3) & ~3;
+            const size_t qsmem = large_smem_floats(ldp) * sizeof(float);
+            const bool qr = qsmem <= (size_t)160 * 1024;
+            const size_t dsm = qr ? qsmem : 0;
+            auto launch_large = [&](auto kern, int G) {
+                static nla::PerDeviceOnce lattr;
+                lattr.run([&] {
+                    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+                    cudaGetLastError();
+                });
+                int per_sm = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, G, dsm) != cudaSuccess || per_sm < 1) {
+                    cudaGetLastError();
+                    per_sm = 1;
+                }
+                per_sm = std::min(per_sm, per_sm_threads / G);
+                kern<<<blocks * per_sm, G, dsm, st>>>(dM, dN, dLda, (float *const *)dA_array, (float *const *)dS_array,
+                                                      order, counter, scratch, slot, qr ? ldp : 0, dInfo);
+            };
             if (cfg.group[kBuckets - 1] == 128)
-                batched_large_kernel<128><<<blocks * (per_sm_threads / 128), 128, 0, st>>>(
-                    dM, dN, dLda, (float *const *)dA_array, (float *const *)dS_array, order, counter, scratch, slot,
-                    dInfo);
+                launch_large(batched_large_kernel<128>, 128);
             else
-                batched_large_kernel<256><<<blocks * (per_sm_threads / 256), 256, 0, st>>>(
-                    dM, dN, dLda, (float *const *)dA_array, (float *const *)dS_array, order, counter, scratch, slot,
-                    dInfo);
+                launch_large(batched_large_kernel<256>, 256);
         }
         batched_svd_kernel<<<blocks, kBThreads, main_smem, st>>>(batch, dM, dN, dLda, (float *const *)dA_array,
                                                                  (float *const *)dS_array, order, counter, scratch, slot,
