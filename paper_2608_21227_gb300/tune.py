@@ -141,7 +141,10 @@ def read_cache(path):
     rows = []
     with open(path) as f:
         for r in csv.DictReader(f):
-            r = {k: (float(v) if k == "median_ms" else int(v)) for k, v in r.items()}
+            extra = r.pop(None, None)  # (a row with the objective column under an older header)
+            r = {k: (float(v) if k == "median_ms" else int(v)) for k, v in r.items() if v is not None}
+            if extra:
+                r["objective"] = int(extra[0])
             if r["status"] == 0 and r["kernel"] in (0, 1) and r["median_ms"] > 0 and r.get("objective", 0) == 0:
                 rows.append(r)
     return rows
