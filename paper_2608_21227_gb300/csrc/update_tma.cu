@@ -33,7 +33,6 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
-#include <cstdio>
 #include <cstdlib>
 
 #include "common.cuh"
@@ -84,11 +83,6 @@ NLA_DEV float unit_lower(int r, int k, float v) { return r > k ? v : (r == k ? 1
 NLA_DEV unsigned char *align1k(unsigned char *p) {
     return reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(p) + 1023) & ~uintptr_t(1023));
 }
-
-// The block's abort flag as the warp sees it: lane 0 reads it and the value is broadcast,
-// so a warp leaves its loop as a whole (the warp-collective operations after the loop
-// then see every lane).
-NLA_DEV bool abort_seen(const int *flag) { return __shfl_sync(0xffffffffu, *(volatile const int *)flag, 0) != 0; }
 
 // Named barrier over the consumer warps (ids 1..; 0 is __syncthreads).
 NLA_DEV void consumers_sync(int nc) { asm volatile("bar.sync 1, %0;" ::"r"(nc * 32) : "memory"); }
@@ -195,7 +189,7 @@ qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             for (int i = 0; i < 4; ++i) acc[a][i] = 0.f;
         for (int t = 0; t < nt; ++t) {
             const int st = t % S;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || abort_seen(&sh_abort)) break;
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
             const unsigned char *sb = base + (size_t)st * stage;
             const int r0 = rbeg + t * th;  // trailing-matrix row of the stage's first row
             const bool diag_stage = r0 < NB;  // only the stage holding V's unit diagonal needs masking
@@ -399,7 +393,7 @@ qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
         const int ct = tid - 64;  // 0..127
         for (int t = 0; t < nt; ++t) {
             const int st = t % S;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || abort_seen(&sh_abort)) {
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) {
                 sh_abort = 1;
                 break;
             }
@@ -436,7 +430,7 @@ qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
         tc::fence_after_sync();
         const int q = warp & 3;  // TMEM lanes 32q .. 32q + 31
         const int col = 32 * q + lane;
-        if (ok && !abort_seen(&sh_abort)) {
+        if (ok && !*(volatile int *)&sh_abort) {
 #pragma unroll
             for (int c = 0; c < NB; c += 16) {
                 float w[16];
@@ -542,7 +536,7 @@ lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             for (int k = 0; k < NB; ++k) acc[a][k] = 0.f;
         for (int t = 0; t < nt; ++t) {
             const int st = t % S;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || abort_seen(&sh_abort)) break;
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
             unsigned char *sb = base + (size_t)st * stage;
             const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
             const int cb = cbeg + t * tcols;
@@ -732,7 +726,7 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
         }
         for (int t = 0; t < nt; ++t) {
             const int st = t % S;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || abort_seen(&sh_abort)) break;
+            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
             unsigned char *sb = base + (size_t)st * stage;
             const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
             const int cb = cbeg + t * tcols;
