@@ -119,6 +119,25 @@ NLA_DEV bool mbar_wait_warp(uint64_t *mbar, uint32_t parity, int *info) {
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
+// Wait by every lane of a warp, with no warp shuffle on the way: each lane polls the
+// phase itself; lane 0 alone keeps the time budget and, when it runs out, records
+// kInfoTimeout and raises *abort (a shared-memory flag the other lanes poll too), so the
+// whole warp gives up.  For loops whose per-stage latency matters.
+NLA_DEV bool mbar_wait_lanes(uint64_t *mbar, uint32_t parity, int *info, volatile int *abort) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    const bool leader = (threadIdx.x & 31) == 0;
+    const unsigned long long t0 = leader ? global_ns() : 0ull;
+    while (!mbar_try_wait(mbar, parity)) {
+        if (*abort) return false;
+        if (leader && global_ns() - t0 > kSpinBudgetNs) {
+            if (info) atomicExch(info, kInfoTimeout);
+            *abort = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
 // ---- TMEM -> registers: this warp's 32 lanes, 16 consecutive 32-bit columns
 NLA_DEV void tmem_ld16(uint32_t taddr, float v[16]) {
     uint32_t r[16];

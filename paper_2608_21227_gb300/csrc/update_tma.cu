@@ -189,7 +189,7 @@ qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             for (int i = 0; i < 4; ++i) acc[a][i] = 0.f;
         for (int t = 0; t < nt; ++t) {
             const int st = t % S;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
+            if (!tc::mbar_wait_lanes(&full[st], (uint32_t)((t / S) & 1), info, &sh_abort) || sh_abort) break;
             const unsigned char *sb = base + (size_t)st * stage;
             const int r0 = rbeg + t * th;  // trailing-matrix row of the stage's first row
             const bool diag_stage = r0 < NB;  // only the stage holding V's unit diagonal needs masking
@@ -393,7 +393,7 @@ qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
         const int ct = tid - 64;  // 0..127
         for (int t = 0; t < nt; ++t) {
             const int st = t % S;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) {
+            if (!tc::mbar_wait_lanes(&full[st], (uint32_t)((t / S) & 1), info, &sh_abort) || sh_abort) {
                 sh_abort = 1;
                 break;
             }
@@ -536,7 +536,7 @@ lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
             for (int k = 0; k < NB; ++k) acc[a][k] = 0.f;
         for (int t = 0; t < nt; ++t) {
             const int st = t % S;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
+            if (!tc::mbar_wait_lanes(&full[st], (uint32_t)((t / S) & 1), info, &sh_abort) || sh_abort) break;
             unsigned char *sb = base + (size_t)st * stage;
             const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
             const int cb = cbeg + t * tcols;
@@ -726,7 +726,7 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
         }
         for (int t = 0; t < nt; ++t) {
             const int st = t % S;
-            if (!tc::mbar_wait_warp(&full[st], (uint32_t)((t / S) & 1), info) || *(volatile int *)&sh_abort) break;
+            if (!tc::mbar_wait_lanes(&full[st], (uint32_t)((t / S) & 1), info, &sh_abort) || sh_abort) break;
             unsigned char *sb = base + (size_t)st * stage;
             const float *qs = reinterpret_cast<const float *>(sb + RL * xbytes);
             const int cb = cbeg + t * tcols;
