@@ -73,6 +73,10 @@ nla_cfg resolve_cfg(int m, int n, nla_dtype dt, const nla_opts *opts, int side_h
     nla_cfg c = kDefaultCfg;
     nla_cfg tuned;
     int upd = opts ? (int)opts->update : 0;
+    // the compensated forms run the TF32 / BF16 kernels with three products: their tuned
+    // band is the base form's
+    if (upd == NLA_UPD_TF32X3) upd = NLA_UPD_TF32;
+    if (upd == NLA_UPD_BF16X3) upd = NLA_UPD_BF16;
     if (nla_tuned_lookup(m, n, (int)dt, upd, side_hint, &tuned)) c = tuned;
     if (opts && opts->cfg) {
         const nla_cfg *u = opts->cfg;

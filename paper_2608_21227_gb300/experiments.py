@@ -93,7 +93,10 @@ def mixed(args):
                    "mixed_config": "tuned table" if args.table else "default",
                    "fp64_err_vs_sigma": float(np.max(np.abs(s64 - sig)) / sig[0])}
             mask = sig >= 1e-3 * sig[0]
-            for name, upd in (("tf32", nla.UPD_TF32), ("bf16", nla.UPD_BF16)):
+            for name, upd in (("tf32", nla.UPD_TF32), ("bf16", nla.UPD_BF16), ("tf32x3", nla.UPD_TF32X3),
+                              ("bf16x3", nla.UPD_BF16X3)):
+                # the compensated forms have no tuned entries of their own: they take the
+                # table's TF32 band when the table is installed (same kernels, three products)
                 t, s = timed_call(A, upd, reps, args.table)
                 rec[name] = {"ms": t, "speedup_vs_fp64": t64 / t,
                              "err_vs_sigma": float(np.max(np.abs(s - sig)) / sig[0]),
