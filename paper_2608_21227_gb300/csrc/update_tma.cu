@@ -355,8 +355,8 @@ qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
                     sh_abort = 1;
                     break;
                 }
-                tma::expect_tx(&full[st], (uint32_t)(xbytes + vbytes));
                 const int r0 = rbeg + t * kBoxRows;
+                tma::expect_tx(&full[st], (uint32_t)(xbytes + vbytes));
                 tma::load_2d(xhi(st), &tmX, r0, c0, &full[st]);
                 tma::load_2d(vhi(st), &tmV, r0, 0, &full[st]);
                 issued = t + 1;
@@ -478,8 +478,12 @@ qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
 // ------------------------------------------------------------------ lq_proj
 // Block (strip, s): partial Y(strip rows, :) = X(strip rows, columns of split s) V
 // over stages of tc columns; last block of the strip: Y' = Y T -> fin[k*M + i].
+// At NB = 16 the kernel is capped at 128 registers so three blocks of 160 threads share
+// an SM (12 consumer warps instead of 8 hide the shared-memory latency of the FMA
+// stream; 46.8 -> 44.4 ms of LQ-side update per 8192 SVD, no spills); the wider forms
+// keep their 168.
 template <int NB>
-__global__ void __launch_bounds__(kMaxThreads, 1)
+__global__ void __launch_bounds__(kMaxThreads, 1) __maxnreg__(NB == 16 ? 128 : 168)
 lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmQ, int M, int N,
                const float *__restrict__ Tm, int tcols, int NC, int S, int Ns, float *part, float *fin,
                unsigned int *tickets, int *info) {
@@ -815,6 +819,24 @@ TmaShape shape_of(int nb, const UpdCfg &c) {
     return sh;
 }
 
+// NLA_PROJ_TC=0: the SIMT QR projection instead of the tensor-core one.
+bool proj_tc() {
+    static const bool on = [] {
+        const char *v = getenv("NLA_PROJ_TC");
+        return !v || atoi(v) != 0;
+    }();
+    return on;
+}
+// Pipeline depth of the tensor-core projection: 3 stages measured best at 8192 (deeper
+// rings cost blocks per SM); NLA_TC_STAGES overrides.
+int tc_stages(int stage_bytes) {
+    static const int sforce = [] {
+        const char *v = getenv("NLA_TC_STAGES");
+        return v ? atoi(v) : 0;
+    }();
+    return std::max(2, std::min({sforce > 0 ? sforce : 3, kMaxStages, (200 * 1024) / stage_bytes}));
+}
+
 template <int NB>
 cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long ldv, const float *Tm,
                          const TmaShape &sh, const UpdScratch &sc, cudaStream_t st) {
@@ -825,21 +847,12 @@ cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long 
         !tma_encode_2d(&mV, V, 4, M, NB, ldv * 4, kBoxRows, NB, false))
         return cudaErrorInvalidValue;
     // pass 1 (+ step 2): W' = T^T V^T X -- on the tensor cores (3xTF32) unless disabled
-    static const bool use_tc = [] {
-        const char *v = getenv("NLA_PROJ_TC");
-        return !v || atoi(v) != 0;
-    }();
     CUtensorMap mVs;
-    if (use_tc && tma_encode_2d(&mVs, V, 4, M, NB, ldv * 4, kBoxRows, NB, true)) {
+    if (proj_tc() && tma_encode_2d(&mVs, V, 4, M, NB, ldv * 4, kBoxRows, NB, true)) {
         static PerDeviceOnce attr;
         allow_max_smem(qr_proj_tc_kernel<NB>, attr);
         const int stage = 2 * (32 * 128 * 4) + 2 * NB * 128;
-        static const int sforce = [] {  // NLA_TC_STAGES: pipeline depth of the tensor-core projection
-            const char *v = getenv("NLA_TC_STAGES");
-            return v ? atoi(v) : 0;
-        }();
-        // 3 stages measured best at 8192 (deeper rings cost blocks per SM)
-        const int S = std::max(2, std::min({sforce > 0 ? sforce : 3, kMaxStages, (200 * 1024) / stage}));
+        const int S = tc_stages(stage);
         const int nstrip = (N + 127) / 128;
         int nsplit = splits_for(nstrip, (M + kBoxRows - 1) / kBoxRows, sh.waves);
         const int Ms = ((M + nsplit - 1) / nsplit + kBoxRows - 1) / kBoxRows * kBoxRows;

@@ -19,7 +19,10 @@ def nla():
 
 
 @pytest.mark.parametrize("dt", [0, 1])
-@pytest.mark.parametrize("m,n,b", [(300, 200, 16), (256, 256, 32), (150, 150, 64), (90, 45, 8)])
+@pytest.mark.parametrize("m,n,b", [(300, 200, 16), (256, 256, 32), (150, 150, 64), (90, 45, 8),
+                                   # FP32: several 128-row strips, column splits and ragged tails of the
+                                   # TMA / tensor-core projections on both sides
+                                   (1100, 900, 16), (1032, 1000, 32), (1064, 1064, 64)])
 def test_stage1_band(nla, dt, m, n, b):
     A = inputs.gaussian(m, n, 500 + m + b)
     tdt = torch.float64 if dt == 0 else torch.float32
