@@ -21,6 +21,9 @@
 //   qr_proj_tc    W = V^T X on the tensor cores (the default QR projection):
 //                 tcgen05 kind::tf32 MMAs on the TMA boxes, FP32 accuracy from
 //                 the three-term hi/lo split, accumulator in TMEM.
+//   lq_proj_tm    Y = X V on the tensor cores (the default LQ projection): the
+//                 hi/lo rows of X go from the landed boxes to tensor memory
+//                 (tcgen05.st) and feed the MMAs as their A operand there.
 //
 // The projections are split over the long dimension; the last block of each
 // strip (atomic ticket, nobody waits) sums the partials in a fixed order and
@@ -634,6 +637,219 @@ lq_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
     if (tid == 0) tickets[blockIdx.x] = 0u;
 }
 
+// ------------------------------------------------------------------ lq_proj_tm
+// Block (strip, s): partial Y(128 strip rows, :) = X(strip rows, columns of split s) V on
+// the tensor cores (kind::tf32, M = 128 rows, N = NB, K = 8 columns per instruction) over
+// stages of 32 columns; last block of the strip: Y' = Y T -> fin[k*M + i].
+// The reduction runs over X's columns, which are strided in a column-major matrix, and a
+// kind::tf32 operand in shared memory must be K-major; so the A operand goes through
+// tensor memory instead.  Each converter warp owns 32 rows (its TMEM lane quadrant):
+// lane i reads X(i, c) for the stage's 32 columns from the landed box (one 128-byte line
+// per column, no bank conflict), splits it into hi + lo (the same three-term split as
+// qr_proj_tc) and stores both to TMEM (tcgen05.st, 32 columns each); the box is free
+// as soon as it has been read.  V(c, k) of the stage's columns comes from global memory
+// (L2), masked to the unit lower form and written K-major as its hi and lo copies (B).
+// Rings: kLqStages TMEM/B operand slots (freed by the MMA commit) behind an X ring
+// sized to the shared memory (freed by the converters).
+constexpr int kLqCols = 32;    // columns per stage
+constexpr int kLqStages = 3;   // operand slots: 64 TMEM columns each (A hi, A lo)
+constexpr int kLqXBox = kBoxRows * kLqCols * 4;  // one 32 x 32 box, no swizzle: 4 KB
+constexpr int lq_tm_opnd_bytes(int nb) { return 2 * nb * 128; }
+
+template <int NB>
+__global__ void __launch_bounds__(32 * kTcWarps, 1)
+lq_proj_tm_kernel(const __grid_constant__ CUtensorMap tmX, int M, int N, const float *__restrict__ Vt, long ldvt,
+                  const float *__restrict__ Tm, int SX, int Ns, float *part, float *fin, unsigned int *tickets,
+                  int *info) {
+    pdl_wait();
+    pdl_trigger();
+    constexpr int H = 128;                            // rows per block = the MMA's M
+    constexpr int kX = 4 * kLqXBox;                   // the stage's 128 rows
+    constexpr int kB = NB * 128;                      // V^T of the stage's 32 columns (hi or lo)
+    constexpr uint32_t kD = NB < 32 ? 32 : NB;        // TMEM columns of the accumulator
+    constexpr uint32_t kCols = kD + 64 * kLqStages <= 256 ? 256 : 512;
+    static_assert(kD + 64 * kLqStages <= 256, "TMEM budget: two blocks per SM");
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t xfull[kMaxStages], xfree[kMaxStages], conv[kLqStages], ofree[kLqStages], accdone;
+    __shared__ uint32_t tmem_base;
+    __shared__ int sh_last, sh_abort;
+    unsigned char *base = align1k(smem_raw);
+    unsigned char *bring = base + (size_t)SX * kX;    // operand B slots (1024-byte aligned)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int i0 = blockIdx.x * H, hr = min(H, M - i0);
+    const int s = blockIdx.y, nsplit = gridDim.y;
+    const int cbeg = s * Ns, cend = min(N, cbeg + Ns);
+    const int nt = (cend - cbeg + kLqCols - 1) / kLqCols;
+    if (tid == 0) {
+        for (int i = 0; i < SX; ++i) {
+            tc::mbar_init(&xfull[i], 1);
+            tc::mbar_init(&xfree[i], 4);
+        }
+        for (int i = 0; i < kLqStages; ++i) {
+            tc::mbar_init(&conv[i], 4);
+            tc::mbar_init(&ofree[i], 1);
+        }
+        tc::mbar_init(&accdone, 1);
+        sh_abort = 0;
+        tma::fence_init();
+        tma::prefetch_map(&tmX);
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(&tmem_base, kCols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = tmem_base;
+    auto acol = [&](int o) { return kD + 64u * (uint32_t)o; };  // A hi at acol, A lo at acol + 32
+    auto bhi = [&](int o) { return bring + (size_t)o * 2 * kB; };
+    auto blo = [&](int o) { return bring + (size_t)o * 2 * kB + kB; };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int issued = 0;
+            for (int t = 0; t < nt; ++t) {
+                const int xs = t % SX;
+                if (t >= SX && !tc::mbar_wait(&xfree[xs], (uint32_t)(((t / SX) - 1) & 1), info)) {
+                    sh_abort = 1;
+                    break;
+                }
+                unsigned char *xb = base + (size_t)xs * kX;
+                tma::expect_tx(&xfull[xs], (uint32_t)kX);
+                const int cb = cbeg + t * kLqCols;
+                for (int bx = 0; bx < 4; ++bx) tma::load_2d(xb + bx * kLqXBox, &tmX, i0 + bx * kBoxRows, cb, &xfull[xs]);
+                issued = t + 1;
+            }
+            drain_loads(xfull, issued, SX, info);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t id = tc::idesc(2, 128, NB);
+            for (int t = 0; t < nt; ++t) {
+                const int o = t % kLqStages;
+                if (*(volatile int *)&sh_abort || !tc::mbar_wait(&conv[o], (uint32_t)((t / kLqStages) & 1), info)) {
+                    sh_abort = 1;
+                    break;
+                }
+                tc::fence_after_sync();
+                const uint32_t ah = tbase + acol(o), al = ah + 32;
+                const uint32_t bh = tc::smem_u32(bhi(o)), bl = tc::smem_u32(blo(o));
+#pragma unroll
+                for (int kk = 0; kk < kLqCols / 8; ++kk) {  // 8 columns per instruction
+                    const uint32_t off = kk * 32;
+                    tc::mma_tf32_tmem_a(tbase, ah + 8 * kk, tc::sdesc_sw128(bh + off), id, (t > 0 || kk > 0) ? 1u : 0u);
+                    tc::mma_tf32_tmem_a(tbase, ah + 8 * kk, tc::sdesc_sw128(bl + off), id, 1u);
+                    tc::mma_tf32_tmem_a(tbase, al + 8 * kk, tc::sdesc_sw128(bh + off), id, 1u);
+                }
+                tc::mma_commit(&ofree[o]);  // the operand slot is free once these MMAs have read it
+            }
+            tc::mma_commit(&accdone);
+        }
+        __syncwarp();
+    } else {
+        // ---- warps 2..5: rows 32q .. 32q + 31 of the strip (TMEM lane quadrant q = box q)
+        const int q = warp & 3, ct = tid - 64;
+        constexpr int kVe = NB * kLqCols / 128;  // V entries per thread and stage
+        const uint32_t lane_base = tbase + ((uint32_t)(32 * q) << 16);
+        for (int t = 0; t < nt; ++t) {
+            const int xs = t % SX, o = t % kLqStages;
+            const int cb = cbeg + t * kLqCols;
+            float v[kVe];
+#pragma unroll
+            for (int u = 0; u < kVe; ++u) {  // entry (k, j): V(cb + j, k), unit lower
+                const int e = ct + 128 * u, j = e / NB, k = e % NB, c = cb + j;
+                v[u] = c < cend ? unit_lower(c, k, __ldg(Vt + k + (size_t)c * ldvt)) : 0.f;
+            }
+            if (!tc::mbar_wait_lanes(&xfull[xs], (uint32_t)((t / SX) & 1), info, &sh_abort) || sh_abort) {
+                sh_abort = 1;
+                break;
+            }
+            float x[kLqCols], h[kLqCols];
+            const float *xb = reinterpret_cast<const float *>(base + (size_t)xs * kX + q * kLqXBox);
+#pragma unroll
+            for (int c = 0; c < kLqCols; ++c) x[c] = xb[c * kBoxRows + lane];  // X(32q + lane, cb + c)
+            __syncwarp();
+            if (lane == 0) tma::arrive(&xfree[xs]);  // the box is read
+            if (t >= kLqStages &&
+                (!tc::mbar_wait_lanes(&ofree[o], (uint32_t)(((t / kLqStages) - 1) & 1), info, &sh_abort) ||
+                 sh_abort)) {
+                sh_abort = 1;
+                break;
+            }
+            tc::fence_after_sync();
+#pragma unroll
+            for (int c = 0; c < kLqCols; ++c) {
+                h[c] = tf32_hi(x[c]);
+                x[c] -= h[c];
+            }
+            tc::tmem_st32(lane_base + acol(o), h);
+            tc::tmem_st32(lane_base + acol(o) + 32, x);
+            float *vh = reinterpret_cast<float *>(bhi(o));
+            float *vl = reinterpret_cast<float *>(blo(o));
+#pragma unroll
+            for (int u = 0; u < kVe; ++u) {  // row k, 16-byte chunk (j/4) ^ (k & 7), word j % 4
+                const int e = ct + 128 * u, j = e / NB, k = e % NB;
+                const int w = k * 32 + (((j >> 2) ^ (k & 7)) << 2) + (j & 3);
+                vh[w] = v[u];
+                vl[w] = v[u] - tf32_hi(v[u]);
+            }
+            tc::tmem_wait_st();
+            tc::fence_async_smem();  // the B copies -> visible to the tensor core
+            tc::fence_before_sync();
+            __syncwarp();
+            if (lane == 0) tma::arrive(&conv[o]);
+        }
+        // epilogue: rows 32q .. 32q + 31 of the block from the accumulator's lane quadrant
+        const bool ok = tc::mbar_wait_warp(&accdone, 0, info);
+        tc::fence_after_sync();
+        const int i = 32 * q + lane;
+        if (ok && !*(volatile int *)&sh_abort) {
+#pragma unroll
+            for (int c = 0; c < NB; c += 16) {
+                float y[16];
+                tc::tmem_ld16(lane_base + (uint32_t)c, y);
+                tc::tmem_wait_ld();
+                if (i < hr) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) part[((size_t)s * NB + c + k) * M + i0 + i] = y[k];
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 1) tc::tmem_dealloc(tbase, kCols);
+    __threadfence();
+    __syncthreads();
+    if (sh_abort) return;
+    if (tid == 0) sh_last = atomicAdd(&tickets[blockIdx.x], 1u) == (unsigned)(nsplit - 1);
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+    float *Y = reinterpret_cast<float *>(base);
+    for (int idx = tid; idx < NB * H; idx += blockDim.x) {
+        const int k = idx / H, i = idx % H;
+        float sum = 0.f;
+        if (i < hr)
+#pragma unroll
+            for (int qq = 0; qq < kMaxSplitTma; ++qq)  // (all partial loads in flight at once)
+                if (qq < nsplit) sum += __ldcg(part + ((size_t)qq * NB + k) * M + i0 + i);
+        Y[idx] = sum;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NB * H; idx += blockDim.x) {
+        const int k = idx / H, i = idx % H;
+        if (i >= hr) continue;
+        float sum = 0.f;
+#pragma unroll
+        for (int j = 0; j < NB; ++j)
+            if (j <= k) sum = fmaf(Y[j * H + i], __ldg(Tm + j + (size_t)k * NB), sum);
+        fin[(size_t)k * M + i0 + i] = sum;
+    }
+    if (tid == 0) tickets[blockIdx.x] = 0u;
+}
+
 // ------------------------------------------------------------------ strip_update
 // Block (strip, cs): X(strip rows, columns of split cs) -= P(strip rows, :) Q(cols, :)^T.
 // SIDE 0 (QR): P = V (unit lower, column-major at Pv, ld ldp), Q = W'^T from
@@ -819,13 +1035,14 @@ TmaShape shape_of(int nb, const UpdCfg &c) {
     return sh;
 }
 
-// NLA_PROJ_TC=0: the SIMT QR projection instead of the tensor-core one.
-bool proj_tc() {
-    static const bool on = [] {
+// NLA_PROJ_TC: which projections run on the tensor cores (bit 0: QR side, bit 1: LQ
+// side; default both; 0: both on the SIMT kernels).
+bool proj_tc(int side) {
+    static const int mask = [] {
         const char *v = getenv("NLA_PROJ_TC");
-        return !v || atoi(v) != 0;
+        return v ? (atoi(v) & 3) : 3;
     }();
-    return on;
+    return (mask >> side) & 1;
 }
 // Pipeline depth of the tensor-core projection: 3 stages measured best at 8192 (deeper
 // rings cost blocks per SM); NLA_TC_STAGES overrides.
@@ -848,7 +1065,7 @@ cudaError_t left_proj_nb(float *X, long ldx, int M, int N, const float *V, long 
         return cudaErrorInvalidValue;
     // pass 1 (+ step 2): W' = T^T V^T X -- on the tensor cores (3xTF32) unless disabled
     CUtensorMap mVs;
-    if (proj_tc() && tma_encode_2d(&mVs, V, 4, M, NB, ldv * 4, kBoxRows, NB, true)) {
+    if (proj_tc(0) && tma_encode_2d(&mVs, V, 4, M, NB, ldv * 4, kBoxRows, NB, true)) {
         static PerDeviceOnce attr;
         allow_max_smem(qr_proj_tc_kernel<NB>, attr);
         const int stage = 2 * (32 * 128 * 4) + 2 * NB * 128;
@@ -913,11 +1130,26 @@ cudaError_t right_proj_nb(float *X, long ldx, int M, int N, const float *Vt, lon
     if (!tma_encode_2d(&mX, X, 4, M, N, ldx * 4, kBoxRows, sh.tc, true) ||
         !tma_encode_2d(&mQ, Vt, 4, NB, N, ldvt * 4, NB, sh.tc, false))
         return cudaErrorInvalidValue;
+    // pass 1 (+ step 2): Y' = X V T -- on the tensor cores (3xTF32, A through TMEM) unless disabled
+    CUtensorMap mXt;
+    if (proj_tc(1) && tma_encode_2d(&mXt, X, 4, M, N, ldx * 4, kBoxRows, kLqCols, false)) {
+        static PerDeviceOnce attr_tm;
+        allow_max_smem(lq_proj_tm_kernel<NB>, attr_tm);
+        // X ring: what two blocks per SM leave beside the operand slots
+        const int sx = std::max(2, std::min(kMaxStages, (int)((108 * 1024 - kLqStages * lq_tm_opnd_bytes(NB)) /
+                                                              (4 * kLqXBox))));
+        const int nstrip = (M + 127) / 128;
+        int nsplit = splits_for(nstrip, (N + kLqCols - 1) / kLqCols, sh.waves);
+        const int Ns = ((N + nsplit - 1) / nsplit + kLqCols - 1) / kLqCols * kLqCols;
+        nsplit = (N + Ns - 1) / Ns;
+        const size_t smem = (size_t)sx * 4 * kLqXBox + (size_t)kLqStages * lq_tm_opnd_bytes(NB) + 1024;
+        return launch_pdl(lq_proj_tm_kernel<NB>, dim3(nstrip, nsplit), dim3(32 * kTcWarps), smem, st, mXt, M, N, Vt,
+                          ldvt, Tm, sx, Ns, part, fin, sc.tickets, sc.info);
+    }
     constexpr int H = 32 * (64 / NB);
     const int stage = stage_bytes_cols(NB, sh.tc);
     const int nstrip = (M + H - 1) / H;
     const size_t smem = (size_t)sh.stages * stage + 1024;
-    // pass 1 (+ step 2): Y' = X V T
     static PerDeviceOnce attr;
     allow_max_smem(lq_proj_kernel<NB>, attr);
     int nsplit = splits_for(nstrip, (N + sh.tc - 1) / sh.tc, sh.waves);

@@ -1,6 +1,6 @@
 """Alternative execution paths that environment switches select (read once per
 process, so each runs in a subprocess): the SIMT projections instead of the
-tensor-core ones, the one-sweep-per-block bulge chase, the grid-wide panel, the
+tensor-core ones (both sides, or the LQ side alone), the one-sweep-per-block bulge chase, the grid-wide panel, the
 shared-memory cluster panel, programmatic dependent launch and other sweep-group sizes.  Each must give the same
 singular values as the FP64 oracle within the parity tolerance."""
 import json
@@ -35,7 +35,8 @@ print(json.dumps(out))
 """
 
 VARIANTS = {
-    "simt_projection": {"NLA_PROJ_TC": "0"},
+    "simt_projections": {"NLA_PROJ_TC": "0"},
+    "simt_lq_projection": {"NLA_PROJ_TC": "1"},
     "chase_one_sweep_per_block": {"NLA_CHASE_GROUP": "0"},
     "chase_group_4": {"NLA_CHASE_GROUP": "4"},
     "grid_panel": {"NLA_PANEL_CLUSTER": "0"},
