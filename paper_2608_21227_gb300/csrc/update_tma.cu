@@ -936,8 +936,10 @@ strip_update_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
             for (int k = 0; k < NB; ++k) {
                 float v = 0.f;
                 if (i < M) {
+                    // (SIDE 0: the entries on and above V's diagonal hold R, inside the panel's
+                    // storage: loaded like the rest and masked, so the 64 loads carry no branch)
                     if constexpr (SIDE == 0)
-                        v = unit_lower(moff + i, k, moff + i > k ? __ldg(Pv + i + (long)k * ldp) : 0.f);
+                        v = unit_lower(moff + i, k, __ldg(Pv + i + (long)k * ldp));
                     else
                         v = __ldg(Pv + (size_t)k * M + i);
                 }
