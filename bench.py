@@ -42,6 +42,11 @@ N_PAPER = 16384      # the paper's own workload (Section 5.2): 16384 x 16384 FP3
 # tile 64, over its parameter space -- other GPUs, context only
 PAPER_TABLE2 = {"MI210": (5.7, 32), "MI300X": (1.8, 12), "A4000": (10.5, 36), "H200": (2.9, 11), "L40S": (4.5, 12),
                 "PVC_Max_1550": (9.1, 32), "M1_Pro": (80, 244)}
+# DRAM bytes (read + written) of every trailing-update launch of one FP32 8192 SVD at band 16
+# (2,044 launches: both projections and both strip updates), from one ncu capture of this
+# benchmark (dram__bytes_read.sum + dram__bytes_write.sum; profiles/launches_svdvals_fp32_8192.md).
+# Retake it whenever an update kernel changes.
+UPDATE_TRAFFIC_8192 = 235.156e9
 METRIC = "SVD GFLOP/s (4mn^2 - 4n^3/3 per matrix), singular values of a dense FP32 matrix"
 
 
@@ -477,9 +482,12 @@ def main():
         byts = (trail_bytes_per_step(n, n, b, 0) + trail_bytes_per_step(n, n, b, 1)) * args.steps
         note = "3-pass bytes per side (read X twice, write once); trailing blocks below 129 MB run from L2"
         achieved = byts / secs / 1e9
+        traffic = UPDATE_TRAFFIC_8192 if (n == 8192 and b == 16) else None
         roof = {"kernel": "trailing update (" + " + ".join(upd_regions) + ")", "bound": "hbm",
                 "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                "traffic": None, "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)", "note": note}
+                "traffic": traffic, "traffic_unit": "bytes per step (all update launches of one SVD; ncu)",
+                "algorithmic_bytes_per_step": byts / args.steps,
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (burst copy)", "note": note}
     elif dom == "band2bd":
         # each block step reads and writes its window: 3 b^2 entries, about n^2 / (2 b) steps
         b = nla.plan_cfg(n, n, nla.F32, side=0)[0]

@@ -758,8 +758,10 @@ lq_proj_tm_kernel(const __grid_constant__ CUtensorMap tmX, int M, int N, const f
             float v[kVe];
 #pragma unroll
             for (int u = 0; u < kVe; ++u) {  // entry (k, j): V(cb + j, k), unit lower
+                // (the address clamped into the split, the entry masked: no branch per load)
                 const int e = ct + 128 * u, j = e / NB, k = e % NB, c = cb + j;
-                v[u] = c < cend ? unit_lower(c, k, __ldg(Vt + k + (size_t)c * ldvt)) : 0.f;
+                const float raw = __ldg(Vt + k + (size_t)min(c, cend - 1) * ldvt);
+                v[u] = c < cend ? unit_lower(c, k, raw) : 0.f;
             }
             if (!tc::mbar_wait_lanes(&xfull[xs], (uint32_t)((t / SX) & 1), info, &sh_abort) || sh_abort) {
                 sh_abort = 1;
