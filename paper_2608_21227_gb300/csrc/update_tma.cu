@@ -752,17 +752,29 @@ lq_proj_tm_kernel(const __grid_constant__ CUtensorMap tmX, int M, int N, const f
         const int q = warp & 3, ct = tid - 64;
         constexpr int kVe = NB * kLqCols / 128;  // V entries per thread and stage
         const uint32_t lane_base = tbase + ((uint32_t)(32 * q) << 16);
+        // V of stage t, loaded a stage ahead (its L2 latency hides behind the previous stage):
+        // entry (k, j) = V(cb + j, k), the address clamped into the split, the value masked to
+        // the unit lower form after the load (no branch per load)
+        float vraw[kVe];
+        auto load_v = [&](int t) {
+            const int cb = cbeg + t * kLqCols;
+#pragma unroll
+            for (int u = 0; u < kVe; ++u) {
+                const int e = ct + 128 * u, j = e / NB, k = e % NB;
+                vraw[u] = __ldg(Vt + k + (size_t)min(cb + j, cend - 1) * ldvt);
+            }
+        };
+        if (nt > 0) load_v(0);
         for (int t = 0; t < nt; ++t) {
             const int xs = t % SX, o = t % kLqStages;
             const int cb = cbeg + t * kLqCols;
             float v[kVe];
 #pragma unroll
-            for (int u = 0; u < kVe; ++u) {  // entry (k, j): V(cb + j, k), unit lower
-                // (the address clamped into the split, the entry masked: no branch per load)
+            for (int u = 0; u < kVe; ++u) {
                 const int e = ct + 128 * u, j = e / NB, k = e % NB, c = cb + j;
-                const float raw = __ldg(Vt + k + (size_t)min(c, cend - 1) * ldvt);
-                v[u] = c < cend ? unit_lower(c, k, raw) : 0.f;
+                v[u] = c < cend ? unit_lower(c, k, vraw[u]) : 0.f;
             }
+            if (t + 1 < nt) load_v(t + 1);
             if (!tc::mbar_wait_lanes(&xfull[xs], (uint32_t)((t / SX) & 1), info, &sh_abort) || sh_abort) {
                 sh_abort = 1;
                 break;
