@@ -311,7 +311,8 @@ qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
                   int *info) {
     pdl_wait();
     pdl_trigger();
-    constexpr uint32_t kCols = NB < 32 ? 32 : NB;  // TMEM columns (power of two >= 32)
+    // TMEM: D1 = hi x [V_hi | V_lo] (2 NB columns), D2 = lo x V_hi (NB columns)
+    constexpr uint32_t kCols = 3 * NB <= 32 ? 32 : 3 * NB <= 64 ? 64 : 3 * NB <= 128 ? 128 : 256;
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t full[kMaxStages], conv[kMaxStages], empty[kMaxStages], accdone;
     __shared__ uint32_t tmem_base;
@@ -368,7 +369,9 @@ qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t id = tc::idesc(2, 128, NB);
+            // V_lo lies right after V_hi (NB rows of 128 bytes each): [V_hi; V_lo] is one B
+            // operand of 2 NB rows, so the hi copy of X is read once per K step
+            const uint32_t id2 = tc::idesc(2, 128, 2 * NB), id1 = tc::idesc(2, 128, NB);
             for (int t = 0; t < nt; ++t) {
                 const int st = t % S;
                 if (*(volatile int *)&sh_abort || !tc::mbar_wait(&conv[st], (uint32_t)((t / S) & 1), info)) {
@@ -377,14 +380,12 @@ qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
                 }
                 tc::fence_after_sync();
                 const uint32_t ah = tc::smem_u32(xhi(st)), al = tc::smem_u32(xlo(st));
-                const uint32_t bh = tc::smem_u32(vhi(st)), bl = tc::smem_u32(vlo(st));
+                const uint32_t bh = tc::smem_u32(vhi(st));
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk) {  // 8 TF32 = 32 bytes of K per instruction
-                    const uint32_t off = kk * 32;
-                    tc::mma_tf32(tbase, tc::sdesc_sw128(ah + off), tc::sdesc_sw128(bh + off), id,
-                                 (t > 0 || kk > 0) ? 1u : 0u);
-                    tc::mma_tf32(tbase, tc::sdesc_sw128(ah + off), tc::sdesc_sw128(bl + off), id, 1u);
-                    tc::mma_tf32(tbase, tc::sdesc_sw128(al + off), tc::sdesc_sw128(bh + off), id, 1u);
+                    const uint32_t off = kk * 32, acc = (t > 0 || kk > 0) ? 1u : 0u;
+                    tc::mma_tf32(tbase, tc::sdesc_sw128(ah + off), tc::sdesc_sw128(bh + off), id2, acc);
+                    tc::mma_tf32(tbase + 2 * NB, tc::sdesc_sw128(al + off), tc::sdesc_sw128(bh + off), id1, acc);
                 }
                 tc::mma_commit(&empty[st]);  // the stage is free once these MMAs have read it
             }
@@ -436,12 +437,15 @@ qr_proj_tc_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant
         if (ok && !*(volatile int *)&sh_abort) {
 #pragma unroll
             for (int c = 0; c < NB; c += 16) {
-                float w[16];
-                tc::tmem_ld16(tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c, w);
+                float w[16], wl[16], w2[16];  // hi.hi, hi.lo, lo.hi
+                const uint32_t lb = tbase + ((uint32_t)(32 * q) << 16) + (uint32_t)c;
+                tc::tmem_ld16(lb, w);
+                tc::tmem_ld16(lb + NB, wl);
+                tc::tmem_ld16(lb + 2 * NB, w2);
                 tc::tmem_wait_ld();
                 if (col < wc) {
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) part[((size_t)sp * NB + c + k) * N + c0 + col] = w[k];
+                    for (int k = 0; k < 16; ++k) part[((size_t)sp * NB + c + k) * N + c0 + col] = w[k] + (wl[k] + w2[k]);
                 }
             }
         }
