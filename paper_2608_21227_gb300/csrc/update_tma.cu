@@ -670,8 +670,12 @@ lq_proj_tm_kernel(const __grid_constant__ CUtensorMap tmX, int M, int N, const f
     constexpr int H = 128;                            // rows per block = the MMA's M
     constexpr int kX = 4 * kLqXBox;                   // the stage's 128 rows
     constexpr int kB = NB * 128;                      // V^T of the stage's 32 columns (hi or lo)
-    constexpr uint32_t kD = NB < 32 ? 32 : NB;        // TMEM columns of the accumulator
-    constexpr uint32_t kCols = kD + 64 * kLqStages <= 256 ? 256 : 512;
+    // At NB = 16 the accumulator is split like qr_proj_tc's (D1 = A_hi [V_hi; V_lo], 2 NB
+    // columns; D2 = A_lo V_hi, NB columns: two MMAs per K step); the wider forms keep one
+    // accumulator and three MMAs (the split one would not leave room for three slots).
+    constexpr bool kStack = NB == 16;
+    constexpr uint32_t kD = kStack ? 64 : (NB < 32 ? 32 : NB);  // TMEM columns of the accumulator(s)
+    constexpr uint32_t kCols = 256;
     static_assert(kD + 64 * kLqStages <= 256, "TMEM budget: two blocks per SM");
     extern __shared__ unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t xfull[kMaxStages], xfree[kMaxStages], conv[kLqStages], ofree[kLqStages], accdone;
@@ -729,7 +733,7 @@ lq_proj_tm_kernel(const __grid_constant__ CUtensorMap tmX, int M, int N, const f
         }
     } else if (warp == 1) {
         if (lane == 0) {
-            const uint32_t id = tc::idesc(2, 128, NB);
+            const uint32_t id = tc::idesc(2, 128, NB), id2 = tc::idesc(2, 128, 2 * NB);
             for (int t = 0; t < nt; ++t) {
                 const int o = t % kLqStages;
                 if (*(volatile int *)&sh_abort || !tc::mbar_wait(&conv[o], (uint32_t)((t / kLqStages) & 1), info)) {
@@ -741,10 +745,15 @@ lq_proj_tm_kernel(const __grid_constant__ CUtensorMap tmX, int M, int N, const f
                 const uint32_t bh = tc::smem_u32(bhi(o)), bl = tc::smem_u32(blo(o));
 #pragma unroll
                 for (int kk = 0; kk < kLqCols / 8; ++kk) {  // 8 columns per instruction
-                    const uint32_t off = kk * 32;
-                    tc::mma_tf32_tmem_a(tbase, ah + 8 * kk, tc::sdesc_sw128(bh + off), id, (t > 0 || kk > 0) ? 1u : 0u);
-                    tc::mma_tf32_tmem_a(tbase, ah + 8 * kk, tc::sdesc_sw128(bl + off), id, 1u);
-                    tc::mma_tf32_tmem_a(tbase, al + 8 * kk, tc::sdesc_sw128(bh + off), id, 1u);
+                    const uint32_t off = kk * 32, acc = (t > 0 || kk > 0) ? 1u : 0u;
+                    if constexpr (kStack) {  // B lo lies right after B hi: [V_hi; V_lo] is one operand
+                        tc::mma_tf32_tmem_a(tbase, ah + 8 * kk, tc::sdesc_sw128(bh + off), id2, acc);
+                        tc::mma_tf32_tmem_a(tbase + 2 * NB, al + 8 * kk, tc::sdesc_sw128(bh + off), id, acc);
+                    } else {
+                        tc::mma_tf32_tmem_a(tbase, ah + 8 * kk, tc::sdesc_sw128(bh + off), id, acc);
+                        tc::mma_tf32_tmem_a(tbase, ah + 8 * kk, tc::sdesc_sw128(bl + off), id, 1u);
+                        tc::mma_tf32_tmem_a(tbase, al + 8 * kk, tc::sdesc_sw128(bh + off), id, 1u);
+                    }
                 }
                 tc::mma_commit(&ofree[o]);  // the operand slot is free once these MMAs have read it
             }
@@ -825,9 +834,17 @@ lq_proj_tm_kernel(const __grid_constant__ CUtensorMap tmX, int M, int N, const f
         if (ok && !*(volatile int *)&sh_abort) {
 #pragma unroll
             for (int c = 0; c < NB; c += 16) {
-                float y[16];
+                float y[16], yl[16], y2[16];
                 tc::tmem_ld16(lane_base + (uint32_t)c, y);
+                if constexpr (kStack) {  // hi.hi + (hi.lo + lo.hi)
+                    tc::tmem_ld16(lane_base + (uint32_t)(NB + c), yl);
+                    tc::tmem_ld16(lane_base + (uint32_t)(2 * NB + c), y2);
+                }
                 tc::tmem_wait_ld();
+                if constexpr (kStack) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) y[k] += yl[k] + y2[k];
+                }
                 if (i < hr) {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) part[((size_t)s * NB + c + k) * M + i0 + i] = y[k];
