@@ -290,11 +290,14 @@ qr_proj_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ 
 
 // ------------------------------------------------------------------ qr_proj on the tensor cores
 // W^T (128 strip columns x NB) = X_strip^T V accumulated in TMEM by tcgen05.mma
-// (kind::tf32, M = 128, N = NB, K = 8 per instruction) over 32-row stages of X.
+// (kind::tf32, M = 128, K = 8 per instruction) over 32-row stages of X.
 // FP32 accuracy from TF32 operands by the three-term split x = hi + lo,
 // hi = x with the low 13 mantissa bits cleared (what the tensor core reads of an
 // FP32 word), lo = x - hi (exact): x . v ~ hi_x hi_v + hi_x lo_v + lo_x hi_v, the
-// dropped lo_x lo_v term and the truncation of lo are below 2^-21 relative.
+// dropped lo_x lo_v term and the truncation of lo are below 2^-21 relative.  The
+// first two products are one MMA against [V_hi; V_lo] (N = 2 NB, the hi copy of X
+// read once), the third a second MMA (N = NB) into its own accumulator; the
+// epilogue adds the three parts.
 // Roles: warp 0 issues the TMA loads of X and V (128-byte-swizzled boxes, which
 // are the canonical K-major operand layout); warps 2..5 write the lo copies and
 // mask V's unit diagonal; warp 1 owns TMEM and one lane issues the MMAs, each
