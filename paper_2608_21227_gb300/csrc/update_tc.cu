@@ -111,9 +111,8 @@ NLA_DEV int scale_exp(double mx) {
 // integer instructions.  An FP64 x = (-1)^s 1.m 2^(E-1023) (biased exponent E of
 // 11 bits, 52-bit m) is normal or zero throughout (subnormal inputs read as 0).
 // Biased exponent of |x| (0 for zero); the scale exponent of a set of values is
-// max(E) - 1022 (the frexp exponent of the largest), 0 if all are zero.
+// max(E) - 1022 (the frexp exponent of the largest).
 NLA_DEV int f64_biased_exp(double x) { return (int)(((uint32_t)__double2hiint(x) >> 20) & 0x7FFu); }
-NLA_DEV int scale_exp_from_biased(int emax) { return emax > 0 ? emax - 1022 : 0; }
 // Scale exponent of a tile line for the step-1 accumulation: kNoExp marks a line whose
 // entries are all zero (it adds nothing to the product).
 constexpr int kNoExp = -100000;
